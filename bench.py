@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Throughput of the ERPP coupling step on GB300.
+
+One step = bin + gather + self-disturbance removal + Stokes drag + FP64
+Euler advance + regularised source scatter (erpp_step), FP32 kernels with
+FP64 particle integration, on the homogeneous-shear-like workload: periodic
+box 4pi x 2pi x 2pi, 512 x 256 x 256 grid, 1,000,000 particles, sigma_R = dx,
+stencil radius 3 sigma_R, mean shear S = 1, Stokes-number mix {0.1, 1, 10},
+mass loading 0.4.  The fluid field is held fixed (the fluid solver is not
+part of the coupling step).  Inputs are synthetic and seeded.
+
+Metric: particle-stencil node updates per second (every stencil node of
+every particle, counted once for the gather and once for the scatter), and
+coupling steps per second.  With --gpus N > 1 (torchrun) every rank runs an
+independent box of its own (weak scaling, no data-path collective).
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import erpp_inputs as I  # noqa: E402
+
+WORKLOAD = I.CFG_SHEAR
+METRIC = "particle-stencil node updates/s (gather + scatter) at 1M particles"
+UNIT = "node-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kahan", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples while the timed loop runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower().startswith("active")})
+        loaded = sorted(sm)[len(sm) // 2:] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def stencil_nodes(x, w):
+    """Stencil nodes per particle (same window rule as the kernels), summed."""
+    sig = math.sqrt(2 * w.nu * w.eps_R)
+    rc = w.cutoff * sig
+    total = np.ones(x.shape[1], dtype=np.int64)
+    for a in range(3):
+        inv = w.n[a] / w.L[a]
+        s = x[a] * inv
+        cp = rc * inv
+        total *= (np.floor(s + cp) - np.ceil(s - cp) + 1).astype(np.int64)
+    return int(total.sum())
+
+
+def algorithmic_bytes(w, n_p):
+    """Bytes the step must move: read u and write S once
+    (12 B per node each, FP32), and per particle read x, v, x_prev, D,
+    radius, rho_p (112 B) and write x, v, x_prev, D (96 B)."""
+    return {"gather": 12 * w.n_nodes, "scatter": 12 * w.n_nodes, "advance": 208 * n_p,
+            "step": 24 * w.n_nodes + 208 * n_p}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = WORKLOAD
+    grid, _ = I.make_grid(w)
+    st = I.make_particles(w, None)
+    n_s = 20000
+    p = w.params()
+    times = []
+    nodes = 0
+    for k in range(args.warmup + args.steps):
+        sub = I.ParticleState(*(np.ascontiguousarray(a[..., (k * n_s) % w.n_particles:][..., :n_s])
+                                for a in (st.x, st.v, st.x_prev, st.D, st.radius, st.rho_p)))
+        nn = 2 * stencil_nodes(sub.x, w)
+        t0 = time.perf_counter()
+        oracle.step(p, grid, sub, first_step=False)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            nodes += nn
+    total = sum(times)
+    value = nodes / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "particles_per_step_sample": n_s,
+                   "grid": list(w.n), "box": list(w.L)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n_s} particles of the 1M cloud per step on the full "
+                                   f"512x256x256 grid (one oracle step each)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, grid, st):
+    import oracle
+    oracle.build()
+    n_s = 500_000
+    sub = I.ParticleState(*(np.ascontiguousarray(a[..., :n_s])
+                            for a in (st.x, st.v, st.x_prev, st.D, st.radius, st.rho_p)))
+    nn = 2 * stencil_nodes(sub.x, w)
+    t0 = time.perf_counter()
+    oracle.step(w.params(), grid, sub, first_step=False)
+    dt = time.perf_counter() - t0
+    return {"value": nn / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one FP64 oracle step of {n_s} of the 1M particles on the full "
+                      f"512x256x256 grid ({dt:.1f} s, single thread)"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1405_6969_gb300 import Context, ParticleState
+    from paper_1405_6969_gb300 import build as libbuild
+    libbuild.build()
+
+    w = WORKLOAD
+    seed = rank
+    grid64, _ = I.make_grid(w, seed=w.field_seed + seed)
+    st = I.make_particles(w, None, seed=w.particle_seed + seed)
+    u = torch.as_tensor(grid64, dtype=torch.float32).cuda().contiguous()
+    ps = ParticleState.from_numpy(st)
+    ctx = Context(w.params(), precision="fp32", kahan=args.kahan)
+    S = ctx.new_grid()
+    nodes_per_step = 2 * stencil_nodes(st.x, w)
+    stream = torch.cuda.current_stream()
+
+    # warm-up (the first step has no previous force to remove)
+    for k in range(args.warmup):
+        ctx.step(u, ps, S=S, first_step=(k == 0))
+    ctx.check()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    ctx.profile_enable(True)
+    ctx.profile_read()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.step(u, ps, S=S)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    phase_ms, nsteps = ctx.profile_read()
+    ctx.profile_enable(False)
+    ctx.check()
+    elapsed_ms = e0.elapsed_time(e1)
+    t_max = elapsed_ms
+    if ws > 1:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_per_step = t_max / args.steps
+    value = ws * nodes_per_step * args.steps / (t_max * 1e-3)
+
+    # roofline of the dominant kernel, timed live with CUDA events
+    names = ["bin", "gather", "advance", "scatter"]
+    per = {nm: phase_ms[k] / max(nsteps, 1) for k, nm in enumerate(names)}
+    alg = algorithmic_bytes(w, w.n_particles)
+    dom = max(("gather", "scatter"), key=lambda nm: per[nm])
+    peak, peak_kind = measured_peaks()
+    achieved = alg[dom] / (per[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_kind": peak_kind}
+    step_gbs = alg["step"] / (ms_per_step * 1e-3) / 1e9
+
+    # end to end through the public API: host (pinned) buffers in and out
+    e2e = None
+    if not args.no_e2e:
+        hu = torch.empty(u.shape, dtype=torch.float32, pin_memory=True).copy_(u.cpu())
+        hs = {k: torch.empty(getattr(ps, k).shape, dtype=torch.float64, pin_memory=True)
+              .copy_(getattr(ps, k).cpu()) for k in ("x", "v", "x_prev", "D", "radius", "rho_p")}
+        hS = torch.empty(S.shape, dtype=torch.float32, pin_memory=True)
+        d_u = torch.empty_like(u)
+        h2d = hu.numel() * 4 + sum(t.numel() * 8 for t in hs.values())
+        d2h = hS.numel() * 4 + sum(hs[k].numel() * 8 for k in ("x", "v", "x_prev", "D"))
+        k_e2e = max(3, min(args.steps, 20))
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(k_e2e):
+            d_u.copy_(hu, non_blocking=True)
+            for k, t in hs.items():
+                getattr(ps, k).copy_(t, non_blocking=True)
+            ctx.step(d_u, ps, S=S)
+            hS.copy_(S, non_blocking=True)
+            for k in ("x", "v", "x_prev", "D"):
+                hs[k].copy_(getattr(ps, k), non_blocking=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = a0.elapsed_time(a1)
+        if ws > 1:
+            t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": ws * nodes_per_step * k_e2e / (e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k_e2e,
+               "ms_per_step": e_ms / k_e2e}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, grid64, st)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 kernels, f64 particle integration", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.n), "box": [round(v, 6) for v in w.L],
+                       "particles_per_gpu": w.n_particles, "sigma_over_dx": w.sigma_over_dx,
+                       "cutoff_sigmas": w.cutoff, "precision": "fp32",
+                       "kahan": bool(args.kahan),
+                       "l2": "inputs larger than L2: u and S 403 MB each, particles 112 MB",
+                       "fluid": "held fixed during the timed steps"},
+            "steps_per_s": 1e3 / ms_per_step,
+            "node_updates_per_step": nodes_per_step,
+            "phase_ms": per,
+            "step_hbm": {"alg_bytes": alg["step"], "achieved_gbs": step_gbs,
+                         "frac": step_gbs / peak},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 6 * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * erpp.h -- C ABI of the GB300 implementation of the Exact Regularized Point
+ * Particle (ERPP) two-way coupling step (Gualtieri, Picano, Sardina &
+ * Casciola, arXiv 1405.6969).
+ *
+ * The library computes, on one GPU, the coupling between point particles and
+ * an Eulerian fluid grid:
+ *   - the regularised momentum source of Sec. 2.4, Eq. ns_regularized_filtered:
+ *       S(x) = -(1/rho_f) sum_p D_p g(x - x_p, eps_R),
+ *     with g the heat kernel of App. A.1 (Eq. fundamental_phys): a Gaussian
+ *     of width sigma_R = sqrt(2 nu eps_R), truncated at cutoff * sigma_R on
+ *     every axis and (by default) normalised to unit discrete mass per axis;
+ *   - the matching kernel gather of the fluid velocity at the particles;
+ *   - the removal of each particle's own regularised disturbance
+ *     (Sec. 2.5 and the closed form of App. A.5, Eq. disturbance_velo);
+ *   - the Stokes drag of Sec. 2.5 (Eq. force_stokes_drag) and one explicit
+ *     Euler step of Eq. particle_motion.
+ *
+ * Conventions shared by every entry point
+ *   Grid: periodic box [0,Lx) x [0,Ly) x [0,Lz), nodes at j * L / N.  Grid
+ *     fields are three contiguous components, each nz*ny*nx values with x
+ *     fastest: index ((c*nz + k)*ny + j)*nx + i.  Element type: float with
+ *     ERPP_FP32, double with ERPP_FP64 (fixed at erpp_init).
+ *   Particles: structure of arrays, one device array of n doubles per
+ *     component.  Positions must lie in [0, L) on each axis.
+ *   Pointers: device pointers unless stated otherwise; the caller owns every
+ *     grid and particle buffer.  The context owns only its scratch memory.
+ *   Streams: every call is asynchronous on the given CUDA stream (NULL = the
+ *     legacy default stream) unless stated otherwise.  Calls that share one
+ *     context share its scratch: issue them on one stream, in order.
+ *   Errors: argument errors are reported synchronously by the return value
+ *     and nothing is launched.  Data errors found on the device (NaN or
+ *     out-of-box positions) set a sticky device error word that
+ *     erpp_check() or erpp_momentum() report.  No call aborts or traps.
+ */
+#ifndef ERPP_H
+#define ERPP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (the same object as cudaStream_t). */
+typedef struct CUstream_st* erpp_stream;
+
+typedef enum {
+  ERPP_OK = 0,
+  ERPP_EINVAL = 1,   /* invalid argument or parameter                      */
+  ERPP_ENOMEM = 2,   /* device allocation failed                           */
+  ERPP_ECUDA = 3,    /* a CUDA runtime call failed (no device, launch ...)  */
+  ERPP_ERANGE = 4,   /* a particle position was NaN/Inf or outside [0, L)  */
+  ERPP_EBOUNDS = 5,  /* an internal capacity or index check failed         */
+  ERPP_ETIMEOUT = 6, /* a bounded device-side wait gave up                 */
+  ERPP_ESTATE = 7    /* call not valid in the context's current state      */
+} erpp_status;
+
+/* erpp_params.flags */
+enum {
+  ERPP_FP32 = 1u << 0,         /* float grids; FP32 kernel evaluation and
+                                  accumulation; FP64 particle integration    */
+  ERPP_FP64 = 1u << 1,         /* double grids; plain FP64 kernels           */
+  ERPP_NORMALIZE = 1u << 2,    /* unit discrete mass per axis (recommended)  */
+  ERPP_SELF_REMOVAL = 1u << 3, /* subtract the closed-form self disturbance  */
+  ERPP_KAHAN = 1u << 4         /* FP32 only: compensated (two-sum) scatter
+                                  accumulation; costs a second shared array  */
+};
+
+/* Physical and numerical parameters (Sec. 2.3-2.5).  sigma_R =
+ * sqrt(2 nu eps_R); the stencil keeps, per axis, the nodes within
+ * r_c = cutoff * sigma_R of the particle.  Requirements: 2 r_c smaller than
+ * every box side, r_c at least one grid spacing and at most 15.5 grid
+ * spacings on every axis (windows of at most 31 nodes).  mu = rho_f nu. */
+typedef struct {
+  int32_t nx, ny, nz;  /* grid nodes per axis (>= 1)                          */
+  uint32_t flags;      /* exactly one of ERPP_FP32 / ERPP_FP64, plus options  */
+  double Lx, Ly, Lz;   /* box sides                                          */
+  double nu;           /* kinematic viscosity                                */
+  double rho_f;        /* fluid density                                      */
+  double eps_R;        /* regularisation time                                */
+  double cutoff;       /* stencil radius in units of sigma_R (paper: 3)      */
+  double dt;           /* time step                                          */
+  double gravity[3];   /* acceleration of gravity                            */
+  double shear_rate;   /* mean flow shear_rate * y along x, added at the
+                          particles (the grid holds the fluctuation)          */
+} erpp_params;
+
+/* Particle state: n particles, device arrays of n doubles per component. */
+typedef struct {
+  int64_t n;
+  double* x[3];        /* position, in [0, L)                                */
+  double* v[3];        /* velocity                                           */
+  double* x_prev[3];   /* position one step earlier                          */
+  double* D[3];        /* hydrodynamic force of the previous step            */
+  const double* radius;/* particle radius a_p                                */
+  const double* rho_p; /* particle density                                   */
+} erpp_particles;
+
+typedef struct erpp_ctx erpp_ctx;
+
+/* Creates a context for one grid and parameter set on the current CUDA
+ * device.  Validates params (EINVAL before any CUDA call), then allocates
+ * the context's scratch (tile tables, device error word).  *out receives the
+ * context; on failure *out is set to NULL. */
+erpp_status erpp_init(const erpp_params* params, erpp_ctx** out);
+
+/* Frees the context and its scratch (synchronises the device first).  NULL
+ * is accepted. */
+erpp_status erpp_destroy(erpp_ctx* ctx);
+
+/* Static, NUL-terminated description of a status code. */
+const char* erpp_status_string(erpp_status status);
+
+/* Matching kernel gather: u_p[c][i] = sum_j dV W_i(j) u[c][j] (+ shear_rate *
+ * y_i for c = x), W the truncated (normalised) Gaussian of the scatter.
+ * x: n positions per component; u: grid field (float/double per mode);
+ * u_p: n doubles per component (output). */
+erpp_status erpp_interpolate(erpp_ctx* ctx, const void* u, int64_t n,
+                             const double* const x[3], double* const u_p[3],
+                             erpp_stream stream);
+
+/* Self-disturbance removal, Stokes drag and one explicit Euler step
+ * (Sec. 2.5).  In: u_p = fluid velocity gathered at P->x.  With self
+ * removal and first_step == 0, the disturbance the particle left in the
+ * previous step, v_self(x - x_prev; D), is subtracted first (App. A.5 closed
+ * form at variance 2 nu (eps_R + dt) + sigma_R^2: one step of diffusion,
+ * plus the gather's own filtering).  Out: P->D = 6 pi mu a (u_p - v_self - v),
+ * P->v += dt (D / m_p + (1 - rho_f / rho_p) g), P->x += dt v (old v, wrapped
+ * into [0, L)), P->x_prev = old x.  m_p = (4/3) pi a^3 rho_p. */
+erpp_status erpp_particle_advance(erpp_ctx* ctx, const double* const u_p[3],
+                                  const erpp_particles* P, int first_step,
+                                  erpp_stream stream);
+
+/* Regularised momentum source of forces D at positions x (Eq.
+ * ns_regularized_filtered): S[c][j] = -(1/rho_f) sum_i D[c][i] W_i(j).
+ * S (grid field) is overwritten entirely. */
+erpp_status erpp_scatter_source(erpp_ctx* ctx, int64_t n, const double* const x[3],
+                                const double* const D[3], void* S, erpp_stream stream);
+
+/* One coupling step: gather u at P->x, remove the self disturbance, drag,
+ * Euler advance (as erpp_particle_advance), then scatter the new forces at
+ * the positions they were evaluated at (P->x_prev after the call) into S
+ * (overwritten).  The fluid field u is held fixed during the call. */
+erpp_status erpp_step(erpp_ctx* ctx, const void* u, const erpp_particles* P, void* S,
+                      int first_step, erpp_stream stream);
+
+/* Momentum bookkeeping (the impulse of Sec. 3.1): out[0..2] = dV sum_j S[c][j]
+ * and out[3..5] = -(1/rho_f) sum_i M_i D[c][i], M_i the discrete kernel mass
+ * (1 when normalised); both summed in FP64.  out is a HOST array of 6
+ * doubles.  Synchronises the stream, then reports the sticky device error
+ * word like erpp_check. */
+erpp_status erpp_momentum(erpp_ctx* ctx, const void* S, int64_t n, const double* const x[3],
+                          const double* const D[3], double out[6], erpp_stream stream);
+
+/* Synchronises the stream and returns (and clears) the sticky device error:
+ * ERPP_ERANGE for NaN/Inf/out-of-box positions seen since the last check,
+ * ERPP_EBOUNDS for a failed internal index check, else ERPP_OK. */
+erpp_status erpp_check(erpp_ctx* ctx, erpp_stream stream);
+
+/* Stencil windows as the kernels compute them: for each particle and axis,
+ * the first and last node index (unwrapped, may be < 0 or >= N) whose
+ * distance from x is at most cutoff * sigma_R.  jlo, jhi: device int32
+ * arrays of 3*n (component-major). */
+erpp_status erpp_debug_windows(erpp_ctx* ctx, int64_t n, const double* const x[3],
+                               int32_t* jlo, int32_t* jhi, erpp_stream stream);
+
+/* Per-phase timing (a tracing aid, not part of the method).  After
+ * erpp_profile_enable(ctx, 1) every erpp_step records CUDA events on its
+ * stream around its phases: 0 binning (count, scan, fill), 1 gather,
+ * 2 removal + drag + advance, 3 scatter.  erpp_profile_read synchronises the
+ * device, writes the accumulated milliseconds per phase to the HOST array
+ * ms[4] and the number of timed steps to *steps, and resets the counters.
+ * Up to 1024 steps are kept between two reads (older ones are dropped). */
+erpp_status erpp_profile_enable(erpp_ctx* ctx, int enable);
+erpp_status erpp_profile_read(erpp_ctx* ctx, double ms[4], int64_t* steps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ERPP_H */

@@ -91,6 +91,7 @@ def _load():
                 "orc_momentum": [P, i64, d, d, d, d],
                 "orc_scatter_backward": [P, i64, d, d, d, d, d],
                 "orc_gather_backward": [P, i64, d, d, d, d, d],
+                "orc_scatter_nodes": [P, i64, d, d, i64, i32, d],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -231,3 +232,16 @@ def gather_backward(p, x, u, G):
                                        _ptr(u), _ptr(G), _ptr(du), _ptr(dx)),
            "gather_backward")
     return du, dx
+
+
+def scatter_nodes(p, x, D, nodes):
+    """Source S[3, k] at the nodes [3, k] (int, x/y/z node indices) only."""
+    p = _params(p)
+    x, D = _f64(x), _f64(D)
+    nodes = np.ascontiguousarray(nodes, dtype=np.int32)
+    k = nodes.shape[1]
+    out = np.empty((3, k))
+    _check(_load().orc_scatter_nodes(ctypes.byref(p), x.shape[1], _ptr(x), _ptr(D), k,
+                                     nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     _ptr(out)), "scatter_nodes")
+    return out

@@ -514,3 +514,50 @@ int orc_gather_backward(const orc_params* p, int64_t np, const double* x, const 
   orc_stencil_free(&sc);
   return ORC_OK;
 }
+
+/* The source of Eq. ns_regularized_filtered at selected nodes only:
+ * out[c][k] = -(1/rho_f) sum_p D_p prod_a w_a(j_a) for the nodes
+ * nodes[k] = (jx, jy, jz), summed over every particle whose window contains
+ * the node (after wrapping).  Same arithmetic as orc_scatter, for grids too
+ * large to hold in full. */
+int orc_scatter_nodes(const orc_params* p, int64_t np, const double* x, const double* D,
+                      int64_t nnodes, const int32_t* nodes, double* out) {
+  orc_geom g;
+  int st = orc_geom_init(p, &g);
+  if (st) return st;
+  for (int64_t k = 0; k < 3 * nnodes; ++k) out[k] = 0.0;
+  orc_stencil sc;
+  if (orc_stencil_alloc(&sc, orc_max_window(&g))) { orc_stencil_free(&sc); return ORC_ENOMEM; }
+  double inv_rho = 1.0 / p->rho_f;
+  for (int64_t i = 0; i < np; ++i) {
+    int hit = 0;
+    int64_t kk[3];
+    for (int64_t k = 0; k < nnodes && !hit; ++k) {
+      hit = 1;
+      for (int a = 0; a < 3; ++a) {
+        int64_t lo, hi;
+        double s;
+        orc_window(&g, a, x[(size_t)a * np + i], &lo, &hi, &s);
+        int64_t j = nodes[(size_t)a * nnodes + k];
+        int64_t rel = orc_wrap_index(j - lo, g.n[a]);
+        if (rel > hi - lo) hit = 0;
+      }
+    }
+    if (!hit) continue;
+    orc_stencil_build(&g, p->normalize, x, np, i, &sc);
+    for (int64_t k = 0; k < nnodes; ++k) {
+      double W = 1.0;
+      for (int a = 0; a < 3; ++a) {
+        int64_t j = nodes[(size_t)a * nnodes + k];
+        int64_t rel = orc_wrap_index(j - sc.jlo[a], g.n[a]);
+        if (rel >= sc.m[a]) { W = 0.0; break; }
+        kk[a] = rel;
+      }
+      if (W == 0.0) continue;
+      W = sc.w[0][kk[0]] * sc.w[1][kk[1]] * sc.w[2][kk[2]];
+      for (int c = 0; c < 3; ++c) out[(size_t)c * nnodes + k] += (-inv_rho * D[(size_t)c * np + i]) * W;
+    }
+  }
+  orc_stencil_free(&sc);
+  return ORC_OK;
+}

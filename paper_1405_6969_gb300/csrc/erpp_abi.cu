@@ -1,0 +1,440 @@
+// erpp_abi.cu -- the C ABI: parameter validation, context and scratch
+// management, and the stream-ordered launch sequences of each entry point.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "erpp_internal.cuh"
+
+namespace {
+
+const double kPi = 3.141592653589793238462643;
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+// Most (tile, image) pieces a window of up to `xs` nodes can be cut into on
+// one axis, found by trying every window start.
+int max_pieces(int n, int T, int hlo, int xs) {
+  int best = 1;
+  for (int jlo = -hlo; jlo < n + 1; ++jlo) {
+    int cnt = 0;
+    for (int j = jlo; j <= jlo + xs - 1;) {
+      int m = (j >= 0) ? j / n : -((-j + n - 1) / n);
+      int w = j - m * n;
+      int t = w / T;
+      int e = std::min(std::min((t + 1) * T, n) - w + j - 1, jlo + xs - 1);
+      ++cnt;
+      j = e + 1;
+    }
+    best = std::max(best, cnt);
+  }
+  return best;
+}
+
+// Number of shared-memory bank conflicts (extra wavefronts) for one pass of
+// `rows` rows of `xs` lanes whose row starts are at offsets off[0..rows).
+int conflicts(const int* off, int rows, int xs) {
+  int hits[32] = {0};
+  int worst = 0;
+  for (int q = 0; q < rows; ++q)
+    for (int i = 0; i < xs; ++i) {
+      int bank = ((off[q] + i) % 32 + 32) % 32;
+      worst = std::max(worst, ++hits[bank]);
+    }
+  return worst - 1;
+}
+
+// Row pitch: smallest px >= T_x with conflict-free passes of consecutive rows.
+int choose_px(int Tx, int xs, int rows) {
+  for (int px = Tx; px < Tx + 32; ++px) {
+    int off[32];
+    for (int q = 0; q < rows; ++q) off[q] = q * px;
+    if (conflicts(off, rows, xs) == 0) return px;
+  }
+  return Tx;
+}
+
+// Plane pitch: smallest pxy >= T_y px that keeps passes crossing a z plane
+// conflict-free for the typical window height ny_w.
+int choose_pxy(int Ty, int px, int xs, int rows, int ny_w) {
+  int best = Ty * px, best_c = 1 << 30;
+  for (int pxy = Ty * px; pxy < Ty * px + 32; ++pxy) {
+    int total = 0;
+    for (int r0 = 0; r0 < 2 * ny_w; r0 += 1) {
+      int off[32];
+      for (int q = 0; q < rows; ++q) {
+        int r = r0 + q;
+        off[q] = (r % ny_w) * px + (r / ny_w) * pxy;
+      }
+      total += conflicts(off, rows, xs);
+    }
+    if (total < best_c) {
+      best_c = total;
+      best = pxy;
+      if (total == 0) break;
+    }
+  }
+  return best;
+}
+
+erpp_status set_cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return ERPP_OK;
+  if (e == cudaErrorMemoryAllocation) return ERPP_ENOMEM;
+  return ERPP_ECUDA;
+}
+
+void free_scratch(erpp_ctx* c) {
+  cudaFree(c->geo_t);
+  cudaFree(c->geo_c);
+  cudaFree(c->up_acc);
+  cudaFree(c->fscat);
+  cudaFree(c->entries);
+  cudaFree(c->up64);
+  c->geo_t = nullptr;
+  c->geo_c = nullptr;
+  c->up_acc = nullptr;
+  c->fscat = nullptr;
+  c->entries = nullptr;
+  c->up64 = nullptr;
+  c->cap = 0;
+  c->entries_cap = 0;
+}
+
+// Grow the per-particle scratch to hold n particles (synchronous when it
+// grows; the device allocation waits for outstanding work).
+erpp_status ensure_capacity(erpp_ctx* c, int64_t n) {
+  if (n <= c->cap) return ERPP_OK;
+  int64_t cap = std::max<int64_t>(n, 1024);
+  free_scratch(c);
+  cudaError_t e = cudaSuccess;
+  if (c->fp64) {
+    e = cudaMalloc(&c->up64, sizeof(double) * 3 * (size_t)cap);
+  } else {
+    int64_t ecap = cap * (int64_t)c->maxseg[0] * c->maxseg[1] * c->maxseg[2];
+    e = cudaMalloc(&c->geo_t, sizeof(float4) * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc(&c->geo_c, sizeof(int4) * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc(&c->up_acc, sizeof(float) * 3 * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc(&c->fscat, sizeof(float4) * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc(&c->entries, sizeof(uint32_t) * (size_t)ecap);
+    c->entries_cap = ecap;
+  }
+  if (e != cudaSuccess) {
+    free_scratch(c);
+    return set_cuda_err(e);
+  }
+  c->cap = cap;
+  return ERPP_OK;
+}
+
+bool valid_vec(const double* const v[3]) { return v && v[0] && v[1] && v[2]; }
+
+erpp_status check_n(int64_t n) {
+  if (n < 0 || n > ERPP_MAX_PARTICLES) return ERPP_EINVAL;
+  return ERPP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* erpp_status_string(erpp_status s) {
+  switch (s) {
+    case ERPP_OK: return "ok";
+    case ERPP_EINVAL: return "invalid argument";
+    case ERPP_ENOMEM: return "device allocation failed";
+    case ERPP_ECUDA: return "CUDA runtime error";
+    case ERPP_ERANGE: return "particle position NaN/Inf or outside the box";
+    case ERPP_EBOUNDS: return "internal capacity or index check failed";
+    case ERPP_ETIMEOUT: return "bounded device wait gave up";
+    case ERPP_ESTATE: return "call not valid in the current state";
+  }
+  return "unknown status";
+}
+
+erpp_status erpp_init(const erpp_params* p, erpp_ctx** out) {
+  if (!out) return ERPP_EINVAL;
+  *out = nullptr;
+  if (!p) return ERPP_EINVAL;
+  const int n[3] = {p->nx, p->ny, p->nz};
+  const double L[3] = {p->Lx, p->Ly, p->Lz};
+  for (int a = 0; a < 3; ++a)
+    if (n[a] < 1 || n[a] > (1 << 20) || !finite_pos(L[a])) return ERPP_EINVAL;
+  if (!finite_pos(p->nu) || !finite_pos(p->rho_f) || !finite_pos(p->eps_R) ||
+      !finite_pos(p->cutoff) || !isfinite(p->dt) || p->dt < 0.0 || !isfinite(p->shear_rate))
+    return ERPP_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (!isfinite(p->gravity[a])) return ERPP_EINVAL;
+  const uint32_t prec = p->flags & (ERPP_FP32 | ERPP_FP64);
+  if (prec != ERPP_FP32 && prec != ERPP_FP64) return ERPP_EINVAL;
+  if ((p->flags & ERPP_KAHAN) && prec != ERPP_FP32) return ERPP_EINVAL;
+  if (p->flags & ~(uint32_t)(ERPP_FP32 | ERPP_FP64 | ERPP_NORMALIZE | ERPP_SELF_REMOVAL |
+                             ERPP_KAHAN))
+    return ERPP_EINVAL;
+  if ((double)n[0] * n[1] * n[2] * 3.0 >= 9.0e18) return ERPP_EINVAL;
+
+  erpp_kparams kp;
+  memset(&kp, 0, sizeof(kp));
+  // Same expressions, same order as the FP64 oracle: the stencil windows
+  // must agree bit for bit.
+  const double sig2 = (2.0 * p->nu) * p->eps_R;
+  const double sig = sqrt(sig2);
+  const double rc = p->cutoff * sig;
+  double cpmax = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    kp.n[a] = n[a];
+    kp.L[a] = L[a];
+    kp.inv_dx[a] = (double)n[a] / L[a];
+    kp.dx[a] = L[a] / (double)n[a];
+    kp.cp[a] = rc * kp.inv_dx[a];
+    if (!(2.0 * rc < L[a])) return ERPP_EINVAL;
+    cpmax = std::max(cpmax, kp.cp[a]);
+  }
+  double cpmin = std::min(kp.cp[0], std::min(kp.cp[1], kp.cp[2]));
+  if (cpmin < 1.0) return ERPP_EINVAL;  // r_c must reach at least one grid spacing
+  // A window starts at most floor(c') nodes below the particle's cell and holds
+  // at most floor(2 c') + 1 nodes (one more when 2 c' sits within rounding of
+  // an integer).
+  kp.hlo = (int)floor(cpmax);
+  kp.xs = (int)floor(2.0 * cpmax + 1e-6) + 1;
+  if (kp.hlo > 15 || kp.xs > 31) return ERPP_EINVAL;  // windows of at most 31 nodes
+  kp.rows = 32 / kp.xs;
+  kp.dV = kp.dx[0] * kp.dx[1] * kp.dx[2];
+  kp.rho_f = p->rho_f;
+  kp.nu = p->nu;
+  kp.eps_R = p->eps_R;
+  kp.dt = p->dt;
+  kp.mu = p->rho_f * p->nu;
+  for (int a = 0; a < 3; ++a) kp.gravity[a] = p->gravity[a];
+  kp.shear_rate = p->shear_rate;
+  kp.sig2 = sig2;
+  kp.raw_norm3 = pow(2.0 * kPi * sig2, -1.5);
+  kp.self_s2 = (2.0 * p->nu) * (p->eps_R + p->dt) + (2.0 * p->nu) * p->eps_R;
+  kp.self_pref = (float)(-(p->dt / p->rho_f) / pow(2.0 * kPi * kp.self_s2, 1.5));
+  kp.self_inv_w = (float)(1.0 / sqrt(2.0 * kp.self_s2));
+  const double log2e = 1.4426950408889634;
+  for (int a = 0; a < 3; ++a) kp.beta[a] = (float)(log2e * kp.dx[a] * kp.dx[a] / (2.0 * sig2));
+  kp.inv_rho_dV = (float)(1.0 / (p->rho_f * kp.dV));
+  kp.normalize = (p->flags & ERPP_NORMALIZE) ? 1 : 0;
+  kp.self_removal = (p->flags & ERPP_SELF_REMOVAL) ? 1 : 0;
+  kp.kahan = (p->flags & ERPP_KAHAN) ? 1 : 0;
+  // Tiles: 32 x 16 x 8 nodes (clamped to the grid).
+  const int Tdef[3] = {32, 16, 8};
+  int64_t ntiles = 1;
+  for (int a = 0; a < 3; ++a) {
+    kp.T[a] = std::min(Tdef[a], n[a]);
+    kp.nt[a] = (n[a] + kp.T[a] - 1) / kp.T[a];
+    ntiles *= kp.nt[a];
+  }
+  if (ntiles > (1 << 26)) return ERPP_EINVAL;
+  kp.ntiles = (int)ntiles;
+  kp.px = choose_px(kp.T[0], kp.xs, kp.rows);
+  const int ny_w = std::max(1, (int)floor(2.0 * kp.cp[1]));
+  kp.pxy = choose_pxy(kp.T[1], kp.px, kp.xs, kp.rows, ny_w);
+  kp.plane = kp.pxy * kp.T[2];
+  if ((size_t)kp.plane * 6 * sizeof(float) > 227 * 1024) return ERPP_EINVAL;
+
+  erpp_ctx* c = (erpp_ctx*)calloc(1, sizeof(erpp_ctx));
+  if (!c) return ERPP_ENOMEM;
+  c->params = *p;
+  c->kp = kp;
+  c->fp64 = prec == ERPP_FP64;
+  for (int a = 0; a < 3; ++a) c->maxseg[a] = max_pieces(n[a], kp.T[a], kp.hlo, kp.xs);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&c->red, sizeof(double) * (6 * 304 + 8));
+  if (e == cudaSuccess && !c->fp64) {
+    e = cudaMalloc(&c->tile_cnt, sizeof(int32_t) * (size_t)kp.ntiles);
+    if (e == cudaSuccess) e = cudaMalloc(&c->tile_start, sizeof(int32_t) * ((size_t)kp.ntiles + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&c->tile_cursor, sizeof(int32_t) * (size_t)kp.ntiles);
+  }
+  if (e != cudaSuccess) {
+    erpp_status s = set_cuda_err(e);
+    erpp_destroy(c);
+    cudaGetLastError();
+    return s;
+  }
+  *out = c;
+  return ERPP_OK;
+}
+
+erpp_status erpp_destroy(erpp_ctx* c) {
+  if (!c) return ERPP_OK;
+  cudaDeviceSynchronize();
+  if (c->prof_ev) {
+    for (int k = 0; k < kProfSets * 5; ++k) cudaEventDestroy(c->prof_ev[k]);
+    free(c->prof_ev);
+  }
+  free_scratch(c);
+  cudaFree(c->tile_cnt);
+  cudaFree(c->tile_start);
+  cudaFree(c->tile_cursor);
+  cudaFree(c->err);
+  cudaFree(c->red);
+  free(c);
+  return ERPP_OK;
+}
+
+erpp_status erpp_interpolate(erpp_ctx* c, const void* u, int64_t n, const double* const x[3],
+                             double* const up[3], erpp_stream stream) {
+  if (!c || !u || check_n(n)) return ERPP_EINVAL;
+  if (n == 0) return ERPP_OK;
+  if (!valid_vec(x) || !up || !up[0] || !up[1] || !up[2]) return ERPP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  erpp_status s = ensure_capacity(c, n);
+  if (s) return s;
+  cudaError_t e;
+  if (c->fp64) {
+    e = erpp::launch_gather_f64(c, (const double*)u, n, x, up, st);
+  } else {
+    e = erpp::bin_particles(c, n, x, true, st);
+    if (e == cudaSuccess) e = erpp::launch_gather_f32(c, (const float*)u, n, st);
+    if (e == cudaSuccess) e = erpp::launch_finalize_up(c, n, x, up, st);
+  }
+  return set_cuda_err(e);
+}
+
+erpp_status erpp_particle_advance(erpp_ctx* c, const double* const up[3], const erpp_particles* P,
+                                  int first_step, erpp_stream stream) {
+  if (!c || !P || check_n(P->n)) return ERPP_EINVAL;
+  if (P->n == 0) return ERPP_OK;
+  if (!up || !up[0] || !up[1] || !up[2] || !P->radius || !P->rho_p) return ERPP_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (!P->x[a] || !P->v[a] || !P->x_prev[a] || !P->D[a]) return ERPP_EINVAL;
+  cudaError_t e = erpp::launch_advance(c, P, up, false, false, first_step, (cudaStream_t)stream);
+  return set_cuda_err(e);
+}
+
+erpp_status erpp_scatter_source(erpp_ctx* c, int64_t n, const double* const x[3],
+                                const double* const D[3], void* S, erpp_stream stream) {
+  if (!c || !S || check_n(n)) return ERPP_EINVAL;
+  if (n > 0 && (!valid_vec(x) || !valid_vec(D))) return ERPP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  erpp_status s = ensure_capacity(c, n);
+  if (s) return s;
+  cudaError_t e;
+  if (c->fp64) {
+    e = erpp::launch_scatter_f64(c, n, x, D, (double*)S, st);
+  } else {
+    e = erpp::bin_particles(c, n, x, false, st);
+    if (e == cudaSuccess) e = erpp::launch_prep_fscat(c, n, D, st);
+    if (e == cudaSuccess) e = erpp::launch_scatter_f32(c, (float*)S, st);
+  }
+  return set_cuda_err(e);
+}
+
+erpp_status erpp_step(erpp_ctx* c, const void* u, const erpp_particles* P, void* S,
+                      int first_step, erpp_stream stream) {
+  if (!c || !u || !P || !S || check_n(P->n)) return ERPP_EINVAL;
+  if (P->n > 0) {
+    if (!P->radius || !P->rho_p) return ERPP_EINVAL;
+    for (int a = 0; a < 3; ++a)
+      if (!P->x[a] || !P->v[a] || !P->x_prev[a] || !P->D[a]) return ERPP_EINVAL;
+  }
+  const int64_t n = P->n;
+  cudaStream_t st = (cudaStream_t)stream;
+  erpp_status s = ensure_capacity(c, n);
+  if (s) return s;
+  const double* const xin[3] = {P->x[0], P->x[1], P->x[2]};
+  const double* const xprev[3] = {P->x_prev[0], P->x_prev[1], P->x_prev[2]};
+  const double* const Dv[3] = {P->D[0], P->D[1], P->D[2]};
+  cudaError_t e;
+  if (c->fp64) {
+    double* up[3] = {c->up64, c->up64 + c->cap, c->up64 + 2 * c->cap};
+    e = erpp::launch_gather_f64(c, (const double*)u, n, xin, up, st);
+    const double* const upc[3] = {up[0], up[1], up[2]};
+    if (e == cudaSuccess) e = erpp::launch_advance(c, P, upc, false, false, first_step, st);
+    if (e == cudaSuccess) e = erpp::launch_scatter_f64(c, n, xprev, Dv, (double*)S, st);
+  } else {
+    cudaEvent_t* ev = nullptr;
+    if (c->prof_on) ev = c->prof_ev + 5 * (c->prof_n++ % kProfSets);
+    if (ev) cudaEventRecord(ev[0], st);
+    e = erpp::bin_particles(c, n, xin, true, st);
+    if (ev) cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess) e = erpp::launch_gather_f32(c, (const float*)u, n, st);
+    if (ev) cudaEventRecord(ev[2], st);
+    if (e == cudaSuccess) e = erpp::launch_advance(c, P, nullptr, true, true, first_step, st);
+    if (ev) cudaEventRecord(ev[3], st);
+    if (e == cudaSuccess) e = erpp::launch_scatter_f32(c, (float*)S, st);
+    if (ev) cudaEventRecord(ev[4], st);
+  }
+  return set_cuda_err(e);
+}
+
+erpp_status erpp_profile_enable(erpp_ctx* c, int enable) {
+  if (!c) return ERPP_EINVAL;
+  if (enable && !c->prof_ev) {
+    c->prof_ev = (cudaEvent_t*)calloc((size_t)kProfSets * 5, sizeof(cudaEvent_t));
+    if (!c->prof_ev) return ERPP_ENOMEM;
+    for (int k = 0; k < kProfSets * 5; ++k) {
+      cudaError_t e = cudaEventCreate(&c->prof_ev[k]);
+      if (e != cudaSuccess) return set_cuda_err(e);
+    }
+  }
+  c->prof_on = enable ? 1 : 0;
+  return ERPP_OK;
+}
+
+erpp_status erpp_profile_read(erpp_ctx* c, double ms[4], int64_t* steps) {
+  if (!c || !ms || !steps) return ERPP_EINVAL;
+  for (int k = 0; k < 4; ++k) ms[k] = 0.0;
+  *steps = 0;
+  if (!c->prof_ev) return ERPP_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return set_cuda_err(e);
+  int nsets = c->prof_n < kProfSets ? c->prof_n : kProfSets;
+  for (int s = 0; s < nsets; ++s) {
+    cudaEvent_t* ev = c->prof_ev + 5 * s;
+    for (int k = 0; k < 4; ++k) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      if (e != cudaSuccess) return set_cuda_err(e);
+      ms[k] += t;
+    }
+  }
+  *steps = nsets;
+  c->prof_n = 0;
+  return ERPP_OK;
+}
+
+erpp_status erpp_check(erpp_ctx* c, erpp_stream stream) {
+  if (!c) return ERPP_EINVAL;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return set_cuda_err(e);
+  uint32_t h = 0;
+  e = cudaMemcpy(&h, c->err, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return set_cuda_err(e);
+  if (h) {
+    e = cudaMemset(c->err, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) return set_cuda_err(e);
+  }
+  if (h & ERPP_ERRBIT_RANGE) return ERPP_ERANGE;
+  if (h & ERPP_ERRBIT_BOUNDS) return ERPP_EBOUNDS;
+  if (h & ERPP_ERRBIT_TIMEOUT) return ERPP_ETIMEOUT;
+  return ERPP_OK;
+}
+
+erpp_status erpp_momentum(erpp_ctx* c, const void* S, int64_t n, const double* const x[3],
+                          const double* const D[3], double out[6], erpp_stream stream) {
+  if (!c || !S || !out || check_n(n)) return ERPP_EINVAL;
+  if (n > 0 && (!valid_vec(x) || !valid_vec(D))) return ERPP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = erpp::launch_momentum(c, S, n, x, D, st);
+  if (e != cudaSuccess) return set_cuda_err(e);
+  e = cudaMemcpyAsync(out, c->red + 6 * 304, sizeof(double) * 6, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return set_cuda_err(e);
+  return erpp_check(c, stream);
+}
+
+erpp_status erpp_debug_windows(erpp_ctx* c, int64_t n, const double* const x[3], int32_t* jlo,
+                               int32_t* jhi, erpp_stream stream) {
+  if (!c || check_n(n)) return ERPP_EINVAL;
+  if (n == 0) return ERPP_OK;
+  if (!valid_vec(x) || !jlo || !jhi) return ERPP_EINVAL;
+  return set_cuda_err(erpp::launch_windows(c, n, x, jlo, jhi, (cudaStream_t)stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// erpp_internal.cuh -- shared declarations of the ERPP CUDA library.
+//
+// Layout of the per-step data in HBM (FP32 tiled path):
+//   geo_t[i]  float4  (t_x, t_y, t_z, norm): fractional position of particle i
+//                     inside its home cell and the kernel normalisation
+//   geo_c[i]  int4    (c_x, c_y, c_z, pack): home cell and packed window
+//                     (offset of the first node below the cell, window length)
+//   entries[] uint32  one per (particle, tile, periodic shift) whose window
+//                     reaches the tile interior, grouped by tile (counting sort)
+//   up_acc    float[3][n]  gathered velocity before normalisation
+//   fscat[i]  float4  -(1/rho_f) D_i norm / dV: the force as the scatter uses it
+// Grids are [3][nz][ny][nx] (x fastest), tiles are boxes of T_x*T_y*T_z nodes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/erpp.h"
+
+// Sticky device error bits.
+#define ERPP_ERRBIT_RANGE 1u
+#define ERPP_ERRBIT_BOUNDS 2u
+#define ERPP_ERRBIT_TIMEOUT 4u
+
+// Packed window field of geo_c.w: bits 0-3 / 4-7 / 8-11 = -offset of the
+// first window node from the home cell on x / y / z, bits 12-16 / 17-21 /
+// 22-26 = window length on x / y / z, bit 31 = valid.
+#define ERPP_GEO_VALID 0x80000000u
+
+// Entry word: particle index in bits 0-26, periodic-shift code in 27-31
+// (code = (mx+1) + 3 (my+1) + 9 (mz+1), m the image shift per axis).
+#define ERPP_ENTRY_PBITS 27
+#define ERPP_ENTRY_PMASK ((1u << ERPP_ENTRY_PBITS) - 1u)
+#define ERPP_MAX_PARTICLES ((int64_t)ERPP_ENTRY_PMASK)
+
+// Kernel-side constants of one grid and parameter set.
+struct erpp_kparams {
+  int32_t n[3];      // nodes per axis
+  int32_t T[3];      // tile size per axis
+  int32_t nt[3];     // tiles per axis
+  int32_t ntiles;
+  int32_t hlo;       // floor(r_c / dx): lowest window offset is -hlo
+  int32_t xs;        // x slots per row = 2 hlo + 1 (>= any window length)
+  int32_t rows;      // rows per warp pass = 32 / xs
+  int32_t px, pxy;   // shared-memory pitches (floats) of one tile
+  int32_t plane;     // floats per component of one tile = pxy * T_z
+  int32_t normalize, self_removal, kahan;
+  double inv_dx[3];  // N / L
+  double L[3];
+  double cp[3];      // r_c / dx
+  double dx[3];
+  double dV;
+  double rho_f, nu, eps_R, dt, mu;
+  double gravity[3];
+  double shear_rate;
+  double raw_norm3;  // (2 pi sigma_R^2)^(-3/2)
+  double sig2;       // sigma_R^2
+  double self_s2;    // variance of the self disturbance as gathered
+  float beta[3];     // log2(e) dx_a^2 / (2 sigma_R^2)
+  float inv_rho_dV;  // 1 / (rho_f dV)
+  float self_pref;   // -(dt/rho_f) (2 pi s2)^(-3/2)
+  float self_inv_w;  // 1 / sqrt(2 s2)
+};
+
+struct erpp_ctx {
+  erpp_params params;
+  erpp_kparams kp;
+  int device;
+  int fp64;
+  int maxseg[3];          // most tiles one window can reach per axis
+  // scratch (owned)
+  int64_t cap;            // particle capacity of the per-particle arrays
+  float4* geo_t;
+  int4* geo_c;
+  float* up_acc;          // [3][cap]
+  float4* fscat;
+  double* up64;           // FP64 mode: gathered velocity [3][cap]
+  uint32_t* entries;
+  int64_t entries_cap;
+  int32_t* tile_cnt;      // [ntiles]
+  int32_t* tile_start;    // [ntiles + 1]
+  int32_t* tile_cursor;   // [ntiles]
+  uint32_t* err;          // device error word
+  double* red;            // reduction scratch
+  int red_cap;
+  // per-phase timing (erpp_profile_*)
+  int prof_on;
+  int prof_n;             // event sets recorded since the last read
+  cudaEvent_t* prof_ev;   // [kProfSets][5]
+};
+
+constexpr int kProfSets = 1024;
+
+// ---- host-side launchers (stream-ordered, no synchronisation) ----
+namespace erpp {
+
+cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bool zero_acc,
+                          cudaStream_t st);
+cudaError_t launch_gather_f32(erpp_ctx* ctx, const float* u, int64_t n, cudaStream_t st);
+cudaError_t launch_scatter_f32(erpp_ctx* ctx, float* S, cudaStream_t st);
+cudaError_t launch_finalize_up(erpp_ctx* ctx, int64_t n, const double* const x[3],
+                               double* const up[3], cudaStream_t st);
+cudaError_t launch_prep_fscat(erpp_ctx* ctx, int64_t n, const double* const D[3],
+                              cudaStream_t st);
+cudaError_t launch_advance(erpp_ctx* ctx, const erpp_particles* P, const double* const up[3],
+                           bool from_acc, bool write_fscat, int first_step, cudaStream_t st);
+cudaError_t launch_gather_f64(erpp_ctx* ctx, const double* u, int64_t n,
+                              const double* const x[3], double* const up[3], cudaStream_t st);
+cudaError_t launch_scatter_f64(erpp_ctx* ctx, int64_t n, const double* const x[3],
+                               const double* const D[3], double* S, cudaStream_t st);
+cudaError_t launch_momentum(erpp_ctx* ctx, const void* S, int64_t n, const double* const x[3],
+                            const double* const D[3], cudaStream_t st);
+cudaError_t launch_windows(erpp_ctx* ctx, int64_t n, const double* const x[3], int32_t* jlo,
+                           int32_t* jhi, cudaStream_t st);
+
+}  // namespace erpp
+
+// ---- device helpers shared by the kernels ----
+
+// Window of one coordinate, exactly as the oracle decides it: s = x * (N/L)
+// rounded once, j_lo = ceil(s - c'), j_hi = floor(s + c') with one rounding
+// each (no contraction into fused multiply-adds).
+__device__ __forceinline__ void erpp_axis_window(double x, double inv_dx, double cp, double* s,
+                                                 double* jlo, double* jhi) {
+  double sv = __dmul_rn(x, inv_dx);
+  *s = sv;
+  *jlo = ceil(__dadd_rn(sv, -cp));
+  *jhi = floor(__dadd_rn(sv, cp));
+}
+
+__device__ __forceinline__ int erpp_geo_off(uint32_t pack, int a) {
+  return -(int)((pack >> (4 * a)) & 15u);
+}
+__device__ __forceinline__ int erpp_geo_nw(uint32_t pack, int a) {
+  return (int)((pack >> (12 + 5 * a)) & 31u);
+}
+
+__device__ __forceinline__ void erpp_set_err(uint32_t* err, uint32_t bit) {
+  if (err) atomicOr(err, bit);
+}
+
+__device__ __forceinline__ int erpp_floordiv(int a, int n) {
+  int q = a / n;
+  return (a % n != 0 && ((a < 0) != (n < 0))) ? q - 1 : q;
+}

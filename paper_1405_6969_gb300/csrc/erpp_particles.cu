@@ -1,0 +1,370 @@
+// erpp_particles.cu -- per-particle kernels: self-disturbance removal, Stokes
+// drag and explicit Euler advance (Sec. 2.5), normalisation of the gathered
+// velocity, the scatter's force words, momentum sums and debug windows.
+#include <cuda_runtime.h>
+
+#include "erpp_internal.cuh"
+
+namespace {
+
+struct PartPtrs {
+  double* x[3];
+  double* v[3];
+  double* xp[3];
+  double* D[3];
+  const double* radius;
+  const double* rho_p;
+};
+
+struct UpPtrs {
+  const double* up[3];
+};
+
+__device__ __forceinline__ double min_image(double d, double L) {
+  if (d > 0.5 * L) return d - L;
+  if (d < -0.5 * L) return d + L;
+  return d;
+}
+
+__device__ __forceinline__ double wrap_coord(double x, double L) {
+  if (x < 0.0) x = x + L;
+  if (x >= L) x = x - L;
+  return x;
+}
+
+// Closed-form regularised disturbance of App. A.5 (Eq. disturbance_velo),
+// prefactor -dt/rho_f included, variance self_s2:
+//   v = pref { [e^-eta^2 - F(eta)] D - (D.rh) [e^-eta^2 - 3 F(eta)] rh },
+//   F(eta) = f(eta) / (2 eta^3), f(eta) = (sqrt(pi)/2) erf(eta) - eta e^-eta^2.
+// Below eta = 1/2 the two terms of f cancel; there F is summed from its
+// Taylor series sum_k (-1)^k eta^2k / (k! (2k+3)).
+__device__ void self_velocity_f32(const erpp_kparams& kp, const float r[3], const float D[3],
+                                  float out[3]) {
+  float rr = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  float eta = rr * kp.self_inv_w;
+  float e2 = eta * eta;
+  float e = expf(-e2);
+  float F;
+  if (eta < 0.5f) {
+    float term = 1.f, sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      sum += term / (float)(2 * k + 3);
+      term = -term * e2 / (float)(k + 1);
+    }
+    F = sum;
+  } else {
+    float f = 0.886226925452758f * erff(eta) - eta * e;
+    F = f / (2.f * eta * e2);
+  }
+  float rh[3] = {0.f, 0.f, 0.f};
+  float Ddr = 0.f;
+  if (rr > 0.f) {
+    float inv = 1.f / rr;
+    rh[0] = r[0] * inv;
+    rh[1] = r[1] * inv;
+    rh[2] = r[2] * inv;
+    Ddr = D[0] * rh[0] + D[1] * rh[1] + D[2] * rh[2];
+  }
+  float c1 = e - F, c2 = Ddr * (e - 3.f * F);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) out[a] = kp.self_pref * (c1 * D[a] - c2 * rh[a]);
+}
+
+__device__ void self_velocity_f64(const erpp_kparams& kp, const double r[3], const double D[3],
+                                  double out[3]) {
+  const double pi = 3.141592653589793238462643;
+  double s2 = kp.self_s2;
+  double pref = -(kp.dt / kp.rho_f) / pow(2.0 * pi * s2, 1.5);
+  double rr = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  double eta = rr / sqrt(2.0 * s2);
+  double F;
+  if (eta < 0.5) {
+    double e2 = eta * eta, term = 1.0, sum = 0.0;
+    for (int k = 0; k < 20; ++k) {
+      sum += term / (double)(2 * k + 3);
+      term = -term * e2 / (double)(k + 1);
+    }
+    F = sum;
+  } else {
+    double f = 0.5 * sqrt(pi) * erf(eta) - eta * exp(-eta * eta);
+    F = f / (2.0 * eta * eta * eta);
+  }
+  double e = exp(-eta * eta);
+  double rh[3] = {0.0, 0.0, 0.0};
+  double Ddr = 0.0;
+  if (rr > 0.0) {
+    for (int a = 0; a < 3; ++a) rh[a] = r[a] / rr;
+    Ddr = D[0] * rh[0] + D[1] * rh[1] + D[2] * rh[2];
+  }
+  for (int a = 0; a < 3; ++a) out[a] = pref * ((e - F) * D[a] - Ddr * (e - 3.0 * F) * rh[a]);
+}
+
+// Removal + drag + Euler (Sec. 2.5, Eqs. particle_motion, force_stokes_drag).
+// FROM_ACC: the gathered velocity comes from the tile gather's accumulator
+// (scaled by the kernel normalisation); otherwise from caller arrays.
+template <bool FROM_ACC, bool F32SELF>
+__global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, PartPtrs P,
+                                                 UpPtrs U, const float* __restrict__ up_acc,
+                                                 int64_t acc_stride,
+                                                 const float4* __restrict__ geo_t,
+                                                 float4* __restrict__ fscat, int first_step) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double up[3];
+  float norm = 0.f;
+  if (FROM_ACC) {
+    norm = geo_t[i].w;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) up[a] = (double)(up_acc[a * acc_stride + i] * norm);
+    up[0] += kp.shear_rate * P.x[1][i];
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) up[a] = U.up[a][i];
+  }
+  double x[3], v[3], D[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    x[a] = P.x[a][i];
+    v[a] = P.v[a][i];
+  }
+  double vs[3] = {0.0, 0.0, 0.0};
+  if (kp.self_removal && !first_step) {
+    double r[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      r[a] = min_image(x[a] - P.xp[a][i], kp.L[a]);
+      D[a] = P.D[a][i];
+    }
+    if (F32SELF) {
+      float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
+      float Df[3] = {(float)D[0], (float)D[1], (float)D[2]};
+      float o[3];
+      self_velocity_f32(kp, rf, Df, o);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) vs[a] = (double)o[a];
+    } else {
+      self_velocity_f64(kp, r, D, vs);
+    }
+  }
+  const double pi = 3.141592653589793238462643;
+  const double a_p = P.radius[i];
+  const double rho = P.rho_p[i];
+  const double k_drag = 6.0 * pi * kp.mu * a_p;
+  const double m_p = (4.0 / 3.0) * pi * a_p * a_p * a_p * rho;
+  const double buoy = 1.0 - kp.rho_f / rho;
+  double Dn[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double ut = up[a] - vs[a];
+    Dn[a] = k_drag * (ut - v[a]);
+    double vn = v[a] + kp.dt * (Dn[a] / m_p + buoy * kp.gravity[a]);
+    double xn = wrap_coord(x[a] + kp.dt * v[a], kp.L[a]);
+    P.v[a][i] = vn;
+    P.x[a][i] = xn;
+    P.xp[a][i] = x[a];
+    P.D[a][i] = Dn[a];
+  }
+  if (fscat) {
+    float s = -norm * kp.inv_rho_dV;
+    fscat[i] = make_float4(s * (float)Dn[0], s * (float)Dn[1], s * (float)Dn[2], 0.f);
+  }
+}
+
+__global__ void k_finalize_up(erpp_kparams kp, int64_t n, const float* __restrict__ up_acc,
+                              int64_t acc_stride, const float4* __restrict__ geo_t,
+                              const double* __restrict__ y, double* up0, double* up1,
+                              double* up2) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float norm = geo_t[i].w;
+  up0[i] = (double)(up_acc[i] * norm) + kp.shear_rate * y[i];
+  up1[i] = (double)(up_acc[acc_stride + i] * norm);
+  up2[i] = (double)(up_acc[2 * acc_stride + i] * norm);
+}
+
+__global__ void k_prep_fscat(erpp_kparams kp, int64_t n, const double* __restrict__ D0,
+                             const double* __restrict__ D1, const double* __restrict__ D2,
+                             const float4* __restrict__ geo_t, float4* __restrict__ fscat) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = -geo_t[i].w * kp.inv_rho_dV;
+  fscat[i] = make_float4(s * (float)D0[i], s * (float)D1[i], s * (float)D2[i], 0.f);
+}
+
+__global__ void k_windows(erpp_kparams kp, int64_t n, const double* __restrict__ x0,
+                          const double* __restrict__ x1, const double* __restrict__ x2,
+                          int32_t* jlo, int32_t* jhi) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* xs[3] = {x0, x1, x2};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double s, lo, hi;
+    erpp_axis_window(xs[a][i], kp.inv_dx[a], kp.cp[a], &s, &lo, &hi);
+    jlo[a * n + i] = (int32_t)lo;
+    jhi[a * n + i] = (int32_t)hi;
+  }
+}
+
+// ---------------------------------------------------------------- momentum
+constexpr int kRedBlocks = 304;
+
+template <typename T>
+__global__ void k_grid_sum(const T* __restrict__ S, size_t nn, double* __restrict__ part) {
+  __shared__ double sh[3][8];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j < nn;
+       j += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] += (double)S[c * nn + j];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[c][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
+    part[threadIdx.x * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+__device__ double axis_mass(const erpp_kparams& kp, int a, double x) {
+  double s, lo, hi;
+  erpp_axis_window(x, kp.inv_dx[a], kp.cp[a], &s, &lo, &hi);
+  const double raw1 = 1.0 / sqrt(2.0 * 3.141592653589793238462643 * kp.sig2);
+  double sum = 0.0;
+  for (double j = lo; j <= hi; j += 1.0) {
+    double d = (j - s) * kp.dx[a];
+    sum += raw1 * exp(-(d * d) / (2.0 * kp.sig2));
+  }
+  return kp.dx[a] * sum;
+}
+
+__global__ void k_part_sum(erpp_kparams kp, int64_t n, const double* __restrict__ x0,
+                           const double* __restrict__ x1, const double* __restrict__ x2,
+                           const double* __restrict__ D0, const double* __restrict__ D1,
+                           const double* __restrict__ D2, double* __restrict__ part) {
+  __shared__ double sh[3][8];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double M = 1.0;
+    if (!kp.normalize) M = axis_mass(kp, 0, x0[i]) * axis_mass(kp, 1, x1[i]) * axis_mass(kp, 2, x2[i]);
+    acc[0] += M * D0[i];
+    acc[1] += M * D1[i];
+    acc[2] += M * D2[i];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[c][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
+    part[threadIdx.x * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+// out[0..2] = dV * grid sums, out[3..5] = -(1/rho_f) * particle sums
+__global__ void k_momentum_final(erpp_kparams kp, const double* __restrict__ gpart,
+                                 const double* __restrict__ ppart, int nb, double* out) {
+  int c = threadIdx.x;
+  if (c >= 6) return;
+  const double* src = c < 3 ? gpart + c * nb : ppart + (c - 3) * nb;
+  double v = 0.0;
+  for (int k = 0; k < nb; ++k) v += src[k];
+  out[c] = c < 3 ? kp.dV * v : -v / kp.rho_f;
+}
+
+}  // namespace
+
+namespace erpp {
+
+static PartPtrs part_ptrs(const erpp_particles* P) {
+  PartPtrs q;
+  for (int a = 0; a < 3; ++a) {
+    q.x[a] = P->x[a];
+    q.v[a] = P->v[a];
+    q.xp[a] = P->x_prev[a];
+    q.D[a] = P->D[a];
+  }
+  q.radius = P->radius;
+  q.rho_p = P->rho_p;
+  return q;
+}
+
+cudaError_t launch_advance(erpp_ctx* ctx, const erpp_particles* P, const double* const up[3],
+                           bool from_acc, bool write_fscat, int first_step, cudaStream_t st) {
+  const int64_t n = P->n;
+  if (n <= 0) return cudaSuccess;
+  PartPtrs q = part_ptrs(P);
+  UpPtrs U;
+  for (int a = 0; a < 3; ++a) U.up[a] = up ? up[a] : nullptr;
+  int blocks = (int)((n + 255) / 256);
+  float4* fs = write_fscat ? ctx->fscat : nullptr;
+  const bool f32 = !ctx->fp64;
+  if (from_acc) {
+    k_advance<true, true><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, ctx->up_acc, ctx->cap,
+                                                  ctx->geo_t, fs, first_step);
+  } else if (f32) {
+    k_advance<false, true><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, nullptr, 0, nullptr,
+                                                   nullptr, first_step);
+  } else {
+    k_advance<false, false><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, nullptr, 0, nullptr,
+                                                    nullptr, first_step);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_up(erpp_ctx* ctx, int64_t n, const double* const x[3],
+                               double* const up[3], cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (int)((n + 255) / 256);
+  k_finalize_up<<<blocks, 256, 0, st>>>(ctx->kp, n, ctx->up_acc, ctx->cap, ctx->geo_t, x[1],
+                                        up[0], up[1], up[2]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_fscat(erpp_ctx* ctx, int64_t n, const double* const D[3],
+                              cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (int)((n + 255) / 256);
+  k_prep_fscat<<<blocks, 256, 0, st>>>(ctx->kp, n, D[0], D[1], D[2], ctx->geo_t, ctx->fscat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_windows(erpp_ctx* ctx, int64_t n, const double* const x[3], int32_t* jlo,
+                           int32_t* jhi, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (int)((n + 255) / 256);
+  k_windows<<<blocks, 256, 0, st>>>(ctx->kp, n, x[0], x[1], x[2], jlo, jhi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_momentum(erpp_ctx* ctx, const void* S, int64_t n, const double* const x[3],
+                            const double* const D[3], cudaStream_t st) {
+  const erpp_kparams& kp = ctx->kp;
+  size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
+  double* gpart = ctx->red;
+  double* ppart = ctx->red + 3 * kRedBlocks;
+  double* out = ctx->red + 6 * kRedBlocks;
+  if (ctx->fp64)
+    k_grid_sum<double><<<kRedBlocks, 256, 0, st>>>((const double*)S, nn, gpart);
+  else
+    k_grid_sum<float><<<kRedBlocks, 256, 0, st>>>((const float*)S, nn, gpart);
+  k_part_sum<<<kRedBlocks, 256, 0, st>>>(kp, n, x[0], x[1], x[2], D[0], D[1], D[2], ppart);
+  k_momentum_final<<<1, 32, 0, st>>>(kp, gpart, ppart, kRedBlocks, out);
+  return cudaGetLastError();
+}
+
+}  // namespace erpp

@@ -1,0 +1,192 @@
+"""PyTorch binding of the ERPP C ABI.
+
+PyTorch supplies device memory and the current CUDA stream; every step of
+the coupling runs in the CUDA kernels of ``liberpp.so``.  Tensors are
+passed by data pointer: particle vectors are ``[3, n]`` float64 CUDA tensors
+(component-major, contiguous), grid fields ``[3, nz, ny, nx]`` float32
+(``precision="fp32"``) or float64 (``precision="fp64"``).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import torch
+
+from . import _lib
+
+
+def _dptr(t):
+    return ctypes.cast(ctypes.c_void_p(t.data_ptr()), _lib._dp)
+
+
+def _vec3(t):
+    """[3, n] float64 CUDA tensor -> double*[3]."""
+    _require(t, torch.float64, 2)
+    assert t.shape[0] == 3
+    n = t.shape[1]
+    base = t.data_ptr()
+    return _lib._dp3(*[ctypes.cast(ctypes.c_void_p(base + 8 * n * c), _lib._dp)
+                       for c in range(3)])
+
+
+def _require(t, dtype, ndim):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != dtype or t.dim() != ndim or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} tensor of rank {ndim}, "
+                        f"got {t.dtype} {tuple(t.shape)}")
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclasses.dataclass
+class ParticleState:
+    """Particle arrays on the device: x, v, x_prev, D are [3, n] float64;
+    radius and rho_p are [n] float64."""
+
+    x: torch.Tensor
+    v: torch.Tensor
+    x_prev: torch.Tensor
+    D: torch.Tensor
+    radius: torch.Tensor
+    rho_p: torch.Tensor
+
+    @property
+    def n(self):
+        return self.x.shape[1]
+
+    @staticmethod
+    def from_numpy(st, device="cuda"):
+        f = lambda a: torch.as_tensor(a, dtype=torch.float64).contiguous().to(device)  # noqa: E731
+        return ParticleState(f(st.x), f(st.v), f(st.x_prev), f(st.D), f(st.radius),
+                             f(st.rho_p))
+
+    def to_c(self):
+        P = _lib.Particles()
+        P.n = self.n
+        P.x, P.v = _vec3(self.x), _vec3(self.v)
+        P.x_prev, P.D = _vec3(self.x_prev), _vec3(self.D)
+        _require(self.radius, torch.float64, 1)
+        _require(self.rho_p, torch.float64, 1)
+        P.radius, P.rho_p = _dptr(self.radius), _dptr(self.rho_p)
+        return P
+
+
+class Context:
+    """One ERPP context (grid, parameters, scratch) on the current device.
+
+    params: dict with n=(nx, ny, nz), L=(Lx, Ly, Lz), nu, rho_f, eps_R,
+    cutoff, dt, gravity=(gx, gy, gz), shear_rate.
+    """
+
+    def __init__(self, params, precision="fp32", normalize=True, self_removal=True,
+                 kahan=False):
+        self.lib = _lib.load()
+        p = _lib.Params()
+        p.nx, p.ny, p.nz = (int(v) for v in params["n"])
+        p.Lx, p.Ly, p.Lz = (float(v) for v in params["L"])
+        p.nu, p.rho_f = float(params["nu"]), float(params.get("rho_f", 1.0))
+        p.eps_R, p.cutoff = float(params["eps_R"]), float(params["cutoff"])
+        p.dt = float(params["dt"])
+        p.gravity = (ctypes.c_double * 3)(*[float(g) for g in params.get("gravity", (0, 0, 0))])
+        p.shear_rate = float(params.get("shear_rate", 0.0))
+        flags = {"fp32": _lib.FP32, "fp64": _lib.FP64}[precision]
+        if normalize:
+            flags |= _lib.NORMALIZE
+        if self_removal:
+            flags |= _lib.SELF_REMOVAL
+        if kahan:
+            flags |= _lib.KAHAN
+        p.flags = flags
+        self.params = dict(params)
+        self.precision = precision
+        self.grid_dtype = torch.float32 if precision == "fp32" else torch.float64
+        self.shape = (3, p.nz, p.ny, p.nx)
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.erpp_init(ctypes.byref(p), ctypes.byref(h)), "erpp_init")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.erpp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _grid(self, g):
+        _require(g, self.grid_dtype, 4)
+        if tuple(g.shape) != self.shape:
+            raise ValueError(f"grid shape {tuple(g.shape)} != {self.shape}")
+        return ctypes.c_void_p(g.data_ptr())
+
+    def new_grid(self):
+        return torch.empty(self.shape, dtype=self.grid_dtype, device="cuda")
+
+    def interpolate(self, u, x, out=None, stream=None):
+        n = x.shape[1]
+        out = torch.empty((3, n), dtype=torch.float64, device=x.device) if out is None else out
+        _lib.check(self.lib.erpp_interpolate(self._h, self._grid(u), n, _vec3(x), _vec3(out),
+                                             _stream(stream)), "erpp_interpolate")
+        return out
+
+    def particle_advance(self, up, state, first_step=False, stream=None):
+        P = state.to_c()
+        _lib.check(self.lib.erpp_particle_advance(self._h, _vec3(up), ctypes.byref(P),
+                                                  int(bool(first_step)), _stream(stream)),
+                   "erpp_particle_advance")
+        return state
+
+    def scatter_source(self, x, D, S=None, stream=None):
+        S = self.new_grid() if S is None else S
+        _lib.check(self.lib.erpp_scatter_source(self._h, x.shape[1], _vec3(x), _vec3(D),
+                                                self._grid(S), _stream(stream)),
+                   "erpp_scatter_source")
+        return S
+
+    def step(self, u, state, S=None, first_step=False, stream=None):
+        S = self.new_grid() if S is None else S
+        P = state.to_c()
+        _lib.check(self.lib.erpp_step(self._h, self._grid(u), ctypes.byref(P), self._grid(S),
+                                      int(bool(first_step)), _stream(stream)), "erpp_step")
+        return S
+
+    def momentum(self, S, x, D, stream=None):
+        out = (ctypes.c_double * 6)()
+        _lib.check(self.lib.erpp_momentum(self._h, self._grid(S), x.shape[1], _vec3(x),
+                                          _vec3(D), ctypes.cast(out, _lib._dp),
+                                          _stream(stream)), "erpp_momentum")
+        return list(out[:3]), list(out[3:])
+
+    def check(self, stream=None):
+        _lib.check(self.lib.erpp_check(self._h, _stream(stream)), "erpp_check")
+
+    def profile_enable(self, enable=True):
+        _lib.check(self.lib.erpp_profile_enable(self._h, int(bool(enable))),
+                   "erpp_profile_enable")
+
+    def profile_read(self):
+        """(milliseconds per phase [bin, gather, advance, scatter], steps)."""
+        ms = (ctypes.c_double * 4)()
+        n = ctypes.c_int64()
+        _lib.check(self.lib.erpp_profile_read(self._h, ctypes.cast(ms, _lib._dp),
+                                              ctypes.byref(n)), "erpp_profile_read")
+        return list(ms), int(n.value)
+
+    def debug_windows(self, x, stream=None):
+        n = x.shape[1]
+        lo = torch.empty((3, n), dtype=torch.int32, device=x.device)
+        hi = torch.empty((3, n), dtype=torch.int32, device=x.device)
+        _lib.check(self.lib.erpp_debug_windows(self._h, n, _vec3(x),
+                                               ctypes.c_void_p(lo.data_ptr()),
+                                               ctypes.c_void_p(hi.data_ptr()),
+                                               _stream(stream)), "erpp_debug_windows")
+        return lo, hi

@@ -1,0 +1,261 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (relative L2 over the whole output): 1e-5 for the FP32 kernels,
+1e-12 for the FP64 kernels; stencil windows bit-exact.  Every input comes
+from the seeded generators in ``erpp_inputs``; every expected value from
+``oracle``.
+"""
+
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import erpp_inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "fp64": 1e-12}
+
+
+@pytest.fixture(scope="module")
+def erpp(oracle_lib):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1405_6969_gb300 as pkg
+    return pkg
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def cuda(a, dtype=None):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64).cuda()
+
+
+def grid_t(g, precision):
+    import torch
+    return cuda(g, torch.float32 if precision == "fp32" else torch.float64)
+
+
+def rep(w, **kw):
+    return dataclasses.replace(w, **kw)
+
+
+# Grids chosen to span several tiles (32 x 16 x 8) with ragged last tiles,
+# and small grids where one tile covers a whole periodic axis.
+CASES = [
+    ("cube32_uniform", rep(I.CFG_SMALL), 1000),
+    ("ragged_72x40x20_clustered", rep(I.CFG_CLUSTERED, n=(72, 40, 20), n_particles=3000,
+                                       cluster_std=0.3), 3000),
+    ("small_16x12x10_sigma1.5", rep(I.CFG_CLUSTERED, n=(16, 12, 10), L=(2 * math.pi, 5.0, 4.0),
+                                     n_particles=500, cluster_std=0.5, kmax=3.0), 500),
+    ("aniso_96x33x17", rep(I.CFG_SMALL, n=(96, 33, 17), L=(2 * math.pi, 2.0, 1.0)), 2000),
+]
+
+
+def _setup(w, npart):
+    grid, field = I.make_grid(w)
+    st = I.make_particles(w, field if npart <= 3000 else None, n_particles=npart)
+    return grid, st
+
+
+@pytest.mark.parametrize("name,w,npart", CASES, ids=[c[0] for c in CASES])
+def test_windows_bit_exact(erpp, oracle_lib, name, w, npart):
+    """Integer stencil membership is identical to the oracle's."""
+    p = w.params()
+    _, st = _setup(w, npart)
+    # add particles on nodes, on cell faces and next to the box edges
+    L = np.array(w.L)[:, None]
+    n = np.array(w.n)[:, None]
+    special = np.concatenate([
+        (np.arange(12) % n) * (L / n),
+        (np.arange(12) % n + 0.5) * (L / n),
+        np.nextafter(L, 0) * np.ones((3, 4)),
+        np.zeros((3, 2)),
+    ], axis=1)
+    x = np.concatenate([st.x, special], axis=1)
+    ctx = erpp.Context(p, precision="fp32")
+    lo, hi = ctx.debug_windows(cuda(x))
+    rlo, rhi = oracle_lib.windows(p, x)
+    np.testing.assert_array_equal(lo.cpu().numpy(), rlo)
+    np.testing.assert_array_equal(hi.cpu().numpy(), rhi)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("name,w,npart", CASES, ids=[c[0] for c in CASES])
+def test_scatter_source(erpp, oracle_lib, precision, name, w, npart):
+    p = w.params()
+    _, st = _setup(w, npart)
+    D = I.make_forces(npart, 1.0, seed=7)
+    ctx = erpp.Context(p, precision=precision)
+    S = ctx.scatter_source(cuda(st.x), cuda(D))
+    ctx.check()
+    ref = oracle_lib.scatter(p, st.x, D)
+    assert rel(S.cpu().numpy(), ref) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("name,w,npart", CASES, ids=[c[0] for c in CASES])
+def test_interpolate(erpp, oracle_lib, precision, name, w, npart):
+    p = w.params()
+    grid, st = _setup(w, npart)
+    ctx = erpp.Context(p, precision=precision)
+    up = ctx.interpolate(grid_t(grid, precision), cuda(st.x))
+    ctx.check()
+    ref = oracle_lib.gather(p, st.x, grid)
+    assert rel(up.cpu().numpy(), ref) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("self_removal", [True, False])
+@pytest.mark.parametrize("name,w,npart", CASES, ids=[c[0] for c in CASES])
+def test_step(erpp, oracle_lib, precision, self_removal, name, w, npart):
+    p = w.params(gravity=(0.0, -9.81, 0.0))
+    grid, st = _setup(w, npart)
+    ctx = erpp.Context(p, precision=precision, self_removal=self_removal)
+    ps = erpp.ParticleState.from_numpy(st)
+    S = ctx.step(grid_t(grid, precision), ps, first_step=False)
+    ctx.check()
+    ref = st.copy()
+    S_ref = oracle_lib.step(dict(p, self_removal=self_removal), grid, ref, first_step=False)
+    tol = TOL[precision]
+    assert rel(S.cpu().numpy(), S_ref) < tol
+    assert rel(ps.D.cpu().numpy(), ref.D) < tol
+    assert rel(ps.v.cpu().numpy(), ref.v) < tol
+    np.testing.assert_array_equal(ps.x_prev.cpu().numpy(), st.x)
+    # positions: FP64 integration of FP64 (or FP32-accurate) velocities
+    dxp = np.abs(ps.x.cpu().numpy() - ref.x)
+    dxp = np.minimum(dxp, np.array(w.L)[:, None] - dxp)
+    assert dxp.max() < (1e-15 if precision == "fp64" else 1e-12) * 10 * max(w.L)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_particle_advance_standalone(erpp, oracle_lib, precision):
+    w = I.CFG_SMALL
+    p = w.params(gravity=(0.0, 0.0, -1.0))
+    grid, st = _setup(w, 1000)
+    up = oracle_lib.gather(p, st.x, grid)
+    ctx = erpp.Context(p, precision=precision)
+    ps = erpp.ParticleState.from_numpy(st)
+    ctx.particle_advance(cuda(up), ps, first_step=False)
+    ref = st.copy()
+    oracle_lib.advance(p, up, ref, first_step=False)
+    tol = 1e-6 if precision == "fp32" else 1e-13
+    assert rel(ps.D.cpu().numpy(), ref.D) < tol
+    assert rel(ps.v.cpu().numpy(), ref.v) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_clustered_ten_steps(erpp, oracle_lib, precision):
+    """The clustered workload (50 Gaussian clusters, std 0.05, mean shear
+    S = 1, sigma_R = 1.5 dx) on a reduced grid: ten coupled steps with the
+    fluid frozen, FP32 and FP64 against the FP64 oracle."""
+    w = rep(I.CFG_CLUSTERED, n=(64, 64, 64), n_particles=20000)
+    p = w.params()
+    grid, st = _setup(w, 20000)
+    ctx = erpp.Context(p, precision=precision)
+    ps = erpp.ParticleState.from_numpy(st)
+    u = grid_t(grid, precision)
+    ref = st.copy()
+    for k in range(10):
+        S = ctx.step(u, ps, first_step=(k == 0))
+        S_ref = oracle_lib.step(p, grid, ref, first_step=(k == 0))
+    ctx.check()
+    tol = TOL[precision]
+    assert rel(S.cpu().numpy(), S_ref) < tol
+    assert rel(ps.D.cpu().numpy(), ref.D) < tol
+    assert rel(ps.v.cpu().numpy(), ref.v) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_momentum_conservation(erpp, oracle_lib, precision):
+    w = rep(I.CFG_CLUSTERED, n=(72, 40, 20))
+    p = w.params()
+    _, st = _setup(w, 3000)
+    ctx = erpp.Context(p, precision=precision)
+    x, D = cuda(st.x), cuda(st.D)
+    S = ctx.scatter_source(x, D)
+    Pg, Pp = ctx.momentum(S, x, D)
+    rg, rp = oracle_lib.momentum(p, st.x, st.D, oracle_lib.scatter(p, st.x, st.D))
+    scale = np.abs(rp).max()
+    np.testing.assert_allclose(Pp, rp, rtol=1e-12, atol=1e-13 * scale)
+    np.testing.assert_allclose(Pg, rg, atol=(1e-6 if precision == "fp32" else 1e-12) * scale)
+
+
+def test_kahan_scatter(erpp, oracle_lib):
+    """Compensated FP32 accumulation on a dense cluster (thousands of
+    contributions per node) is closer to the FP64 oracle than plain FP32."""
+    w = rep(I.CFG_CLUSTERED, n=(48, 48, 48), n_clusters=2, cluster_std=0.02)
+    p = w.params()
+    _, st = _setup(w, 20000)
+    D = I.make_forces(20000, 1.0, seed=3) + 0.5
+    ref = oracle_lib.scatter(p, st.x, D)
+    errs = {}
+    for kahan in (False, True):
+        ctx = erpp.Context(p, precision="fp32", kahan=kahan)
+        S = ctx.scatter_source(cuda(st.x), cuda(D))
+        errs[kahan] = rel(S.cpu().numpy(), ref)
+    assert errs[True] < TOL["fp32"] and errs[False] < TOL["fp32"]
+    assert errs[True] <= errs[False]
+
+
+def test_permutation_invariance(erpp):
+    w = rep(I.CFG_CLUSTERED, n=(72, 40, 20))
+    p = w.params()
+    _, st = _setup(w, 3000)
+    perm = np.random.default_rng(1).permutation(3000)
+    ctx = erpp.Context(p, precision="fp32")
+    S1 = ctx.scatter_source(cuda(st.x), cuda(st.D)).cpu().numpy()
+    S2 = ctx.scatter_source(cuda(st.x[:, perm]), cuda(st.D[:, perm])).cpu().numpy()
+    assert rel(S2, S1) < 1e-6
+
+
+def test_edge_cases(erpp, oracle_lib):
+    import torch
+    w = rep(I.CFG_SMALL, n=(40, 24, 20))
+    p = w.params()
+    ctx = erpp.Context(p, precision="fp32")
+    # no particles: the source is zero everywhere (fully overwritten)
+    S = ctx.new_grid().fill_(7.0)
+    ctx.scatter_source(cuda(np.zeros((3, 0))), cuda(np.zeros((3, 0))), S=S)
+    assert float(S.abs().max()) == 0.0
+    # one particle at the origin and one just below L (windows wrap)
+    L = np.array(w.L)
+    x = np.stack([np.zeros(3), np.nextafter(L, 0)], axis=1)
+    D = np.array([[1.0, -2.0], [0.5, 0.25], [-1.0, 3.0]])
+    S = ctx.scatter_source(cuda(x), cuda(D))
+    assert rel(S.cpu().numpy(), oracle_lib.scatter(p, x, D)) < TOL["fp32"]
+    # all particles in one cell (heavy atomic contention)
+    xc = np.full((3, 4000), 1.0) + 1e-3 * np.random.default_rng(0).random((3, 4000))
+    Dc = np.random.default_rng(1).standard_normal((3, 4000))
+    S = ctx.scatter_source(cuda(xc), cuda(Dc))
+    assert rel(S.cpu().numpy(), oracle_lib.scatter(p, xc, Dc)) < TOL["fp32"]
+    # invalid positions are reported, never trapped
+    bad = x.copy()
+    bad[0, 0] = float("nan")
+    bad[1, 1] = L[1]
+    ctx.scatter_source(cuda(bad), cuda(D))
+    with pytest.raises(erpp.ErppError) as ei:
+        ctx.check()
+    assert ei.value.status == 4  # ERPP_ERANGE
+    ctx.check()  # the error word was cleared
+    torch.cuda.synchronize()
+
+
+def test_invalid_arguments(erpp):
+    p = I.CFG_SMALL.params()
+    with pytest.raises(erpp.ErppError):
+        erpp.Context(dict(p, cutoff=40.0))  # 2 r_c >= L
+    with pytest.raises(erpp.ErppError):
+        erpp.Context(dict(p, nu=-1.0))
+    with pytest.raises(erpp.ErppError):
+        erpp.Context(p, precision="fp64", kahan=True)

@@ -447,3 +447,16 @@ def test_gather_adjoint_finite_differences(oracle_lib):
     probe = rng.standard_normal(grid.shape)
     lin = np.sum(oracle_lib.gather(dict(p, shear_rate=0.0), x, probe) * G)
     assert abs(np.sum(du * probe) - lin) < 1e-12 * abs(lin) + 1e-14
+
+
+def test_scatter_nodes_matches_full_scatter(oracle_lib):
+    """The node-sampled source is the full source read at those nodes."""
+    w = dataclass_replace(I.CFG_CLUSTERED, n=(20, 18, 16))
+    p = w.params()
+    st = I.make_particles(w, None, n_particles=500)
+    S = oracle_lib.scatter(p, st.x, st.D)
+    rng = np.random.default_rng(0)
+    nodes = np.stack([rng.integers(0, n, 64) for n in w.n])
+    sub = oracle_lib.scatter_nodes(p, st.x, st.D, nodes)
+    np.testing.assert_allclose(sub, S[:, nodes[2], nodes[1], nodes[0]], rtol=1e-13,
+                               atol=1e-13 * np.abs(S).max())
