@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kahan", action="store_true")
+    ap.add_argument("--workload", default="shear", choices=["shear", "cube256"],
+                    help="shear: 512x256x256 box (the benchmark); cube256: 256^3, 1M "
+                         "particles (profiling case)")
     return ap.parse_args()
 
 
@@ -219,7 +222,7 @@ def main():
     from paper_1405_6969_gb300 import build as libbuild
     libbuild.build()
 
-    w = WORKLOAD
+    w = WORKLOAD if args.workload == "shear" else I.CFG_CUBE256
     seed = rank
     grid64, _ = I.make_grid(w, seed=w.field_seed + seed)
     st = I.make_particles(w, None, seed=w.particle_seed + seed)

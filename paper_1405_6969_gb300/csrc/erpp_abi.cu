@@ -154,10 +154,15 @@ const char* erpp_status_string(erpp_status s) {
   return "unknown status";
 }
 
-erpp_status erpp_init(const erpp_params* p, erpp_ctx** out) {
-  if (!out) return ERPP_EINVAL;
-  *out = nullptr;
-  if (!p) return ERPP_EINVAL;
+}  // extern "C"
+
+namespace erpp {
+
+// Validates the parameters and fills the context's derived constants (kernel
+// parameters, tile geometry, piece bounds).  Host only: no CUDA call, no
+// allocation.
+erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
+  if (!p || !c) return ERPP_EINVAL;
   const int n[3] = {p->nx, p->ny, p->nz};
   const double L[3] = {p->Lx, p->Ly, p->Lz};
   for (int a = 0; a < 3; ++a)
@@ -235,13 +240,31 @@ erpp_status erpp_init(const erpp_params* p, erpp_ctx** out) {
   kp.pxy = choose_pxy(kp.T[1], kp.px, kp.xs, kp.rows, ny_w);
   kp.plane = kp.pxy * kp.T[2];
   if ((size_t)kp.plane * 6 * sizeof(float) > 227 * 1024) return ERPP_EINVAL;
+  kp.kahan_alloc = 1;
 
-  erpp_ctx* c = (erpp_ctx*)calloc(1, sizeof(erpp_ctx));
-  if (!c) return ERPP_ENOMEM;
   c->params = *p;
   c->kp = kp;
   c->fp64 = prec == ERPP_FP64;
   for (int a = 0; a < 3; ++a) c->maxseg[a] = max_pieces(n[a], kp.T[a], kp.hlo, kp.xs);
+  return ERPP_OK;
+}
+
+}  // namespace erpp
+
+extern "C" {
+
+erpp_status erpp_init(const erpp_params* p, erpp_ctx** out) {
+  if (!out) return ERPP_EINVAL;
+  *out = nullptr;
+  if (!p) return ERPP_EINVAL;
+  erpp_ctx* c = (erpp_ctx*)calloc(1, sizeof(erpp_ctx));
+  if (!c) return ERPP_ENOMEM;
+  erpp_status s0 = erpp::derive_ctx(p, c);
+  if (s0 != ERPP_OK) {
+    free(c);
+    return s0;
+  }
+  const erpp_kparams& kp = c->kp;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(uint32_t));

@@ -93,30 +93,13 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
     geo_c[i] = make_int4(0, 0, 0, 0);
     return;
   }
-  float norm;
-  if (kp.normalize) {
-    float prod = 1.f;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      float sum = 0.f;
-      float d0 = (float)off[a] - t[a];
-      for (int k = 0; k < nw[a]; ++k) {
-        float d = d0 + (float)k;
-        sum += exp2f(-kp.beta[a] * d * d);
-      }
-      prod *= sum;
-    }
-    norm = 1.f / prod;
-  } else {
-    norm = (float)(kp.dV * kp.raw_norm3);
-  }
   uint32_t pack = ERPP_GEO_VALID;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     pack |= (uint32_t)(-off[a]) << (4 * a);
     pack |= (uint32_t)nw[a] << (12 + 5 * a);
   }
-  geo_t[i] = make_float4(t[0], t[1], t[2], norm);
+  geo_t[i] = make_float4(t[0], t[1], t[2], 0.f);
   geo_c[i] = make_int4(c[0], c[1], c[2], (int)pack);
   for_each_piece(kp, jlo, nw, [&](int tile, uint32_t) { atomicAdd(&tile_cnt[tile], 1); });
 }

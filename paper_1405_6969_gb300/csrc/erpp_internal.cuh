@@ -45,6 +45,7 @@ struct erpp_kparams {
   int32_t px, pxy;   // shared-memory pitches (floats) of one tile
   int32_t plane;     // floats per component of one tile = pxy * T_z
   int32_t normalize, self_removal, kahan;
+  int32_t kahan_alloc;  // scatter shared memory holds a compensation plane set
   double inv_dx[3];  // N / L
   double L[3];
   double cp[3];      // r_c / dx
@@ -94,6 +95,7 @@ constexpr int kProfSets = 1024;
 // ---- host-side launchers (stream-ordered, no synchronisation) ----
 namespace erpp {
 
+erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c);
 cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bool zero_acc,
                           cudaStream_t st);
 cudaError_t launch_gather_f32(erpp_ctx* ctx, const float* u, int64_t n, cudaStream_t st);
@@ -137,6 +139,30 @@ __device__ __forceinline__ int erpp_geo_nw(uint32_t pack, int a) {
 
 __device__ __forceinline__ void erpp_set_err(uint32_t* err, uint32_t bit) {
   if (err) atomicOr(err, bit);
+}
+
+// Kernel normalisation of one particle from its geometry record: the gather
+// returns norm * sum_j e_x e_y e_z u_j with e_a = 2^(-beta_a d_a^2) (d in grid
+// units), so norm = 1 / (sum_x e_x sum_y e_y sum_z e_z) for unit discrete mass
+// per axis, or dV (2 pi sigma_R^2)^(-3/2) for the raw Gaussian.
+__device__ __forceinline__ float erpp_norm(const erpp_kparams& kp, float4 gt, int4 gc) {
+  if (!kp.normalize) return (float)(kp.dV * kp.raw_norm3);
+  const uint32_t pack = (uint32_t)gc.w;
+  if (!(pack & ERPP_GEO_VALID)) return 0.f;
+  const float t[3] = {gt.x, gt.y, gt.z};
+  float prod = 1.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int nw = (int)((pack >> (12 + 5 * a)) & 31u);
+    const float d0 = -(float)((pack >> (4 * a)) & 15u) - t[a];
+    float sum = 0.f;
+    for (int k = 0; k < nw; ++k) {
+      const float d = d0 + (float)k;
+      sum += exp2f(-kp.beta[a] * d * d);
+    }
+    prod *= sum;
+  }
+  return 1.f / prod;
 }
 
 __device__ __forceinline__ int erpp_floordiv(int a, int n) {

@@ -102,41 +102,45 @@ __device__ void self_velocity_f64(const erpp_kparams& kp, const double r[3], con
 
 // Removal + drag + Euler (Sec. 2.5, Eqs. particle_motion, force_stokes_drag).
 // FROM_ACC: the gathered velocity comes from the tile gather's accumulator
-// (scaled by the kernel normalisation); otherwise from caller arrays.
-template <bool FROM_ACC, bool F32SELF>
+// (scaled here by the kernel normalisation); otherwise from caller arrays.
+// F32: the drag and the velocity increment are formed in FP32 from the FP64
+// slip (the increment is a small correction to the FP64 velocity); the
+// velocity and position updates themselves stay in FP64.
+template <bool FROM_ACC, bool F32>
 __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, PartPtrs P,
                                                  UpPtrs U, const float* __restrict__ up_acc,
                                                  int64_t acc_stride,
                                                  const float4* __restrict__ geo_t,
+                                                 const int4* __restrict__ geo_c,
                                                  float4* __restrict__ fscat, int first_step) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double up[3];
-  float norm = 0.f;
-  if (FROM_ACC) {
-    norm = geo_t[i].w;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) up[a] = (double)(up_acc[a * acc_stride + i] * norm);
-    up[0] += kp.shear_rate * P.x[1][i];
-  } else {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) up[a] = U.up[a][i];
-  }
-  double x[3], v[3], D[3];
+  double x[3], v[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     x[a] = P.x[a][i];
     v[a] = P.v[a][i];
   }
+  double up[3];
+  float norm = 0.f;
+  if (FROM_ACC) {
+    norm = erpp_norm(kp, geo_t[i], geo_c[i]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) up[a] = (double)(up_acc[a * acc_stride + i] * norm);
+    up[0] += kp.shear_rate * x[1];
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) up[a] = U.up[a][i];
+  }
   double vs[3] = {0.0, 0.0, 0.0};
   if (kp.self_removal && !first_step) {
-    double r[3];
+    double r[3], D[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       r[a] = min_image(x[a] - P.xp[a][i], kp.L[a]);
       D[a] = P.D[a][i];
     }
-    if (F32SELF) {
+    if (F32) {
       float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
       float Df[3] = {(float)D[0], (float)D[1], (float)D[2]};
       float o[3];
@@ -150,34 +154,52 @@ __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, Par
   const double pi = 3.141592653589793238462643;
   const double a_p = P.radius[i];
   const double rho = P.rho_p[i];
-  const double k_drag = 6.0 * pi * kp.mu * a_p;
-  const double m_p = (4.0 / 3.0) * pi * a_p * a_p * a_p * rho;
-  const double buoy = 1.0 - kp.rho_f / rho;
   double Dn[3];
+  if (F32) {
+    const float af = (float)a_p, rf = (float)rho;
+    const float k_drag = (float)(6.0 * pi * kp.mu) * af;
+    const float inv_m = 1.f / ((float)(4.0 / 3.0 * pi) * af * af * af * rf);
+    const float buoy = 1.f - (float)kp.rho_f / rf;
+    const float dtf = (float)kp.dt;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    double ut = up[a] - vs[a];
-    Dn[a] = k_drag * (ut - v[a]);
-    double vn = v[a] + kp.dt * (Dn[a] / m_p + buoy * kp.gravity[a]);
-    double xn = wrap_coord(x[a] + kp.dt * v[a], kp.L[a]);
-    P.v[a][i] = vn;
-    P.x[a][i] = xn;
-    P.xp[a][i] = x[a];
-    P.D[a][i] = Dn[a];
+    for (int a = 0; a < 3; ++a) {
+      const float slip = (float)((up[a] - vs[a]) - v[a]);
+      const float Df = k_drag * slip;
+      const float dv = dtf * (Df * inv_m + buoy * (float)kp.gravity[a]);
+      Dn[a] = (double)Df;
+      P.v[a][i] = v[a] + (double)dv;
+      P.x[a][i] = wrap_coord(x[a] + kp.dt * v[a], kp.L[a]);
+      P.xp[a][i] = x[a];
+      P.D[a][i] = Dn[a];
+    }
+  } else {
+    const double k_drag = 6.0 * pi * kp.mu * a_p;
+    const double m_p = (4.0 / 3.0) * pi * a_p * a_p * a_p * rho;
+    const double buoy = 1.0 - kp.rho_f / rho;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double ut = up[a] - vs[a];
+      Dn[a] = k_drag * (ut - v[a]);
+      P.v[a][i] = v[a] + kp.dt * (Dn[a] / m_p + buoy * kp.gravity[a]);
+      P.x[a][i] = wrap_coord(x[a] + kp.dt * v[a], kp.L[a]);
+      P.xp[a][i] = x[a];
+      P.D[a][i] = Dn[a];
+    }
   }
   if (fscat) {
-    float s = -norm * kp.inv_rho_dV;
-    fscat[i] = make_float4(s * (float)Dn[0], s * (float)Dn[1], s * (float)Dn[2], 0.f);
+    const float s = -norm * kp.inv_rho_dV;
+    const float f0 = s * (float)Dn[0], f1 = s * (float)Dn[1], f2 = s * (float)Dn[2];
+    fscat[i] = make_float4(f0, f1, f2, fmaxf(fabsf(f0), fmaxf(fabsf(f1), fabsf(f2))));
   }
 }
 
 __global__ void k_finalize_up(erpp_kparams kp, int64_t n, const float* __restrict__ up_acc,
                               int64_t acc_stride, const float4* __restrict__ geo_t,
-                              const double* __restrict__ y, double* up0, double* up1,
-                              double* up2) {
+                              const int4* __restrict__ geo_c, const double* __restrict__ y,
+                              double* up0, double* up1, double* up2) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float norm = geo_t[i].w;
+  const float norm = erpp_norm(kp, geo_t[i], geo_c[i]);
   up0[i] = (double)(up_acc[i] * norm) + kp.shear_rate * y[i];
   up1[i] = (double)(up_acc[acc_stride + i] * norm);
   up2[i] = (double)(up_acc[2 * acc_stride + i] * norm);
@@ -185,11 +207,13 @@ __global__ void k_finalize_up(erpp_kparams kp, int64_t n, const float* __restric
 
 __global__ void k_prep_fscat(erpp_kparams kp, int64_t n, const double* __restrict__ D0,
                              const double* __restrict__ D1, const double* __restrict__ D2,
-                             const float4* __restrict__ geo_t, float4* __restrict__ fscat) {
+                             const float4* __restrict__ geo_t, const int4* __restrict__ geo_c,
+                             float4* __restrict__ fscat) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float s = -geo_t[i].w * kp.inv_rho_dV;
-  fscat[i] = make_float4(s * (float)D0[i], s * (float)D1[i], s * (float)D2[i], 0.f);
+  const float s = -erpp_norm(kp, geo_t[i], geo_c[i]) * kp.inv_rho_dV;
+  const float f0 = s * (float)D0[i], f1 = s * (float)D1[i], f2 = s * (float)D2[i];
+  fscat[i] = make_float4(f0, f1, f2, fmaxf(fabsf(f0), fmaxf(fabsf(f1), fabsf(f2))));
 }
 
 __global__ void k_windows(erpp_kparams kp, int64_t n, const double* __restrict__ x0,
@@ -315,13 +339,13 @@ cudaError_t launch_advance(erpp_ctx* ctx, const erpp_particles* P, const double*
   const bool f32 = !ctx->fp64;
   if (from_acc) {
     k_advance<true, true><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, ctx->up_acc, ctx->cap,
-                                                  ctx->geo_t, fs, first_step);
+                                                  ctx->geo_t, ctx->geo_c, fs, first_step);
   } else if (f32) {
     k_advance<false, true><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, nullptr, 0, nullptr,
-                                                   nullptr, first_step);
+                                                   nullptr, nullptr, first_step);
   } else {
     k_advance<false, false><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, nullptr, 0, nullptr,
-                                                    nullptr, first_step);
+                                                    nullptr, nullptr, first_step);
   }
   return cudaGetLastError();
 }
@@ -330,8 +354,8 @@ cudaError_t launch_finalize_up(erpp_ctx* ctx, int64_t n, const double* const x[3
                                double* const up[3], cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int blocks = (int)((n + 255) / 256);
-  k_finalize_up<<<blocks, 256, 0, st>>>(ctx->kp, n, ctx->up_acc, ctx->cap, ctx->geo_t, x[1],
-                                        up[0], up[1], up[2]);
+  k_finalize_up<<<blocks, 256, 0, st>>>(ctx->kp, n, ctx->up_acc, ctx->cap, ctx->geo_t,
+                                        ctx->geo_c, x[1], up[0], up[1], up[2]);
   return cudaGetLastError();
 }
 
@@ -339,7 +363,8 @@ cudaError_t launch_prep_fscat(erpp_ctx* ctx, int64_t n, const double* const D[3]
                               cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int blocks = (int)((n + 255) / 256);
-  k_prep_fscat<<<blocks, 256, 0, st>>>(ctx->kp, n, D[0], D[1], D[2], ctx->geo_t, ctx->fscat);
+  k_prep_fscat<<<blocks, 256, 0, st>>>(ctx->kp, n, D[0], D[1], D[2], ctx->geo_t, ctx->geo_c,
+                                       ctx->fscat);
   return cudaGetLastError();
 }
 
