@@ -165,6 +165,30 @@ erpp_status erpp_check(erpp_ctx* ctx, erpp_stream stream);
 erpp_status erpp_debug_windows(erpp_ctx* ctx, int64_t n, const double* const x[3],
                                int32_t* jlo, int32_t* jhi, erpp_stream stream);
 
+/* Kernel gather without any allocation, for callers that must not allocate
+ * device memory: code running while a memory pool is frozen or exhausted,
+ * plugins handed a fixed device budget by their host application, or paths
+ * that must never enter the allocator.  The paper has no counterpart; this is
+ * a deployment convenience.
+ * Computes exactly what erpp_interpolate computes with an ERPP_FP32 context
+ * made from the same params (u is a float grid, u_p n doubles per component),
+ * but takes the parameters directly and needs no context: its scratch lives
+ * in one fixed 2.6 MB array inside the library image, which every GPU that
+ * loads the library holds until the process exits.  No cudaMalloc, cudaFree
+ * or other allocating call is made.
+ * Limits: n <= 32768 particles, at most 262144 stencil pieces (n times the
+ * largest number of tiles one window can touch) and 16384 grid tiles; larger
+ * problems, an ERPP_FP64 flag or invalid params return ERPP_EINVAL before any
+ * launch.  Asynchronous on `stream`.  The first call on each device looks up
+ * the array's device address with that device current; make that first call
+ * before any stream capture.  Every call, from any thread or stream, uses the
+ * same array and leaves its contents behind: calls that overlap on the GPU
+ * race and must be serialised (one stream, or events).  Positions outside
+ * [0, L) are not reported (no error word is readable); their u_p is zero. */
+erpp_status erpp_interpolate_noalloc(const erpp_params* params, const void* u, int64_t n,
+                                     const double* const x[3], double* const u_p[3],
+                                     erpp_stream stream);
+
 /* Per-phase timing (a tracing aid, not part of the method).  After
  * erpp_profile_enable(ctx, 1) every erpp_step records CUDA events on its
  * stream around its phases: 0 binning (count, scan, fill), 1 gather,

@@ -75,6 +75,7 @@ _SIGS = {
     "erpp_momentum": (_st, [_vp, _vp, _i64, _dp3, _dp3, _dp, _vp]),
     "erpp_check": (_st, [_vp, _vp]),
     "erpp_debug_windows": (_st, [_vp, _i64, _dp3, _vp, _vp, _vp]),
+    "erpp_interpolate_noalloc": (_st, [ctypes.POINTER(Params), _vp, _i64, _dp3, _dp3, _vp]),
     "erpp_profile_enable": (_st, [_vp, ctypes.c_int]),
     "erpp_profile_read": (_st, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)]),
 }
