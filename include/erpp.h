@@ -173,11 +173,11 @@ erpp_status erpp_debug_windows(erpp_ctx* ctx, int64_t n, const double* const x[3
  * Computes exactly what erpp_interpolate computes with an ERPP_FP32 context
  * made from the same params (u is a float grid, u_p n doubles per component),
  * but takes the parameters directly and needs no context: its scratch lives
- * in one fixed 2.6 MB array inside the library image, which every GPU that
+ * in one fixed 5.2 MiB array inside the library image, which every GPU that
  * loads the library holds until the process exits.  No cudaMalloc, cudaFree
  * or other allocating call is made.
- * Limits: n <= 32768 particles, at most 262144 stencil pieces (n times the
- * largest number of tiles one window can touch) and 16384 grid tiles; larger
+ * Limits: n <= 16384 particles, at most 131072 stencil pieces (n times the
+ * largest number of tiles one window can touch) and 4096 grid tiles; larger
  * problems, an ERPP_FP64 flag or invalid params return ERPP_EINVAL before any
  * launch.  Asynchronous on `stream`.  The first call on each device looks up
  * the array's device address with that device current; make that first call

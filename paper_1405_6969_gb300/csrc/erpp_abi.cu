@@ -34,52 +34,6 @@ int max_pieces(int n, int T, int hlo, int xs) {
   return best;
 }
 
-// Number of shared-memory bank conflicts (extra wavefronts) for one pass of
-// `rows` rows of `xs` lanes whose row starts are at offsets off[0..rows).
-int conflicts(const int* off, int rows, int xs) {
-  int hits[32] = {0};
-  int worst = 0;
-  for (int q = 0; q < rows; ++q)
-    for (int i = 0; i < xs; ++i) {
-      int bank = ((off[q] + i) % 32 + 32) % 32;
-      worst = std::max(worst, ++hits[bank]);
-    }
-  return worst - 1;
-}
-
-// Row pitch: smallest px >= T_x with conflict-free passes of consecutive rows.
-int choose_px(int Tx, int xs, int rows) {
-  for (int px = Tx; px < Tx + 32; ++px) {
-    int off[32];
-    for (int q = 0; q < rows; ++q) off[q] = q * px;
-    if (conflicts(off, rows, xs) == 0) return px;
-  }
-  return Tx;
-}
-
-// Plane pitch: smallest pxy >= T_y px that keeps passes crossing a z plane
-// conflict-free for the typical window height ny_w.
-int choose_pxy(int Ty, int px, int xs, int rows, int ny_w) {
-  int best = Ty * px, best_c = 1 << 30;
-  for (int pxy = Ty * px; pxy < Ty * px + 32; ++pxy) {
-    int total = 0;
-    for (int r0 = 0; r0 < 2 * ny_w; r0 += 1) {
-      int off[32];
-      for (int q = 0; q < rows; ++q) {
-        int r = r0 + q;
-        off[q] = (r % ny_w) * px + (r / ny_w) * pxy;
-      }
-      total += conflicts(off, rows, xs);
-    }
-    if (total < best_c) {
-      best_c = total;
-      best = pxy;
-      if (total == 0) break;
-    }
-  }
-  return best;
-}
-
 erpp_status set_cuda_err(cudaError_t e) {
   if (e == cudaSuccess) return ERPP_OK;
   if (e == cudaErrorMemoryAllocation) return ERPP_ENOMEM;
@@ -89,12 +43,14 @@ erpp_status set_cuda_err(cudaError_t e) {
 void free_scratch(erpp_ctx* c) {
   cudaFree(c->geo_t);
   cudaFree(c->geo_c);
+  cudaFree(c->xw);
   cudaFree(c->up_acc);
   cudaFree(c->fscat);
   cudaFree(c->entries);
   cudaFree(c->up64);
   c->geo_t = nullptr;
   c->geo_c = nullptr;
+  c->xw = nullptr;
   c->up_acc = nullptr;
   c->fscat = nullptr;
   c->entries = nullptr;
@@ -115,10 +71,11 @@ erpp_status ensure_capacity(erpp_ctx* c, int64_t n) {
   } else {
     int64_t ecap = cap * (int64_t)c->maxseg[0] * c->maxseg[1] * c->maxseg[2];
     e = cudaMalloc(&c->geo_t, sizeof(float4) * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc(&c->xw, sizeof(float) * (size_t)c->xw_len * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->geo_c, sizeof(int4) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->up_acc, sizeof(float) * 3 * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->fscat, sizeof(float4) * (size_t)cap);
-    if (e == cudaSuccess) e = cudaMalloc(&c->entries, sizeof(uint32_t) * (size_t)ecap);
+    if (e == cudaSuccess) e = cudaMalloc(&c->entries, sizeof(int4) * (size_t)ecap);
     c->entries_cap = ecap;
   }
   if (e != cudaSuccess) {
@@ -225,27 +182,47 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
   kp.normalize = (p->flags & ERPP_NORMALIZE) ? 1 : 0;
   kp.self_removal = (p->flags & ERPP_SELF_REMOVAL) ? 1 : 0;
   kp.kahan = (p->flags & ERPP_KAHAN) ? 1 : 0;
-  // Tiles: 32 x 16 x 8 nodes (clamped to the grid).
-  const int Tdef[3] = {32, 16, 8};
-  int64_t ntiles = 1;
-  for (int a = 0; a < 3; ++a) {
-    kp.T[a] = std::min(Tdef[a], n[a]);
+  // Tiles: x-tiles of 64 nodes (a smaller even split for short axes), staged
+  // in rows of 96 floats with an x-halo of xhlo nodes below and xhhi above
+  // (the whole x-window of every particle whose home cell is in the tile);
+  // 8 x 8 in y and z.
+  kp.xhlo = (int)floor(kp.cp[0]);
+  kp.xhhi = kp.xhlo + 1;
+  kp.xlmin = (int)floor(2.0 * kp.cp[0]);
+  kp.xxs = (int)floor(2.0 * kp.cp[0] + 1e-6) + 1;
+  if (!(p->flags & ERPP_FP64) && kp.xxs > 16) return ERPP_EINVAL;  // FP32: x-windows <= 16
+  kp.px = 96;
+  const int wmax = std::min(64, kp.px - kp.xhlo - kp.xhhi);
+  const int hmax = std::max(kp.xhlo, kp.xhhi);
+  kp.T[0] = std::min(wmax, n[0]);
+  kp.nt[0] = (n[0] + kp.T[0] - 1) / kp.T[0];
+  if (kp.nt[0] > 1 && n[0] - (kp.nt[0] - 1) * kp.T[0] < hmax) {
+    // a sliver would be left over: split the axis evenly instead
+    kp.T[0] = (n[0] + kp.nt[0] - 1) / kp.nt[0];
+    kp.nt[0] = (n[0] + kp.T[0] - 1) / kp.T[0];
+  }
+  const int wlast = n[0] - (kp.nt[0] - 1) * kp.T[0];
+  if (kp.nt[0] > 1 && wlast < hmax) return ERPP_EINVAL;
+  const int Tyz[3] = {0, 8, 8};
+  int64_t ntiles = kp.nt[0];
+  for (int a = 1; a < 3; ++a) {
+    kp.T[a] = std::min(Tyz[a], n[a]);
     kp.nt[a] = (n[a] + kp.T[a] - 1) / kp.T[a];
     ntiles *= kp.nt[a];
   }
-  if (ntiles > (1 << 26)) return ERPP_EINVAL;
+  if (ntiles > (1 << 24)) return ERPP_EINVAL;
   kp.ntiles = (int)ntiles;
-  kp.px = choose_px(kp.T[0], kp.xs, kp.rows);
-  const int ny_w = std::max(1, (int)floor(2.0 * kp.cp[1]));
-  kp.pxy = choose_pxy(kp.T[1], kp.px, kp.xs, kp.rows, ny_w);
+  kp.rows = 0;
+  kp.pxy = kp.px * kp.T[1];
   kp.plane = kp.pxy * kp.T[2];
   if ((size_t)kp.plane * 6 * sizeof(float) > 227 * 1024) return ERPP_EINVAL;
-  kp.kahan_alloc = 1;
 
   c->params = *p;
   c->kp = kp;
   c->fp64 = prec == ERPP_FP64;
-  for (int a = 0; a < 3; ++a) c->maxseg[a] = max_pieces(n[a], kp.T[a], kp.hlo, kp.xs);
+  c->maxseg[0] = 1;  // a particle belongs to the x-tile of its home cell
+  c->xw_len = erpp::xw_len(kp);
+  for (int a = 1; a < 3; ++a) c->maxseg[a] = max_pieces(n[a], kp.T[a], kp.hlo, kp.xs);
   return ERPP_OK;
 }
 
@@ -270,9 +247,13 @@ erpp_status erpp_init(const erpp_params* p, erpp_ctx** out) {
   if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->red, sizeof(double) * (6 * 304 + 8));
   if (e == cudaSuccess && !c->fp64) {
-    e = cudaMalloc(&c->tile_cnt, sizeof(int32_t) * (size_t)kp.ntiles);
-    if (e == cudaSuccess) e = cudaMalloc(&c->tile_start, sizeof(int32_t) * ((size_t)kp.ntiles + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&c->tile_cursor, sizeof(int32_t) * (size_t)kp.ntiles);
+    const size_t nbins = (size_t)kp.ntiles * 32;
+    e = cudaMalloc(&c->tile_cnt, sizeof(int32_t) * nbins);
+    if (e == cudaSuccess) e = cudaMalloc(&c->tile_start, sizeof(int32_t) * (nbins + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&c->tile_cursor, sizeof(int32_t) * nbins);
+    if (e == cudaSuccess) e = cudaMalloc(&c->scan_tmp, sizeof(int32_t) * (nbins / 4096 + 1));
+    const size_t hb = (size_t)kp.ntiles * 3 * kp.T[2] * kp.T[1] * (kp.xhlo + kp.xhhi);
+    if (e == cudaSuccess) e = cudaMalloc(&c->halo, sizeof(float) * hb);
   }
   if (e != cudaSuccess) {
     erpp_status s = set_cuda_err(e);
@@ -295,6 +276,8 @@ erpp_status erpp_destroy(erpp_ctx* c) {
   cudaFree(c->tile_cnt);
   cudaFree(c->tile_start);
   cudaFree(c->tile_cursor);
+  cudaFree(c->scan_tmp);
+  cudaFree(c->halo);
   cudaFree(c->err);
   cudaFree(c->red);
   free(c);

@@ -2,10 +2,10 @@
 //
 // Each particle's truncated stencil (a box of at most xs^3 nodes, Sec. 2.4:
 // the forcing of a particle reaches only the nodes within a few sigma_R) is
-// split along tile boundaries and periodic images into (tile, shift) pieces.
-// One "entry" per piece is written, grouped by tile, so that the gather and
-// the scatter can both work on one tile interior per thread block with no
-// halo and no wrap-around in shared memory.
+// assigned to the x-tile of its home cell and split along y/z tile
+// boundaries and periodic images into (tile, shift) pieces.  One "entry" per
+// piece is written, grouped by tile, so that the gather and the scatter can
+// both work on one staged tile per thread block.
 //
 // Passes: k_bin_count (geometry per particle + per-tile piece counts),
 // k_scan (exclusive scan of the counts), k_bin_fill (place the entries).
@@ -15,43 +15,52 @@
 
 namespace {
 
-// Calls f(tile, code) for every (tile, periodic shift) piece of the window
-// [jlo, jlo + nw - 1] per axis (unwrapped node indices).
+// One piece of a particle's stencil: the y/z window part [jy, ey] x [jz, ez]
+// (unwrapped node indices) inside tile (tx, ty, tz) at periodic image
+// (my, mz).
+struct PieceSeg {
+  int tx, ty, tz;
+  int jy, ey, my, jz, ez, mz;
+};
+
+// Calls f(bin, seg) for every piece of a particle's stencil.  The x-tile is
+// the one holding the particle's home cell c_x (tiles are staged with an
+// x-halo wide enough for the whole x-window); the y and z windows
+// [jlo, jlo + nw - 1] are cut at tile boundaries and periodic images.
+// bin = tile * 32 + (x0 mod 32), x0 the first node of the x-window in the
+// tile's staged row: the tile kernels give bucket l to lane l.
 template <typename F>
-__device__ __forceinline__ void for_each_piece(const erpp_kparams& kp, const int jlo[3],
+__device__ __forceinline__ void for_each_piece(const erpp_kparams& kp, int cx, const int jlo[3],
                                                const int nw[3], F f) {
-  const int jhx = jlo[0] + nw[0] - 1, jhy = jlo[1] + nw[1] - 1, jhz = jlo[2] + nw[2] - 1;
-  for (int jx = jlo[0]; jx <= jhx;) {
-    int mx = erpp_floordiv(jx, kp.n[0]);
-    int wx = jx - mx * kp.n[0];
-    int tx = wx / kp.T[0];
-    int ex = min(min((tx + 1) * kp.T[0], kp.n[0]) - wx + jx - 1, jhx);
-    for (int jy = jlo[1]; jy <= jhy;) {
-      int my = erpp_floordiv(jy, kp.n[1]);
-      int wy = jy - my * kp.n[1];
-      int ty = wy / kp.T[1];
-      int ey = min(min((ty + 1) * kp.T[1], kp.n[1]) - wy + jy - 1, jhy);
-      for (int jz = jlo[2]; jz <= jhz;) {
-        int mz = erpp_floordiv(jz, kp.n[2]);
-        int wz = jz - mz * kp.n[2];
-        int tz = wz / kp.T[2];
-        int ez = min(min((tz + 1) * kp.T[2], kp.n[2]) - wz + jz - 1, jhz);
-        int tile = (tz * kp.nt[1] + ty) * kp.nt[0] + tx;
-        uint32_t code = (uint32_t)((mx + 1) + 3 * (my + 1) + 9 * (mz + 1));
-        f(tile, code);
-        jz = ez + 1;
-      }
-      jy = ey + 1;
+  PieceSeg sg;
+  sg.tx = cx / kp.T[0];
+  const int bucket = (jlo[0] - sg.tx * kp.T[0] + kp.xhlo) & 31;
+  const int jhy = jlo[1] + nw[1] - 1, jhz = jlo[2] + nw[2] - 1;
+  for (int jy = jlo[1]; jy <= jhy;) {
+    sg.my = erpp_floordiv(jy, kp.n[1]);
+    const int wy = jy - sg.my * kp.n[1];
+    sg.ty = wy / kp.T[1];
+    sg.jy = jy;
+    sg.ey = min(min((sg.ty + 1) * kp.T[1], kp.n[1]) - wy + jy - 1, jhy);
+    for (int jz = jlo[2]; jz <= jhz;) {
+      sg.mz = erpp_floordiv(jz, kp.n[2]);
+      const int wz = jz - sg.mz * kp.n[2];
+      sg.tz = wz / kp.T[2];
+      sg.jz = jz;
+      sg.ez = min(min((sg.tz + 1) * kp.T[2], kp.n[2]) - wz + jz - 1, jhz);
+      const int tile = (sg.tz * kp.nt[1] + sg.ty) * kp.nt[0] + sg.tx;
+      f(tile * 32 + bucket, sg);
+      jz = sg.ez + 1;
     }
-    jx = ex + 1;
+    jy = sg.ey + 1;
   }
 }
 
 __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict__ x0,
                             const double* __restrict__ x1, const double* __restrict__ x2,
                             float4* __restrict__ geo_t, int4* __restrict__ geo_c,
-                            float* __restrict__ up_acc, int64_t acc_stride,
-                            int32_t* __restrict__ tile_cnt, uint32_t* err) {
+                            float* __restrict__ xw, int xw_len, float* __restrict__ up_acc,
+                            int64_t acc_stride, int32_t* __restrict__ tile_cnt, uint32_t* err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double xv[3] = {x0[i], x1[i], x2[i]};
@@ -63,34 +72,39 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
   bool ok = true;
 #pragma unroll
   for (int a = 0; a < 3; ++a) ok = ok && (xv[a] >= 0.0) && (xv[a] < kp.L[a]);
-  if (!ok) {
-    erpp_set_err(err, ERPP_ERRBIT_RANGE);
-    geo_t[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    geo_c[i] = make_int4(0, 0, 0, 0);
-    return;
-  }
   int c[3], off[3], nw[3], jlo[3];
   float t[3];
+  if (ok) {
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    double s, lo, hi;
-    erpp_axis_window(xv[a], kp.inv_dx[a], kp.cp[a], &s, &lo, &hi);
-    double fl = floor(s);
-    int ci = (int)fl;
-    off[a] = (int)lo - ci;
-    nw[a] = (int)hi - (int)lo + 1;
-    t[a] = (float)__dadd_rn(s, -fl);
-    // s can round up to exactly N for x just below L: the cell is then the
-    // first one of the next image, which is the same node set shifted by N.
-    if (ci >= kp.n[a]) ci -= kp.n[a];
-    c[a] = ci;
-    jlo[a] = ci + off[a];
-    ok = ok && off[a] >= -kp.hlo && off[a] <= 0 && nw[a] >= 1 && nw[a] <= kp.xs;
+    for (int a = 0; a < 3; ++a) {
+      double s, lo, hi;
+      erpp_axis_window(xv[a], kp.inv_dx[a], kp.cp[a], &s, &lo, &hi);
+      double fl = floor(s);
+      int ci = (int)fl;
+      off[a] = (int)lo - ci;
+      nw[a] = (int)hi - (int)lo + 1;
+      t[a] = (float)__dadd_rn(s, -fl);
+      // s can round up to exactly N for x just below L: the cell is then the
+      // first one of the next image, which is the same node set shifted by N.
+      if (ci >= kp.n[a]) ci -= kp.n[a];
+      c[a] = ci;
+      jlo[a] = ci + off[a];
+    }
+    bool inb = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      inb = inb && off[a] >= -kp.hlo && off[a] <= 0 && nw[a] >= 1 && nw[a] <= kp.xs;
+    inb = inb && nw[0] <= xw_len;
+    if (!inb) erpp_set_err(err, ERPP_ERRBIT_BOUNDS);
+    ok = inb;
+  } else {
+    erpp_set_err(err, ERPP_ERRBIT_RANGE);
   }
+  float4* xw4 = reinterpret_cast<float4*>(xw + (size_t)i * xw_len);
   if (!ok) {
-    erpp_set_err(err, ERPP_ERRBIT_BOUNDS);
     geo_t[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     geo_c[i] = make_int4(0, 0, 0, 0);
+    for (int k = 0; k < xw_len / 4; ++k) xw4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
   uint32_t pack = ERPP_GEO_VALID;
@@ -101,70 +115,133 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
   }
   geo_t[i] = make_float4(t[0], t[1], t[2], 0.f);
   geo_c[i] = make_int4(c[0], c[1], c[2], (int)pack);
-  for_each_piece(kp, jlo, nw, [&](int tile, uint32_t) { atomicAdd(&tile_cnt[tile], 1); });
+  const float d0 = (float)off[0] - t[0];
+  for (int k = 0; k < xw_len / 4; ++k) {
+    float v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = 4 * k + j;
+      const float d = d0 + (float)q;
+      v[j] = q < nw[0] ? exp2f(-kp.beta[0] * d * d) : 0.f;
+    }
+    xw4[k] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  for_each_piece(kp, c[0], jlo, nw, [&](int bin, const PieceSeg&) { atomicAdd(&tile_cnt[bin], 1); });
 }
 
-__global__ void k_bin_fill(erpp_kparams kp, int64_t n, const int4* __restrict__ geo_c,
-                           int32_t* __restrict__ cursor, uint32_t* __restrict__ entries,
-                           int64_t cap, uint32_t* err) {
+// Writes one record per piece, at its place in the (tile, bucket) order.
+__global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict__ geo_t,
+                           const int4* __restrict__ geo_c, int32_t* __restrict__ cursor,
+                           int4* __restrict__ entries, int64_t cap, uint32_t* err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int4 g = geo_c[i];
-  uint32_t pack = (uint32_t)g.w;
+  const int4 g = geo_c[i];
+  const uint32_t pack = (uint32_t)g.w;
   if (!(pack & ERPP_GEO_VALID)) return;
-  int c[3] = {g.x, g.y, g.z};
+  const float4 gt = geo_t[i];
+  const int c[3] = {g.x, g.y, g.z};
   int jlo[3], nw[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     jlo[a] = c[a] + erpp_geo_off(pack, a);
     nw[a] = erpp_geo_nw(pack, a);
   }
-  for_each_piece(kp, jlo, nw, [&](int tile, uint32_t code) {
-    int pos = atomicAdd(&cursor[tile], 1);
+  for_each_piece(kp, c[0], jlo, nw, [&](int bin, const PieceSeg& sg) {
+    const int by = sg.ty * kp.T[1], bz = sg.tz * kp.T[2];
+    const int x0 = jlo[0] - (sg.tx * kp.T[0] - kp.xhlo);
+    const int l0y = sg.jy - sg.my * kp.n[1] - by;
+    const int l0z = sg.jz - sg.mz * kp.n[2] - bz;
+    const int base = l0z * kp.pxy + l0y * kp.px + x0;
+    const int ly = sg.ey - sg.jy + 1, lz = sg.ez - sg.jz + 1;
+    const float d0y = (float)(sg.jy - c[1]) - gt.y;
+    const float d0z = (float)(sg.jz - c[2]) - gt.z;
+    const int pos = atomicAdd(&cursor[bin], 1);
     if (pos < cap)
-      entries[pos] = (uint32_t)i | (code << ERPP_ENTRY_PBITS);
+      entries[pos] = make_int4((int)i, base | (nw[0] << 17) | (ly << 22) | (lz << 27),
+                               __float_as_int(d0y), __float_as_int(d0z));
     else
       erpp_set_err(err, ERPP_ERRBIT_BOUNDS);
   });
 }
 
-// Exclusive scan of the per-tile counts by one thread block.
-__global__ void k_scan(const int32_t* __restrict__ cnt, int32_t* __restrict__ start,
-                       int32_t* __restrict__ cursor, int ntiles) {
-  __shared__ int32_t warp_sums[32];
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int chunk = (ntiles + nthr - 1) / nthr;
-  const int lo = min(tid * chunk, ntiles), hi = min(lo + chunk, ntiles);
-  int32_t local = 0;
-  for (int k = lo; k < hi; ++k) local += cnt[k];
-  // block-wide exclusive scan of the per-thread sums
-  const int lane = tid & 31, warp = tid >> 5;
-  int32_t incl = local;
+// Exclusive scan of the per-bin counts: k_scan_local scans chunks of
+// kScanChunk bins (one block each) and writes the chunk totals, k_scan_top
+// scans the totals in one block, k_scan_add offsets every chunk.
+constexpr int kScanChunk = 4096;
+
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* warp_sums,
+                                                        int32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int32_t incl = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
+    int32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
   }
   if (lane == 31) warp_sums[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    int32_t ws = (lane < (nthr >> 5)) ? warp_sums[lane] : 0;
+    int32_t ws = lane < nw ? warp_sums[lane] : 0;
     int32_t wi = ws;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int32_t v = __shfl_up_sync(0xffffffffu, wi, o);
-      if (lane >= o) wi += v;
+      int32_t u = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += u;
     }
     warp_sums[lane] = wi - ws;
+    if (lane == 31) *total = wi;
   }
   __syncthreads();
-  int32_t run = warp_sums[warp] + incl - local;
-  for (int k = lo; k < hi; ++k) {
-    start[k] = run;
-    cursor[k] = run;
-    run += cnt[k];
+  int32_t r = warp_sums[warp] + incl - v;
+  __syncthreads();
+  return r;
+}
+
+// 1024 threads x 4 bins per thread = one chunk.
+__global__ void k_scan_local(const int32_t* __restrict__ cnt, int32_t* __restrict__ start,
+                             int32_t* __restrict__ chunk_tot, int nbins) {
+  __shared__ int32_t ws[32];
+  __shared__ int32_t tot;
+  const int base = blockIdx.x * kScanChunk + threadIdx.x * 4;
+  int32_t v[4];
+  int32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = (base + k < nbins) ? cnt[base + k] : 0;
+    s += v[k];
   }
-  if (tid == nthr - 1) start[ntiles] = run;
+  int32_t run = block_exclusive_scan(s, ws, &tot);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (base + k < nbins) start[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == 0) chunk_tot[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(int32_t* __restrict__ chunk_tot, int nchunks, int32_t* __restrict__ start,
+                           int nbins) {
+  __shared__ int32_t ws[32];
+  __shared__ int32_t tot;
+  int32_t carry = 0;
+  for (int c0 = 0; c0 < nchunks; c0 += blockDim.x) {
+    const int c = c0 + threadIdx.x;
+    const int32_t v = c < nchunks ? chunk_tot[c] : 0;
+    const int32_t ex = block_exclusive_scan(v, ws, &tot);
+    if (c < nchunks) chunk_tot[c] = carry + ex;
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) start[nbins] = carry;
+}
+
+__global__ void k_scan_add(int32_t* __restrict__ start, int32_t* __restrict__ cursor,
+                           const int32_t* __restrict__ chunk_off, int nbins) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbins) return;
+  const int32_t v = start[i] + chunk_off[i / kScanChunk];
+  start[i] = v;
+  cursor[i] = v;
 }
 
 }  // namespace
@@ -174,19 +251,24 @@ namespace erpp {
 cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bool zero_acc,
                           cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;
-  cudaError_t e = cudaMemsetAsync(ctx->tile_cnt, 0, sizeof(int32_t) * kp.ntiles, st);
+  const int nbins = kp.ntiles * 32;
+  cudaError_t e = cudaMemsetAsync(ctx->tile_cnt, 0, sizeof(int32_t) * nbins, st);
   if (e != cudaSuccess) return e;
   if (n > 0) {
     int blocks = (int)((n + 255) / 256);
     k_bin_count<<<blocks, 256, 0, st>>>(kp, n, x[0], x[1], x[2], ctx->geo_t, ctx->geo_c,
-                                        zero_acc ? ctx->up_acc : nullptr, ctx->cap,
-                                        ctx->tile_cnt, ctx->err);
+                                        ctx->xw, ctx->xw_len, zero_acc ? ctx->up_acc : nullptr,
+                                        ctx->cap, ctx->tile_cnt, ctx->err);
   }
-  k_scan<<<1, 1024, 0, st>>>(ctx->tile_cnt, ctx->tile_start, ctx->tile_cursor, kp.ntiles);
+  const int nchunks = (nbins + kScanChunk - 1) / kScanChunk;
+  k_scan_local<<<nchunks, 1024, 0, st>>>(ctx->tile_cnt, ctx->tile_start, ctx->scan_tmp, nbins);
+  k_scan_top<<<1, 1024, 0, st>>>(ctx->scan_tmp, nchunks, ctx->tile_start, nbins);
+  k_scan_add<<<(nbins + 255) / 256, 256, 0, st>>>(ctx->tile_start, ctx->tile_cursor, ctx->scan_tmp,
+                                                 nbins);
   if (n > 0) {
     int blocks = (int)((n + 255) / 256);
-    k_bin_fill<<<blocks, 256, 0, st>>>(kp, n, ctx->geo_c, ctx->tile_cursor, ctx->entries,
-                                       ctx->entries_cap, ctx->err);
+    k_bin_fill<<<blocks, 256, 0, st>>>(kp, n, ctx->geo_t, ctx->geo_c, ctx->tile_cursor,
+                                       ctx->entries, ctx->entries_cap, ctx->err);
   }
   return cudaGetLastError();
 }

@@ -1,15 +1,29 @@
 // erpp_internal.cuh -- shared declarations of the ERPP CUDA library.
 //
 // Layout of the per-step data in HBM (FP32 tiled path):
-//   geo_t[i]  float4  (t_x, t_y, t_z, norm): fractional position of particle i
-//                     inside its home cell and the kernel normalisation
+//   geo_t[i]  float4  (t_x, t_y, t_z, -): fractional position of particle i
+//                     inside its home cell
 //   geo_c[i]  int4    (c_x, c_y, c_z, pack): home cell and packed window
 //                     (offset of the first node below the cell, window length)
-//   entries[] uint32  one per (particle, tile, periodic shift) whose window
-//                     reaches the tile interior, grouped by tile (counting sort)
+//   xw[i]     float[XW] the particle's x-weights 2^(-beta_x d^2) over its
+//                     x-window (zero beyond it), XW = 8 or 16
+//   entries[] int4    one record per piece (particle, tile, periodic shift in
+//                     y/z) whose window reaches the tile, grouped by tile and,
+//                     inside a tile, by the bucket x0 mod 32 (counting sort):
+//                     {particle, base | lx << 17 | ly << 22 | lz << 27,
+//                      d0y bits, d0z bits}, base the shared-memory index of
+//                     the piece's first node, d0 its distance (grid units)
+//                     A particle belongs to the x-tile of its home cell and
+//                     keeps its whole x-window there (tiles are staged with an
+//                     x-halo); only y and z windows are cut at tile boundaries.
 //   up_acc    float[3][n]  gathered velocity before normalisation
-//   fscat[i]  float4  -(1/rho_f) D_i norm / dV: the force as the scatter uses it
-// Grids are [3][nz][ny][nx] (x fastest), tiles are boxes of T_x*T_y*T_z nodes.
+//   fscat[i]  float4  -(1/rho_f) D_i norm / dV, max|component|
+//   halo      float   per tile, the scatter's x-halo columns (left hlo,
+//                     right hhi), [tile][3][T_z][T_y][hlo + hhi]
+// Grids are [3][nz][ny][nx] (x fastest).  Tiles: x-width W = 64 (last one
+// ragged), T_y x T_z in y/z; a tile is staged in shared memory as
+// [3][T_z][T_y][PX] with PX = 96 floats per row (a multiple of the 32 banks),
+// local x' = x - (tile start - hlo).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -27,25 +41,24 @@
 // 22-26 = window length on x / y / z, bit 31 = valid.
 #define ERPP_GEO_VALID 0x80000000u
 
-// Entry word: particle index in bits 0-26, periodic-shift code in 27-31
-// (code = (mx+1) + 3 (my+1) + 9 (mz+1), m the image shift per axis).
-#define ERPP_ENTRY_PBITS 27
-#define ERPP_ENTRY_PMASK ((1u << ERPP_ENTRY_PBITS) - 1u)
-#define ERPP_MAX_PARTICLES ((int64_t)ERPP_ENTRY_PMASK)
+// Particle indices are 31-bit; the packed piece base is 17 bits.
+#define ERPP_MAX_PARTICLES ((int64_t)0x7fffffff)
+#define ERPP_BASE_BITS 17
 
 // Kernel-side constants of one grid and parameter set.
 struct erpp_kparams {
   int32_t n[3];      // nodes per axis
-  int32_t T[3];      // tile size per axis
+  int32_t T[3];      // tile size per axis (T[0] = W, the x-tile width)
   int32_t nt[3];     // tiles per axis
   int32_t ntiles;
-  int32_t hlo;       // floor(r_c / dx): lowest window offset is -hlo
-  int32_t xs;        // x slots per row = 2 hlo + 1 (>= any window length)
-  int32_t rows;      // rows per warp pass = 32 / xs
+  int32_t hlo;       // floor(c'): lowest window offset is -hlo (all axes)
+  int32_t xs;        // longest window, floor(2 c') + 1 (all axes)
+  int32_t xhlo, xhhi;// x-halo columns staged below / above a tile
+  int32_t xlmin, xxs; // shortest / longest x-window (floor(2 c'_x), floor(2 c'_x) + 1)
+  int32_t rows;      // (unused by the lane-per-piece kernels)
   int32_t px, pxy;   // shared-memory pitches (floats) of one tile
   int32_t plane;     // floats per component of one tile = pxy * T_z
   int32_t normalize, self_removal, kahan;
-  int32_t kahan_alloc;  // scatter shared memory holds a compensation plane set
   double inv_dx[3];  // N / L
   double L[3];
   double cp[3];      // r_c / dx
@@ -73,14 +86,18 @@ struct erpp_ctx {
   int64_t cap;            // particle capacity of the per-particle arrays
   float4* geo_t;
   int4* geo_c;
+  float* xw;              // [cap][xw_len] x-weights per particle
+  int xw_len;
   float* up_acc;          // [3][cap]
   float4* fscat;
   double* up64;           // FP64 mode: gathered velocity [3][cap]
-  uint32_t* entries;
+  int4* entries;
   int64_t entries_cap;
-  int32_t* tile_cnt;      // [ntiles]
-  int32_t* tile_start;    // [ntiles + 1]
-  int32_t* tile_cursor;   // [ntiles]
+  float* halo;            // scatter x-halo columns, [ntiles][3][T_z][T_y][xhlo + xhhi]
+  int32_t* tile_cnt;      // [32 ntiles]: pieces per (tile, bucket) bin
+  int32_t* tile_start;    // [32 ntiles + 1]
+  int32_t* tile_cursor;   // [32 ntiles]
+  int32_t* scan_tmp;      // [ceil(32 ntiles / 4096)] chunk totals of the scan
   uint32_t* err;          // device error word
   double* red;            // reduction scratch
   int red_cap;
@@ -96,10 +113,11 @@ constexpr int kProfSets = 1024;
 namespace erpp {
 
 erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c);
+int xw_len(const erpp_kparams& kp);
 cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bool zero_acc,
                           cudaStream_t st);
 cudaError_t launch_gather_f32(erpp_ctx* ctx, const float* u, int64_t n, cudaStream_t st);
-cudaError_t launch_scatter_f32(erpp_ctx* ctx, float* S, cudaStream_t st);
+cudaError_t launch_scatter_f32(erpp_ctx* ctx, float* S, cudaStream_t st);  // + x-halo merge
 cudaError_t launch_finalize_up(erpp_ctx* ctx, int64_t n, const double* const x[3],
                                double* const up[3], cudaStream_t st);
 cudaError_t launch_prep_fscat(erpp_ctx* ctx, int64_t n, const double* const D[3],

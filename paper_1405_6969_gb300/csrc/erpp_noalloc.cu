@@ -18,24 +18,28 @@
 
 namespace {
 
-constexpr int64_t kNoallocParticles = 32768;       // particles per call, at most
+constexpr int64_t kNoallocParticles = 16384;       // particles per call, at most
 constexpr int64_t kNoallocPieces = 8 * kNoallocParticles;
-constexpr int64_t kNoallocTiles = 16384;           // grid tiles, at most
+constexpr int64_t kNoallocTiles = 4096;            // grid tiles, at most
 
 // Byte layout of the static scratch (each part 256-byte aligned).
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kOffGeoT = 0;
 constexpr size_t kOffGeoC = kOffGeoT + align256(16 * kNoallocParticles);
 constexpr size_t kOffAcc = kOffGeoC + align256(16 * kNoallocParticles);
-constexpr size_t kOffEntries = kOffAcc + align256(12 * kNoallocParticles);
-constexpr size_t kOffCnt = kOffEntries + align256(4 * kNoallocPieces);
-constexpr size_t kOffStart = kOffCnt + align256(4 * kNoallocTiles);
-constexpr size_t kOffCursor = kOffStart + align256(4 * (kNoallocTiles + 1));
-constexpr size_t kOffErr = kOffCursor + align256(4 * kNoallocTiles);
+constexpr size_t kOffXw = kOffAcc + align256(12 * kNoallocParticles);
+constexpr size_t kOffEntries = kOffXw + align256(4 * 16 * kNoallocParticles);
+constexpr int64_t kNoallocBins = 32 * kNoallocTiles;  // (tile, bucket) bins
+constexpr size_t kOffCnt = kOffEntries + align256(16 * kNoallocPieces);
+constexpr size_t kOffStart = kOffCnt + align256(4 * kNoallocBins);
+constexpr size_t kOffCursor = kOffStart + align256(4 * (kNoallocBins + 1));
+constexpr size_t kOffScan = kOffCursor + align256(4 * kNoallocBins);
+constexpr size_t kOffErr = kOffScan + align256(4 * (kNoallocBins / 4096 + 1));
 constexpr size_t kScratchBytes = kOffErr + 256;
 
 // Held by every GPU that loads the library, until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+static_assert(kScratchBytes < 10u * 1024u * 1024u, "no-alloc scratch must stay modest");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -84,10 +88,12 @@ extern "C" erpp_status erpp_interpolate_noalloc(const erpp_params* params, const
   c.geo_t = reinterpret_cast<float4*>(base + kOffGeoT);
   c.geo_c = reinterpret_cast<int4*>(base + kOffGeoC);
   c.up_acc = reinterpret_cast<float*>(base + kOffAcc);
-  c.entries = reinterpret_cast<uint32_t*>(base + kOffEntries);
+  c.entries = reinterpret_cast<int4*>(base + kOffEntries);
+  c.xw = reinterpret_cast<float*>(base + kOffXw);
   c.tile_cnt = reinterpret_cast<int32_t*>(base + kOffCnt);
   c.tile_start = reinterpret_cast<int32_t*>(base + kOffStart);
   c.tile_cursor = reinterpret_cast<int32_t*>(base + kOffCursor);
+  c.scan_tmp = reinterpret_cast<int32_t*>(base + kOffScan);
   c.err = reinterpret_cast<uint32_t*>(base + kOffErr);
   cudaStream_t st = (cudaStream_t)stream;
   // The per-tile counts are cleared by the binning itself and the gather

@@ -59,6 +59,10 @@ CASES = [
     ("small_16x12x10_sigma1.5", rep(I.CFG_CLUSTERED, n=(16, 12, 10), L=(2 * math.pi, 5.0, 4.0),
                                      n_particles=500, cluster_std=0.5, kmax=3.0), 500),
     ("aniso_96x33x17", rep(I.CFG_SMALL, n=(96, 33, 17), L=(2 * math.pi, 2.0, 1.0)), 2000),
+    # isotropic spacing where r_c / dx rounds to just below 3 (windows of 5-7
+    # nodes), two x-tiles of 64 and 8 nodes
+    ("iso_72x40x20", rep(I.CFG_SMALL, n=(72, 40, 20), kmax=3.0,
+                         L=(2 * math.pi, 2 * math.pi * 40 / 72, 2 * math.pi * 20 / 72)), 3000),
 ]
 
 
