@@ -51,9 +51,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kahan", action="store_true")
-    ap.add_argument("--workload", default="shear", choices=["shear", "cube256"],
+    ap.add_argument("--no-loop", action="store_true",
+                    help="skip the closed-loop (coupling + fluid stand-in) timing")
+    ap.add_argument("--workload", default="shear", choices=["shear", "cube256", "batched64"],
                     help="shear: 512x256x256 box (the benchmark); cube256: 256^3, 1M "
-                         "particles (profiling case)")
+                         "particles (profiling case); batched64: 64 independent boxes "
+                         "(64^3-128^3, 1e3-2e5 particles each) stepped as one graph")
     return ap.parse_args()
 
 
@@ -207,11 +210,94 @@ def cpu_baseline(w, grid, st):
                       f"512x256x256 grid ({dt:.1f} s, single thread)"}
 
 
+def run_batched(args, ws, rank, local):
+    """64 independent boxes: one replayed CUDA graph per step, against the
+    same boxes as 64 plain launch sequences and against the plain FP64 form."""
+    import torch
+    from paper_1405_6969_gb300 import Batch, ParticleState
+    boxes = I.batched_boxes(64, seed0=64 * rank)
+    nodes_per_step = 0
+    made = []
+    for w in boxes:
+        grid, _ = I.make_grid(w)
+        st = I.make_particles(w, None)
+        nodes_per_step += 2 * stencil_nodes(st.x, w)
+        made.append((w, grid, st))
+
+    def batch(precision):
+        dt = torch.float32 if precision == "fp32" else torch.float64
+        entries = []
+        for w, grid, st in made:
+            u = torch.as_tensor(grid, dtype=dt).cuda().contiguous()
+            entries.append((w.params(), u, ParticleState.from_numpy(st), torch.empty_like(u)))
+        return Batch(entries, precision=precision)
+
+    stream = torch.cuda.current_stream()
+
+    def timed(b, use_graph, steps):
+        for k in range(args.warmup):
+            b.step(first_step=(k == 0), use_graph=use_graph)
+        b.check()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            b.step(use_graph=use_graph)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        b.check()
+        return e0.elapsed_time(e1) / steps
+
+    b32 = batch("fp32")
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    ms_graph = timed(b32, True, args.steps)
+    clocks = sampler.stop()
+    ms_eager = timed(b32, False, max(3, args.steps // 4))
+    b32.close()
+    b64 = batch("fp64")
+    ms_f64 = timed(b64, False, max(3, min(args.steps // 10, 10)))
+    b64.close()
+    value = nodes_per_step / (ms_graph * 1e-3)
+    if rank == 0:
+        n_p = sum(w.n_particles for w, _, _ in made)
+        line = {
+            "metric": "particle-stencil node updates/s (gather + scatter), 64 batched boxes",
+            "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 kernels, f64 particle integration", "data": "synthetic",
+            "config": {"workload": "batched64_boxes_64-128cube_1e3-2e5_particles",
+                       "boxes": len(made), "particles_total": n_p,
+                       "nodes_total": sum(w.n_nodes for w, _, _ in made),
+                       "l2": "inputs larger than L2 (about 0.9 GB of grids)"},
+            "steps_per_s": 1e3 / ms_graph,
+            "plain_launches_ms_per_step": ms_eager,
+            "graph_speedup_vs_plain_launches": ms_eager / ms_graph,
+            "fp64_plain_form_ms_per_step": ms_f64,
+            "speedup_vs_fp64_plain_form": ms_f64 / ms_graph,
+            "roofline": None, "cpu_baseline": None,
+            "e2e": None,
+            "gpu_launches": 9 * len(made) * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.workload == "batched64":
+        import torch
+        torch.cuda.set_device(local)
+        from paper_1405_6969_gb300 import build as libbuild
+        libbuild.build()
+        run_batched(args, ws, rank, local)
         return
     import torch
     import torch.distributed as dist
@@ -281,6 +367,38 @@ def main():
                 "peak_kind": peak_kind}
     step_gbs = alg["step"] / (ms_per_step * 1e-3) / 1e9
 
+    # the closed loop of the shear workload: coupling step, then the fluid
+    # stand-in forced by the new source (the fluid is timed on its own too)
+    loop = None
+    if not args.no_loop:
+        from paper_1405_6969_gb300 import StokesFluid
+        fl = StokesFluid(w.params(), precision="fp32")
+        u_loop = u.clone()
+        for _ in range(3):
+            fl.step(u_loop, S)
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        l2 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        l0.record(stream)
+        for _ in range(20):
+            fl.step(u_loop, S)
+        l1.record(stream)
+        n_loop = 100
+        for _ in range(n_loop):
+            ctx.step(u_loop, ps, S=S)
+            fl.step(u_loop, S)
+        l2.record(stream)
+        torch.cuda.synchronize()
+        ctx.check()
+        fluid_ms = l0.elapsed_time(l1) / 20
+        loop_ms = l1.elapsed_time(l2) / n_loop
+        loop = {"steps": n_loop, "loop_ms_per_step": loop_ms, "fluid_ms_per_step": fluid_ms,
+                "coupling_ms_per_step": loop_ms - fluid_ms,
+                "fluid": "exact periodic Stokes step (cuFFT R2C/C2R + spectral kernel)"}
+        del u_loop
+        fl.close()
+
     # end to end through the public API: host (pinned) buffers in and out
     e2e = None
     if not args.no_e2e:
@@ -340,8 +458,11 @@ def main():
                          "frac": step_gbs / peak},
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "coupled_loop": loop,
             "e2e": e2e,
-            "gpu_launches": 6 * args.steps,
+            # bin count, three scan kernels, bin fill, gather, advance, scatter,
+            # halo merge
+            "gpu_launches": 9 * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

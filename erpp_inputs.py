@@ -200,6 +200,9 @@ def random_field(n, L, kmax, seed):
         np.add.at(A, (m[:, 2] % nz, m[:, 1] % ny, m[:, 0] % nx), a[:, c])
         grid[c] = np.real(ifftn(A)) * ntot
     rms = np.sqrt(np.mean(grid ** 2, axis=(1, 2, 3)))
+    # a component with no admissible mode (boxes too thin for K_max on two
+    # axes) stays identically zero
+    rms = np.where(rms > 0.0, rms, 1.0)
     grid /= rms[:, None, None, None]
     a = a / rms[None, :]
     return grid, SpectralField(m=m, k=k, a=a)

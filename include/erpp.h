@@ -138,6 +138,30 @@ erpp_status erpp_particle_advance(erpp_ctx* ctx, const double* const u_p[3],
 erpp_status erpp_scatter_source(erpp_ctx* ctx, int64_t n, const double* const x[3],
                                 const double* const D[3], void* S, erpp_stream stream);
 
+/* Adjoint of the source (Eq. ns_regularized_filtered) for a scalar loss L of
+ * S: given the cotangent R = dL/dS (grid field, float/double per mode),
+ *   dD[c][i] = dL/dD_ic = -(1/rho_f) sum_j R[c][j] W_i(j),
+ *   dx[a][i] = dL/dx_ia = -(1/rho_f) sum_j (R_j . D_i) dW_i(j)/dx_ia,
+ * with dw/dx_p = w d / sigma_R^2 per axis factor (d = x_j - x_p) for raw
+ * weights and w (d - dx sum_k w_k d_k) / sigma_R^2 for normalised ones (the
+ * normalising sum depends on x_p too).  x, D: n positions and forces per
+ * component; dD (may be NULL) and dx: n doubles per component (outputs,
+ * overwritten).  Weights and sums in the context's precision (FP32 or FP64). */
+erpp_status erpp_scatter_backward(erpp_ctx* ctx, int64_t n, const double* const x[3],
+                                  const double* const D[3], const void* R, double* const dD[3],
+                                  double* const dx[3], erpp_stream stream);
+
+/* Adjoint of the kernel gather (erpp_interpolate) for a scalar loss L of u_p:
+ * given g = dL/du_p (n doubles per component),
+ *   du[c][j] = dL/du_cj = dV sum_i g[c][i] W_i(j)      (grid, overwritten;
+ *                                                        a scatter of g),
+ *   dx[a][i] = dL/dx_ia = dV sum_j (u_j . g_i) dW_i(j)/dx_ia
+ *                         + shear_rate g[0][i] (a = y only).
+ * du or dx may be NULL (not both).  u: the grid field the gather read. */
+erpp_status erpp_gather_backward(erpp_ctx* ctx, int64_t n, const double* const x[3],
+                                 const void* u, const double* const g[3], void* du,
+                                 double* const dx[3], erpp_stream stream);
+
 /* One coupling step: gather u at P->x, remove the self disturbance, drag,
  * Euler advance (as erpp_particle_advance), then scatter the new forces at
  * the positions they were evaluated at (P->x_prev after the call) into S
@@ -188,6 +212,76 @@ erpp_status erpp_debug_windows(erpp_ctx* ctx, int64_t n, const double* const x[3
 erpp_status erpp_interpolate_noalloc(const erpp_params* params, const void* u, int64_t n,
                                      const double* const x[3], double* const u_p[3],
                                      erpp_stream stream);
+
+/* ---- Batched boxes ---------------------------------------------------
+ * Many independent periodic boxes (each with its own grid, parameters and
+ * particles) stepped together.  The paper treats one box; stepping many
+ * small ones at once is a throughput form of the same step. */
+
+#define ERPP_MAX_BOXES 4096
+
+/* One box: its parameters, its grid fields and its particle state (device
+ * pointers, caller-owned, as for erpp_step).  u is read, S overwritten and
+ * the particle arrays advanced by every step. */
+typedef struct {
+  erpp_params params;
+  const void* u;
+  erpp_particles particles;
+  void* S;
+} erpp_box_desc;
+
+typedef struct erpp_batch erpp_batch;
+
+/* Creates a batch over nbox (1..ERPP_MAX_BOXES) box descriptors (copied):
+ * one context per box, with its scratch allocated now for the box's particle
+ * count.  The descriptors' buffers must stay allocated and in place until
+ * erpp_batch_destroy: the batch keeps their addresses (their contents may
+ * change between steps).  *out is NULL on failure. */
+erpp_status erpp_batch_init(int32_t nbox, const erpp_box_desc* boxes, erpp_batch** out);
+
+/* One coupling step (erpp_step) of every box, asynchronous on `stream`.
+ * use_graph != 0: the first call for each value of first_step captures all
+ * boxes' launch sequences into one CUDA graph (one independent branch per
+ * box, boxes run concurrently) and every call replays it with a single graph
+ * launch on `stream`; the capture itself makes no allocation.  use_graph ==
+ * 0: the boxes' launches are issued one box after another on `stream`.
+ * Both forms compute the same thing. */
+erpp_status erpp_step_batched(erpp_batch* batch, int first_step, int use_graph,
+                              erpp_stream stream);
+
+/* erpp_check over every box: synchronises `stream`, returns the first error
+ * found (and clears each box's error word). */
+erpp_status erpp_batch_check(erpp_batch* batch, erpp_stream stream);
+
+/* Frees the batch, its contexts and graphs (synchronises the device first).
+ * NULL is accepted. */
+erpp_status erpp_batch_destroy(erpp_batch* batch);
+
+/* ---- Fluid stand-in ---------------------------------------------------
+ * One exact step of the periodic unsteady Stokes equations forced by the
+ * source, with the forcing / projection / diffusion split App. A.5 uses for
+ * one step (the linear disturbance problem of Sec. 2.2):
+ *   u_hat <- exp(-nu |k|^2 dt) P(k) (u_hat + dt S_hat),
+ * P(k) = I - k k^T / |k|^2 (identity on the mean mode), k_a = 2 pi m_a / L_a.
+ * It closes the two-way coupling loop in place of the paper's DNS solver
+ * (Sec. 3-4), which is not part of this library. */
+
+typedef struct erpp_fluid erpp_fluid;
+
+/* Creates the stand-in for the grid, nu and dt of params (precision from
+ * ERPP_FP32 / ERPP_FP64; other flags ignored; every axis needs >= 2 nodes).
+ * Allocates the spectral scratch (3 nz ny (nx/2+1) complex values) and the
+ * FFT plans on the current device. */
+erpp_status erpp_fluid_init(const erpp_params* params, erpp_fluid** out);
+
+/* u <- one Stokes step of u forced by S (both grid fields of the fluid's
+ * precision, [3][nz][ny][nx]); u is overwritten (also used as the transform
+ * input), S is read.  Asynchronous on `stream`. */
+erpp_status erpp_fluid_stokes_step(erpp_fluid* fluid, void* u, const void* S,
+                                   erpp_stream stream);
+
+/* Frees the stand-in (synchronises the device first).  NULL is accepted. */
+erpp_status erpp_fluid_destroy(erpp_fluid* fluid);
 
 /* Per-phase timing (a tracing aid, not part of the method).  After
  * erpp_profile_enable(ctx, 1) every erpp_step records CUDA events on its

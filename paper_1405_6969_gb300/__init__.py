@@ -6,7 +6,8 @@ The computation lives in the CUDA library ``liberpp.so`` behind the C ABI of
 """
 
 from ._lib import FP32, FP64, KAHAN, NORMALIZE, SELF_REMOVAL, ErppError, load  # noqa: F401
-from .erpp import Context, ParticleState  # noqa: F401
+from .erpp import (Batch, Context, Interpolate, ParticleState, ScatterSource,  # noqa: F401
+                   StokesFluid)
 
-__all__ = ["Context", "ParticleState", "ErppError", "load", "FP32", "FP64", "NORMALIZE",
-           "SELF_REMOVAL", "KAHAN"]
+__all__ = ["Batch", "Context", "StokesFluid", "ParticleState", "ScatterSource", "Interpolate", "ErppError", "load",
+           "FP32", "FP64", "NORMALIZE", "SELF_REMOVAL", "KAHAN"]

@@ -57,6 +57,11 @@ class Particles(ctypes.Structure):
     ]
 
 
+class BoxDesc(ctypes.Structure):
+    _fields_ = [("params", Params), ("u", ctypes.c_void_p), ("particles", Particles),
+                ("S", ctypes.c_void_p)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -78,6 +83,17 @@ _SIGS = {
     "erpp_interpolate_noalloc": (_st, [ctypes.POINTER(Params), _vp, _i64, _dp3, _dp3, _vp]),
     "erpp_profile_enable": (_st, [_vp, ctypes.c_int]),
     "erpp_profile_read": (_st, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)]),
+    "erpp_batch_init": (_st, [ctypes.c_int32, ctypes.POINTER(BoxDesc), ctypes.POINTER(_vp)]),
+    "erpp_step_batched": (_st, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
+    "erpp_batch_check": (_st, [_vp, _vp]),
+    "erpp_batch_destroy": (_st, [_vp]),
+    "erpp_fluid_init": (_st, [ctypes.POINTER(Params), ctypes.POINTER(_vp)]),
+    "erpp_fluid_stokes_step": (_st, [_vp, _vp, _vp, _vp]),
+    "erpp_fluid_destroy": (_st, [_vp]),
+    "erpp_scatter_backward": (_st, [_vp, _i64, _dp3, _dp3, _vp, ctypes.POINTER(_dp3),
+                                    ctypes.POINTER(_dp3), _vp]),
+    "erpp_gather_backward": (_st, [_vp, _i64, _dp3, _vp, _dp3, _vp, ctypes.POINTER(_dp3),
+                                   _vp]),
 }
 
 

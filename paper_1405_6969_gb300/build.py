@@ -3,7 +3,8 @@
 Every translation unit under ``csrc/`` is compiled in parallel with nvcc
 (host code with -ffp-contract=off so that the parameter arithmetic matches
 the reference bit for bit), then linked into one shared library with the
-static CUDA runtime.  Usage: ``python -m paper_1405_6969_gb300.build``.
+static CUDA runtime and the toolkit's cuFFT (found beside nvcc, kept in the
+library's run path).  Usage: ``python -m paper_1405_6969_gb300.build``.
 """
 
 from __future__ import annotations
@@ -76,7 +77,10 @@ def build(force=False, verbose=False, ptxas_info=False):
         raise RuntimeError("nvcc failed: " + ", ".join(failed))
     if force or jobs or _stale(OUT, objs):
         tmp = OUT + ".tmp%d" % os.getpid()
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
+        cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))),
+                               "lib64")
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + [
+            "-L" + cudalib, "-lcufft", "-Xlinker", "-rpath," + cudalib]
         subprocess.check_call(cmd)
         os.replace(tmp, OUT)
     return OUT

@@ -59,6 +59,10 @@ void free_scratch(erpp_ctx* c) {
   c->entries_cap = 0;
 }
 
+}  // namespace
+
+namespace erpp {
+
 // Grow the per-particle scratch to hold n particles (synchronous when it
 // grows; the device allocation waits for outstanding work).
 erpp_status ensure_capacity(erpp_ctx* c, int64_t n) {
@@ -85,6 +89,10 @@ erpp_status ensure_capacity(erpp_ctx* c, int64_t n) {
   c->cap = cap;
   return ERPP_OK;
 }
+
+}  // namespace erpp
+
+namespace {
 
 bool valid_vec(const double* const v[3]) { return v && v[0] && v[1] && v[2]; }
 
@@ -290,7 +298,7 @@ erpp_status erpp_interpolate(erpp_ctx* c, const void* u, int64_t n, const double
   if (n == 0) return ERPP_OK;
   if (!valid_vec(x) || !up || !up[0] || !up[1] || !up[2]) return ERPP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  erpp_status s = ensure_capacity(c, n);
+  erpp_status s = erpp::ensure_capacity(c, n);
   if (s) return s;
   cudaError_t e;
   if (c->fp64) {
@@ -319,15 +327,52 @@ erpp_status erpp_scatter_source(erpp_ctx* c, int64_t n, const double* const x[3]
   if (!c || !S || check_n(n)) return ERPP_EINVAL;
   if (n > 0 && (!valid_vec(x) || !valid_vec(D))) return ERPP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  erpp_status s = ensure_capacity(c, n);
+  erpp_status s = erpp::ensure_capacity(c, n);
   if (s) return s;
   cudaError_t e;
   if (c->fp64) {
-    e = erpp::launch_scatter_f64(c, n, x, D, (double*)S, st);
+    e = erpp::launch_scatter_f64(c, n, x, D, -1.0 / c->params.rho_f, (double*)S, st);
   } else {
     e = erpp::bin_particles(c, n, x, false, st);
-    if (e == cudaSuccess) e = erpp::launch_prep_fscat(c, n, D, st);
+    if (e == cudaSuccess) e = erpp::launch_prep_fscat(c, n, D, -c->kp.inv_rho_dV, st);
     if (e == cudaSuccess) e = erpp::launch_scatter_f32(c, (float*)S, st);
+  }
+  return set_cuda_err(e);
+}
+
+erpp_status erpp_scatter_backward(erpp_ctx* c, int64_t n, const double* const x[3],
+                                  const double* const D[3], const void* R, double* const dD[3],
+                                  double* const dx[3], erpp_stream stream) {
+  if (!c || !R || check_n(n)) return ERPP_EINVAL;
+  if (n == 0) return ERPP_OK;
+  if (!valid_vec(x) || !valid_vec(D) || !dx || !dx[0] || !dx[1] || !dx[2]) return ERPP_EINVAL;
+  if (dD && (!dD[0] || !dD[1] || !dD[2])) return ERPP_EINVAL;
+  cudaError_t e = erpp::launch_adjoint(c, n, x, R, D, -1.0 / c->params.rho_f, 0.0, dD, dx,
+                                       (cudaStream_t)stream);
+  return set_cuda_err(e);
+}
+
+erpp_status erpp_gather_backward(erpp_ctx* c, int64_t n, const double* const x[3], const void* u,
+                                 const double* const g[3], void* du, double* const dx[3],
+                                 erpp_stream stream) {
+  if (!c || !u || check_n(n)) return ERPP_EINVAL;
+  if (n > 0 && (!valid_vec(x) || !valid_vec(g))) return ERPP_EINVAL;
+  if (dx && (!dx[0] || !dx[1] || !dx[2])) return ERPP_EINVAL;
+  if (!du && !dx) return ERPP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (dx && n > 0)
+    e = erpp::launch_adjoint(c, n, x, u, g, c->kp.dV, c->params.shear_rate, nullptr, dx, st);
+  if (e == cudaSuccess && du) {
+    erpp_status s = erpp::ensure_capacity(c, n);
+    if (s) return s;
+    if (c->fp64) {
+      e = erpp::launch_scatter_f64(c, n, x, g, c->kp.dV, (double*)du, st);
+    } else {
+      e = erpp::bin_particles(c, n, x, false, st);
+      if (e == cudaSuccess) e = erpp::launch_prep_fscat(c, n, g, 1.0f, st);
+      if (e == cudaSuccess) e = erpp::launch_scatter_f32(c, (float*)du, st);
+    }
   }
   return set_cuda_err(e);
 }
@@ -342,7 +387,7 @@ erpp_status erpp_step(erpp_ctx* c, const void* u, const erpp_particles* P, void*
   }
   const int64_t n = P->n;
   cudaStream_t st = (cudaStream_t)stream;
-  erpp_status s = ensure_capacity(c, n);
+  erpp_status s = erpp::ensure_capacity(c, n);
   if (s) return s;
   const double* const xin[3] = {P->x[0], P->x[1], P->x[2]};
   const double* const xprev[3] = {P->x_prev[0], P->x_prev[1], P->x_prev[2]};
@@ -353,7 +398,8 @@ erpp_status erpp_step(erpp_ctx* c, const void* u, const erpp_particles* P, void*
     e = erpp::launch_gather_f64(c, (const double*)u, n, xin, up, st);
     const double* const upc[3] = {up[0], up[1], up[2]};
     if (e == cudaSuccess) e = erpp::launch_advance(c, P, upc, false, false, first_step, st);
-    if (e == cudaSuccess) e = erpp::launch_scatter_f64(c, n, xprev, Dv, (double*)S, st);
+    if (e == cudaSuccess)
+      e = erpp::launch_scatter_f64(c, n, xprev, Dv, -1.0 / c->params.rho_f, (double*)S, st);
   } else {
     cudaEvent_t* ev = nullptr;
     if (c->prof_on) ev = c->prof_ev + 5 * (c->prof_n++ % kProfSets);

@@ -3,8 +3,8 @@
 // One warp per particle, particles in index order, no binning: the lanes
 // evaluate the per-axis weights of Sec. 2.4's truncated Gaussian in double
 // precision, then walk the flattened window.  The gather reads the grid from
-// global memory; the scatter adds into the (zeroed) grid with FP64 global
-// atomics.  This is the straightforward double-precision implementation the
+// global memory; the scatter adds fscale * D_p W_p(j) (fscale = -1/rho_f for
+// the source) into the zeroed grid with FP64 global atomics.  This is the straightforward double-precision implementation the
 // FP32 tile kernels are measured against.
 #include <cuda_runtime.h>
 
@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_scatter_f64(erpp_kparams kp, in
                                                              const double* __restrict__ D0,
                                                              const double* __restrict__ D1,
                                                              const double* __restrict__ D2,
-                                                             double* S, uint32_t* err) {
+                                                             double fscale, double* S,
+                                                             uint32_t* err) {
   __shared__ double w[kWarps][3][kMaxW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t p = (int64_t)blockIdx.x * kWarps + warp;
@@ -121,8 +122,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_scatter_f64(erpp_kparams kp, in
   }
   __syncwarp();
   if (!ok) return;
-  const double inv_rho = 1.0 / kp.rho_f;
-  const double f[3] = {-inv_rho * D0[p], -inv_rho * D1[p], -inv_rho * D2[p]};
+  const double f[3] = {fscale * D0[p], fscale * D1[p], fscale * D2[p]};
   const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
   const int total = nw[0] * nw[1] * nw[2];
   for (int fi = lane; fi < total; fi += 32) {
@@ -154,15 +154,16 @@ cudaError_t launch_gather_f64(erpp_ctx* ctx, const double* u, int64_t n,
 }
 
 cudaError_t launch_scatter_f64(erpp_ctx* ctx, int64_t n, const double* const x[3],
-                               const double* const D[3], double* S, cudaStream_t st) {
+                               const double* const D[3], double fscale, double* S,
+                               cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;
   size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
   cudaError_t e = cudaMemsetAsync(S, 0, sizeof(double) * 3 * nn, st);
   if (e != cudaSuccess) return e;
   if (n <= 0) return cudaSuccess;
   int blocks = (int)((n + kWarps - 1) / kWarps);
-  k_scatter_f64<<<blocks, kWarps * 32, 0, st>>>(kp, n, x[0], x[1], x[2], D[0], D[1], D[2], S,
-                                                ctx->err);
+  k_scatter_f64<<<blocks, kWarps * 32, 0, st>>>(kp, n, x[0], x[1], x[2], D[0], D[1], D[2],
+                                                fscale, S, ctx->err);
   return cudaGetLastError();
 }
 

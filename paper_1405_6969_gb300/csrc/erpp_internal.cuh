@@ -113,6 +113,7 @@ constexpr int kProfSets = 1024;
 namespace erpp {
 
 erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c);
+erpp_status ensure_capacity(erpp_ctx* c, int64_t n);  // may allocate (synchronous)
 int xw_len(const erpp_kparams& kp);
 cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bool zero_acc,
                           cudaStream_t st);
@@ -120,14 +121,21 @@ cudaError_t launch_gather_f32(erpp_ctx* ctx, const float* u, int64_t n, cudaStre
 cudaError_t launch_scatter_f32(erpp_ctx* ctx, float* S, cudaStream_t st);  // + x-halo merge
 cudaError_t launch_finalize_up(erpp_ctx* ctx, int64_t n, const double* const x[3],
                                double* const up[3], cudaStream_t st);
-cudaError_t launch_prep_fscat(erpp_ctx* ctx, int64_t n, const double* const D[3],
+// fscat_i = scale * norm_i * D_i (scale = -1/(rho_f dV) for the source).
+cudaError_t launch_prep_fscat(erpp_ctx* ctx, int64_t n, const double* const D[3], float scale,
                               cudaStream_t st);
 cudaError_t launch_advance(erpp_ctx* ctx, const erpp_particles* P, const double* const up[3],
                            bool from_acc, bool write_fscat, int first_step, cudaStream_t st);
 cudaError_t launch_gather_f64(erpp_ctx* ctx, const double* u, int64_t n,
                               const double* const x[3], double* const up[3], cudaStream_t st);
 cudaError_t launch_scatter_f64(erpp_ctx* ctx, int64_t n, const double* const x[3],
-                               const double* const D[3], double* S, cudaStream_t st);
+                               const double* const D[3], double fscale, double* S,
+                               cudaStream_t st);
+// Per particle: outv = alpha sum_j F_j W (if outv), outx = alpha sum_j (F_j . v)
+// dW/dx + shear_coef v_x on y.
+cudaError_t launch_adjoint(erpp_ctx* ctx, int64_t n, const double* const x[3], const void* F,
+                           const double* const v[3], double alpha, double shear_coef,
+                           double* const outv[3], double* const outx[3], cudaStream_t st);
 cudaError_t launch_momentum(erpp_ctx* ctx, const void* S, int64_t n, const double* const x[3],
                             const double* const D[3], cudaStream_t st);
 cudaError_t launch_windows(erpp_ctx* ctx, int64_t n, const double* const x[3], int32_t* jlo,

@@ -208,10 +208,10 @@ __global__ void k_finalize_up(erpp_kparams kp, int64_t n, const float* __restric
 __global__ void k_prep_fscat(erpp_kparams kp, int64_t n, const double* __restrict__ D0,
                              const double* __restrict__ D1, const double* __restrict__ D2,
                              const float4* __restrict__ geo_t, const int4* __restrict__ geo_c,
-                             float4* __restrict__ fscat) {
+                             float scale, float4* __restrict__ fscat) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const float s = -erpp_norm(kp, geo_t[i], geo_c[i]) * kp.inv_rho_dV;
+  const float s = erpp_norm(kp, geo_t[i], geo_c[i]) * scale;
   const float f0 = s * (float)D0[i], f1 = s * (float)D1[i], f2 = s * (float)D2[i];
   fscat[i] = make_float4(f0, f1, f2, fmaxf(fabsf(f0), fmaxf(fabsf(f1), fabsf(f2))));
 }
@@ -359,12 +359,12 @@ cudaError_t launch_finalize_up(erpp_ctx* ctx, int64_t n, const double* const x[3
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep_fscat(erpp_ctx* ctx, int64_t n, const double* const D[3],
+cudaError_t launch_prep_fscat(erpp_ctx* ctx, int64_t n, const double* const D[3], float scale,
                               cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int blocks = (int)((n + 255) / 256);
   k_prep_fscat<<<blocks, 256, 0, st>>>(ctx->kp, n, D[0], D[1], D[2], ctx->geo_t, ctx->geo_c,
-                                       ctx->fscat);
+                                       scale, ctx->fscat);
   return cudaGetLastError();
 }
 

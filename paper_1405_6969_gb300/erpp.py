@@ -77,6 +77,28 @@ class ParticleState:
         return P
 
 
+def make_params(params, precision="fp32", normalize=True, self_removal=True, kahan=False):
+    """erpp_params from a parameter dict (n, L, nu, rho_f, eps_R, cutoff, dt,
+    gravity, shear_rate) and the option flags."""
+    p = _lib.Params()
+    p.nx, p.ny, p.nz = (int(v) for v in params["n"])
+    p.Lx, p.Ly, p.Lz = (float(v) for v in params["L"])
+    p.nu, p.rho_f = float(params["nu"]), float(params.get("rho_f", 1.0))
+    p.eps_R, p.cutoff = float(params["eps_R"]), float(params["cutoff"])
+    p.dt = float(params["dt"])
+    p.gravity = (ctypes.c_double * 3)(*[float(g) for g in params.get("gravity", (0, 0, 0))])
+    p.shear_rate = float(params.get("shear_rate", 0.0))
+    flags = {"fp32": _lib.FP32, "fp64": _lib.FP64}[precision]
+    if normalize:
+        flags |= _lib.NORMALIZE
+    if self_removal:
+        flags |= _lib.SELF_REMOVAL
+    if kahan:
+        flags |= _lib.KAHAN
+    p.flags = flags
+    return p
+
+
 class Context:
     """One ERPP context (grid, parameters, scratch) on the current device.
 
@@ -87,22 +109,7 @@ class Context:
     def __init__(self, params, precision="fp32", normalize=True, self_removal=True,
                  kahan=False):
         self.lib = _lib.load()
-        p = _lib.Params()
-        p.nx, p.ny, p.nz = (int(v) for v in params["n"])
-        p.Lx, p.Ly, p.Lz = (float(v) for v in params["L"])
-        p.nu, p.rho_f = float(params["nu"]), float(params.get("rho_f", 1.0))
-        p.eps_R, p.cutoff = float(params["eps_R"]), float(params["cutoff"])
-        p.dt = float(params["dt"])
-        p.gravity = (ctypes.c_double * 3)(*[float(g) for g in params.get("gravity", (0, 0, 0))])
-        p.shear_rate = float(params.get("shear_rate", 0.0))
-        flags = {"fp32": _lib.FP32, "fp64": _lib.FP64}[precision]
-        if normalize:
-            flags |= _lib.NORMALIZE
-        if self_removal:
-            flags |= _lib.SELF_REMOVAL
-        if kahan:
-            flags |= _lib.KAHAN
-        p.flags = flags
+        p = make_params(params, precision, normalize, self_removal, kahan)
         self.params = dict(params)
         self.precision = precision
         self.grid_dtype = torch.float32 if precision == "fp32" else torch.float64
@@ -152,6 +159,28 @@ class Context:
                    "erpp_scatter_source")
         return S
 
+    def scatter_backward(self, x, D, R, need_dD=True, stream=None):
+        """(dL/dD or None, dL/dx) for the cotangent R = dL/dS of the source."""
+        n = x.shape[1]
+        dx = torch.empty((3, n), dtype=torch.float64, device=x.device)
+        dD = torch.empty((3, n), dtype=torch.float64, device=x.device) if need_dD else None
+        pdD = ctypes.byref(_vec3(dD)) if need_dD else None
+        _lib.check(self.lib.erpp_scatter_backward(self._h, n, _vec3(x), _vec3(D), self._grid(R),
+                                                  pdD, ctypes.byref(_vec3(dx)),
+                                                  _stream(stream)), "erpp_scatter_backward")
+        return dD, dx
+
+    def gather_backward(self, x, u, g, need_du=True, need_dx=True, stream=None):
+        """(dL/du or None, dL/dx or None) for the cotangent g = dL/du_p."""
+        n = x.shape[1]
+        du = self.new_grid() if need_du else None
+        dx = torch.empty((3, n), dtype=torch.float64, device=x.device) if need_dx else None
+        pdx = ctypes.byref(_vec3(dx)) if need_dx else None
+        _lib.check(self.lib.erpp_gather_backward(
+            self._h, n, _vec3(x), self._grid(u), _vec3(g),
+            self._grid(du) if need_du else None, pdx, _stream(stream)), "erpp_gather_backward")
+        return du, dx
+
     def step(self, u, state, S=None, first_step=False, stream=None):
         S = self.new_grid() if S is None else S
         P = state.to_c()
@@ -190,3 +219,124 @@ class Context:
                                                ctypes.c_void_p(hi.data_ptr()),
                                                _stream(stream)), "erpp_debug_windows")
         return lo, hi
+
+
+class StokesFluid:
+    """The fluid stand-in (erpp_fluid_*): exact periodic unsteady-Stokes
+    steps forced by the source, u <- exp(-nu k^2 dt) P (u + dt S)."""
+
+    def __init__(self, params, precision="fp32"):
+        self.lib = _lib.load()
+        p = make_params(params, precision)
+        self.grid_dtype = torch.float32 if precision == "fp32" else torch.float64
+        self.shape = (3, p.nz, p.ny, p.nx)
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.erpp_fluid_init(ctypes.byref(p), ctypes.byref(h)), "erpp_fluid_init")
+        self._h = h
+
+    def step(self, u, S, stream=None):
+        for g in (u, S):
+            _require(g, self.grid_dtype, 4)
+            if tuple(g.shape) != self.shape:
+                raise ValueError(f"grid shape {tuple(g.shape)} != {self.shape}")
+        _lib.check(self.lib.erpp_fluid_stokes_step(self._h, ctypes.c_void_p(u.data_ptr()),
+                                                   ctypes.c_void_p(S.data_ptr()),
+                                                   _stream(stream)), "erpp_fluid_stokes_step")
+        return u
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.erpp_fluid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent boxes stepped together (erpp_batch_*).
+
+    boxes: list of (params dict, u grid, ParticleState, S grid); every box
+    uses the same precision and options.  The tensors must stay alive and in
+    place for the batch's lifetime (the batch keeps their addresses)."""
+
+    def __init__(self, boxes, precision="fp32", normalize=True, self_removal=True,
+                 kahan=False):
+        self.lib = _lib.load()
+        dtype = torch.float32 if precision == "fp32" else torch.float64
+        arr = (_lib.BoxDesc * len(boxes))()
+        self._keep = []
+        for i, (params, u, state, S) in enumerate(boxes):
+            shape = (3, int(params["n"][2]), int(params["n"][1]), int(params["n"][0]))
+            for g in (u, S):
+                _require(g, dtype, 4)
+                if tuple(g.shape) != shape:
+                    raise ValueError(f"box {i}: grid shape {tuple(g.shape)} != {shape}")
+            arr[i].params = make_params(params, precision, normalize, self_removal, kahan)
+            arr[i].u = ctypes.c_void_p(u.data_ptr())
+            arr[i].S = ctypes.c_void_p(S.data_ptr())
+            arr[i].particles = state.to_c()
+            self._keep.append((u, state, S))
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.erpp_batch_init(len(boxes), arr, ctypes.byref(h)), "erpp_batch_init")
+        self._h = h
+
+    def step(self, first_step=False, use_graph=True, stream=None):
+        _lib.check(self.lib.erpp_step_batched(self._h, int(bool(first_step)),
+                                              int(bool(use_graph)), _stream(stream)),
+                   "erpp_step_batched")
+
+    def check(self, stream=None):
+        _lib.check(self.lib.erpp_batch_check(self._h, _stream(stream)), "erpp_batch_check")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.erpp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ScatterSource(torch.autograd.Function):
+    """S = source(x, D) (Eq. ns_regularized_filtered) with its hand-written
+    adjoint: ``ScatterSource.apply(ctx, x, D)`` for [3, n] float64 x and D."""
+
+    @staticmethod
+    def forward(fctx, ectx, x, D):
+        fctx.ectx = ectx
+        fctx.save_for_backward(x, D)
+        return ectx.scatter_source(x.detach().contiguous(), D.detach().contiguous())
+
+    @staticmethod
+    def backward(fctx, gS):
+        x, D = fctx.saved_tensors
+        dD, dx = fctx.ectx.scatter_backward(x.detach().contiguous(), D.detach().contiguous(),
+                                            gS.contiguous(),
+                                            need_dD=fctx.needs_input_grad[2])
+        return None, (dx if fctx.needs_input_grad[1] else None), dD
+
+
+class Interpolate(torch.autograd.Function):
+    """u_p = gather(u, x) with its hand-written adjoint:
+    ``Interpolate.apply(ctx, u, x)`` for a grid u and [3, n] float64 x."""
+
+    @staticmethod
+    def forward(fctx, ectx, u, x):
+        fctx.ectx = ectx
+        fctx.save_for_backward(u, x)
+        return ectx.interpolate(u.detach().contiguous(), x.detach().contiguous())
+
+    @staticmethod
+    def backward(fctx, g):
+        u, x = fctx.saved_tensors
+        du, dx = fctx.ectx.gather_backward(x.detach().contiguous(), u.detach().contiguous(),
+                                           g.contiguous(), need_du=fctx.needs_input_grad[1],
+                                           need_dx=fctx.needs_input_grad[2])
+        return None, du, dx
