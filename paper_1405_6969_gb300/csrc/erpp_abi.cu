@@ -225,12 +225,71 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
   kp.plane = kp.pxy * kp.T[2];
   if ((size_t)kp.plane * 6 * sizeof(float) > 227 * 1024) return ERPP_EINVAL;
 
+  kp.design = 3;
+  kp.halo_per_tile = (int64_t)3 * kp.T[2] * kp.T[1] * (kp.xhlo + kp.xhhi);
+  c->maxseg[0] = 1;  // a particle belongs to the x-tile of its home cell
+  for (int a = 1; a < 3; ++a) c->maxseg[a] = max_pieces(n[a], kp.T[a], kp.hlo, kp.xs);
+
+  // Design 4 (FP32, windows of at most 16 nodes in x and y): tiles of
+  // W x 16 x 4 nodes with x- and y-halos, rows and planes 16 (mod 32) floats
+  // apart (see erpp_tiles4.cu); pieces are cut in z only.
+  const int yxs = (int)floor(2.0 * kp.cp[1] + 1e-6) + 1;
+  if (prec == ERPP_FP32 && kp.xxs <= 16 && yxs <= 16) {
+    erpp_kparams k4 = kp;
+    k4.design = 4;
+    k4.yhlo = (int)floor(kp.cp[1]);
+    k4.yhhi = k4.yhlo + 1;
+    const int hx = k4.xhlo + k4.xhhi, hy = k4.yhlo + k4.yhhi;
+    // x: W = 64 nodes (even split instead of a sliver narrower than the halo)
+    k4.T[0] = std::min(64, n[0]);
+    k4.nt[0] = (n[0] + k4.T[0] - 1) / k4.T[0];
+    if (k4.nt[0] > 1 && n[0] - (k4.nt[0] - 1) * k4.T[0] < hmax) {
+      k4.T[0] = (n[0] + k4.nt[0] - 1) / k4.nt[0];
+      k4.nt[0] = (n[0] + k4.T[0] - 1) / k4.T[0];
+    }
+    const int ymax = std::max(k4.yhlo, k4.yhhi);
+    k4.T[1] = std::min(16, n[1]);
+    k4.nt[1] = (n[1] + k4.T[1] - 1) / k4.T[1];
+    if (k4.nt[1] > 1 && n[1] - (k4.nt[1] - 1) * k4.T[1] < ymax) {
+      k4.T[1] = (n[1] + k4.nt[1] - 1) / k4.nt[1];
+      k4.nt[1] = (n[1] + k4.T[1] - 1) / k4.T[1];
+    }
+    const bool ok_x = k4.nt[0] == 1 || n[0] - (k4.nt[0] - 1) * k4.T[0] >= hmax;
+    const bool ok_y = k4.nt[1] == 1 || n[1] - (k4.nt[1] - 1) * k4.T[1] >= ymax;
+    k4.xoff = (k4.xhlo + 3) & ~3;
+    const int need = k4.xoff + k4.T[0] + k4.xhhi;
+    k4.px = ((need + 15) / 32) * 32 + 16;  // >= xoff + W + xhhi, 16 (mod 32)
+    if (k4.px - 32 >= need) k4.px -= 32;
+    k4.pxy = k4.px * (k4.T[1] + hy);
+    if (k4.pxy % 32 != 16) k4.pxy += 16;
+    // z: 4 planes, fewer when the staged tile would not fit
+    const int copies = (p->flags & ERPP_KAHAN) ? 6 : 3;
+    auto smem = [&](int tz) {
+      erpp_kparams t = k4;
+      t.plane = t.pxy * tz;
+      return std::max(erpp::smem_bytes4(t, copies, false), erpp::smem_bytes4(t, 3, true)) +
+             1024;  // + static shared memory
+    };
+    int tz = 4;
+    while (tz > 1 && smem(tz) > 227 * 1024) tz >>= 1;
+    k4.T[2] = std::min(tz, n[2]);
+    k4.nt[2] = (n[2] + k4.T[2] - 1) / k4.T[2];
+    k4.plane = k4.pxy * k4.T[2];
+    const int64_t nt4 = (int64_t)k4.nt[0] * k4.nt[1] * k4.nt[2];
+    const bool fits = smem(k4.T[2]) <= 227 * 1024;
+    if (ok_x && ok_y && fits && nt4 <= (1 << 24) && k4.px <= 128 && k4.T[1] + hy <= 64) {
+      k4.ntiles = (int)nt4;
+      k4.halo_per_tile = (int64_t)3 * k4.T[2] * ((int64_t)(k4.T[1] + hy) * hx + (int64_t)hy * k4.T[0]);
+      kp = k4;
+      c->maxseg[1] = 1;
+      c->maxseg[2] = max_pieces(n[2], kp.T[2], kp.hlo, kp.xs);
+    }
+  }
+
   c->params = *p;
   c->kp = kp;
   c->fp64 = prec == ERPP_FP64;
-  c->maxseg[0] = 1;  // a particle belongs to the x-tile of its home cell
   c->xw_len = erpp::xw_len(kp);
-  for (int a = 1; a < 3; ++a) c->maxseg[a] = max_pieces(n[a], kp.T[a], kp.hlo, kp.xs);
   return ERPP_OK;
 }
 
@@ -255,12 +314,12 @@ erpp_status erpp_init(const erpp_params* p, erpp_ctx** out) {
   if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->red, sizeof(double) * (6 * 304 + 8));
   if (e == cudaSuccess && !c->fp64) {
-    const size_t nbins = (size_t)kp.ntiles * 32;
+    const size_t nbins = (size_t)erpp::nbins(kp);
     e = cudaMalloc(&c->tile_cnt, sizeof(int32_t) * nbins);
     if (e == cudaSuccess) e = cudaMalloc(&c->tile_start, sizeof(int32_t) * (nbins + 1));
     if (e == cudaSuccess) e = cudaMalloc(&c->tile_cursor, sizeof(int32_t) * nbins);
     if (e == cudaSuccess) e = cudaMalloc(&c->scan_tmp, sizeof(int32_t) * (nbins / 4096 + 1));
-    const size_t hb = (size_t)kp.ntiles * 3 * kp.T[2] * kp.T[1] * (kp.xhlo + kp.xhhi);
+    const size_t hb = (size_t)kp.ntiles * (size_t)kp.halo_per_tile;
     if (e == cudaSuccess) e = cudaMalloc(&c->halo, sizeof(float) * hb);
   }
   if (e != cudaSuccess) {

@@ -56,6 +56,24 @@ __device__ __forceinline__ void for_each_piece(const erpp_kparams& kp, int cx, c
   }
 }
 
+// Design 4: the x- and y-tiles are the ones holding the particle's home cell
+// (tiles are staged with x- and y-halos); only the z-window is cut at tile
+// boundaries and periodic images.  Calls f(tile, jz, ez) per piece.
+template <typename F>
+__device__ __forceinline__ void for_each_piece4(const erpp_kparams& kp, const int c[3],
+                                                const int jlo[3], const int nw[3], F f) {
+  const int tx = c[0] / kp.T[0], ty = c[1] / kp.T[1];
+  const int jhz = jlo[2] + nw[2] - 1;
+  for (int jz = jlo[2]; jz <= jhz;) {
+    const int mz = erpp_floordiv(jz, kp.n[2]);
+    const int wz = jz - mz * kp.n[2];
+    const int tz = wz / kp.T[2];
+    const int ez = min(min((tz + 1) * kp.T[2], kp.n[2]) - wz + jz - 1, jhz);
+    f((tz * kp.nt[1] + ty) * kp.nt[0] + tx, jz, ez, wz - tz * kp.T[2]);
+    jz = ez + 1;
+  }
+}
+
 __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict__ x0,
                             const double* __restrict__ x1, const double* __restrict__ x2,
                             float4* __restrict__ geo_t, int4* __restrict__ geo_c,
@@ -126,7 +144,10 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
     }
     xw4[k] = make_float4(v[0], v[1], v[2], v[3]);
   }
-  for_each_piece(kp, c[0], jlo, nw, [&](int bin, const PieceSeg&) { atomicAdd(&tile_cnt[bin], 1); });
+  if (kp.design == 4)
+    for_each_piece4(kp, c, jlo, nw, [&](int tile, int, int, int) { atomicAdd(&tile_cnt[tile], 1); });
+  else
+    for_each_piece(kp, c[0], jlo, nw, [&](int bin, const PieceSeg&) { atomicAdd(&tile_cnt[bin], 1); });
 }
 
 // Writes one record per piece, at its place in the (tile, bucket) order.
@@ -145,6 +166,28 @@ __global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict_
   for (int a = 0; a < 3; ++a) {
     jlo[a] = c[a] + erpp_geo_off(pack, a);
     nw[a] = erpp_geo_nw(pack, a);
+  }
+  if (kp.design == 4) {
+    // record: {p, x0 | y0 << 7 | z0 << 13 | lz << 17 | lx << 22 | ly << 27,
+    //          d0y bits, d0z bits}: x0, y0 the staged x/y index of the
+    // window's first node, z0 its first plane in the tile, lz the planes in
+    // the tile, d0 distances (grid units) of the first y node / first plane
+    const int tx = c[0] / kp.T[0], ty = c[1] / kp.T[1];
+    const int x0 = jlo[0] - (tx * kp.T[0] - kp.xoff);
+    const int y0 = jlo[1] - (ty * kp.T[1] - kp.yhlo);
+    const float d0y = (float)(jlo[1] - c[1]) - gt.y;
+    const uint32_t fixed = (uint32_t)x0 | ((uint32_t)y0 << 7) | ((uint32_t)nw[0] << 22) |
+                           ((uint32_t)nw[1] << 27);
+    for_each_piece4(kp, c, jlo, nw, [&](int tile, int jz, int ez, int z0) {
+      const float d0z = (float)(jz - c[2]) - gt.z;
+      const uint32_t pk = fixed | ((uint32_t)z0 << 13) | ((uint32_t)(ez - jz + 1) << 17);
+      const int pos = atomicAdd(&cursor[tile], 1);
+      if (pos < cap)
+        entries[pos] = make_int4((int)i, (int)pk, __float_as_int(d0y), __float_as_int(d0z));
+      else
+        erpp_set_err(err, ERPP_ERRBIT_BOUNDS);
+    });
+    return;
   }
   for_each_piece(kp, c[0], jlo, nw, [&](int bin, const PieceSeg& sg) {
     const int by = sg.ty * kp.T[1], bz = sg.tz * kp.T[2];
@@ -251,7 +294,7 @@ namespace erpp {
 cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bool zero_acc,
                           cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;
-  const int nbins = kp.ntiles * 32;
+  const int nbins = erpp::nbins(kp);
   cudaError_t e = cudaMemsetAsync(ctx->tile_cnt, 0, sizeof(int32_t) * nbins, st);
   if (e != cudaSuccess) return e;
   if (n > 0) {

@@ -58,6 +58,12 @@ struct erpp_kparams {
   int32_t rows;      // (unused by the lane-per-piece kernels)
   int32_t px, pxy;   // shared-memory pitches (floats) of one tile
   int32_t plane;     // floats per component of one tile = pxy * T_z
+  int32_t design;    // 3: x-halo tiles, pieces cut in y and z (bucket bins);
+                     // 4: x/y-halo tiles, pieces cut in z only, unit schedules
+  int32_t yhlo, yhhi;// design 4: y-halo rows staged below / above a tile
+  int32_t xoff;      // design 4: staged column of the tile's first node
+                     // (xhlo rounded up to a multiple of 4)
+  int64_t halo_per_tile; // design 4: floats of one tile's scatter halo strips
   int32_t normalize, self_removal, kahan;
   double inv_dx[3];  // N / L
   double L[3];
@@ -115,10 +121,14 @@ namespace erpp {
 erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c);
 erpp_status ensure_capacity(erpp_ctx* c, int64_t n);  // may allocate (synchronous)
 int xw_len(const erpp_kparams& kp);
+inline int nbins(const erpp_kparams& kp) { return kp.design == 4 ? kp.ntiles : kp.ntiles * 32; }
 cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bool zero_acc,
                           cudaStream_t st);
 cudaError_t launch_gather_f32(erpp_ctx* ctx, const float* u, int64_t n, cudaStream_t st);
 cudaError_t launch_scatter_f32(erpp_ctx* ctx, float* S, cudaStream_t st);  // + x-halo merge
+cudaError_t launch_gather_f32_4(erpp_ctx* ctx, const float* u, cudaStream_t st);
+size_t smem_bytes4(const erpp_kparams& kp, int copies, bool gather);
+cudaError_t launch_scatter_f32_4(erpp_ctx* ctx, float* S, cudaStream_t st);  // + halo merge
 cudaError_t launch_finalize_up(erpp_ctx* ctx, int64_t n, const double* const x[3],
                                double* const up[3], cudaStream_t st);
 // fscat_i = scale * norm_i * D_i (scale = -1/(rho_f dV) for the source).

@@ -529,6 +529,7 @@ int xw_len(const erpp_kparams& kp) { return variant(kp) <= 1 ? 8 : 16; }
 
 cudaError_t launch_gather_f32(erpp_ctx* ctx, const float* u, int64_t n, cudaStream_t st) {
   (void)n;
+  if (ctx->kp.design == 4) return launch_gather_f32_4(ctx, u, st);
   switch (variant(ctx->kp)) {
     case 0: return gather_xm<7, 6, 8>(ctx, u, st);
     case 1: return gather_xm<7, 5, 8>(ctx, u, st);
@@ -539,6 +540,7 @@ cudaError_t launch_gather_f32(erpp_ctx* ctx, const float* u, int64_t n, cudaStre
 }
 
 cudaError_t launch_scatter_f32(erpp_ctx* ctx, float* S, cudaStream_t st) {
+  if (ctx->kp.design == 4) return launch_scatter_f32_4(ctx, S, st);
   cudaError_t e;
   switch (variant(ctx->kp)) {
     case 0: e = scatter_k<7, 6, 8>(ctx, S, st); break;

@@ -1,0 +1,889 @@
+// erpp_tiles4.cu -- FP32 tile kernels with lockstep unit schedules: the
+// kernel gather and the regularised source scatter (Sec. 2.4, Eq.
+// ns_regularized_filtered; the heat kernel of App. A.1 factored per axis).
+//
+// Tiles.  A thread block owns a tile of W x T_y x T_z nodes and stages it in
+// shared memory with an x-halo (xhlo below, xhhi above) and a y-halo (yhlo,
+// yhhi): every particle whose home cell lies in the tile's x/y range finds its
+// whole x- and y-window there, so a particle's stencil is cut only along z
+// (one "piece" per z-tile it reaches).  Staged layout [3][T_z][NY][PX] with
+// NY = T_y + yhlo + yhhi rows, PX floats per row and the tile's first column
+// at x' = xoff (xhlo rounded up to a multiple of 4, so that the interior is
+// 16-byte aligned); PX and the plane pitch PXY are both 16 (mod 32), so node
+// (x', y', z') sits in shared-memory bank (x' + 16 (y' + z')) mod 32.
+// Staging uses asynchronous global-to-shared copies (16-byte chunks for the
+// aligned interior, 4-byte copies for the halo columns, periodic wrap).
+//
+// Units and buckets.  A unit is one z-plane of a piece: ly rows of lx nodes,
+// the same for every particle (lx, ly = the window lengths).  Walking its rows
+// one per step, a unit's first node moves by 16 banks per row, in step with
+// every other unit walked at the same time, so each unit has a fixed bucket
+//   b = (x0 + 16 (first row + z)) mod 32
+// relative to the others: 32 units with 32 different buckets, processed row
+// by row in lockstep by the 32 lanes of a warp, never share a bank.  A unit
+// may start at its second row and end with its first (a rotation of its
+// rows), which moves it to bucket b ^ 16 (for an even ly without any cost; for
+// an odd ly its last row may share a bank); the schedule gives each unit the
+// less loaded of its two buckets.
+//
+// Schedule.  Per batch of pieces the block builds a table
+// sched[round][warp][lane]: bucket b's k-th unit goes to lane b of warp k mod 8
+// in round k / 8, for R = ceil(units / 256) rounds; units beyond a bucket's 8R
+// slots fill the free slots of other buckets, last rounds first (those lanes
+// then share banks with the slot's own bucket).  Every warp runs its R rounds
+// independently; in a round all lanes walk their units' rows together (the
+// longest window of the round), so a unit switch is a few shared-memory reads
+// per lane.  The batch's piece records and x-weights are staged in shared
+// memory with the schedule.
+//
+// Weights are separable, w = e_x(q) * 2^(-(beta_y d_y^2 + beta_z d_z^2)) with
+// e_x the particle's x-weights (precomputed by the binning), d in grid units.
+//
+// Gather: a lane sums w*u over its unit, adds the three totals to the piece's
+// shared accumulator, and the block adds the piece accumulators to the
+// particle's global accumulator once per batch.
+//
+// Scatter: 32-bit fixed point with shared-memory integer atomics (order
+// independent), per-tile scale 2^30 / B with B = sum over the tile's pieces of
+// max|f| (no sum can overflow).  Per unit G = round(f e_x e_z 2^30 / B) per
+// component and x-slot, per row W = round(e_y 2^31), and each node receives
+// the high word of G W + 2^31 (one wide multiply-add and one atomic per node
+// component).  Tiles with more than 1024 pieces add FP32 values instead, and
+// ERPP_KAHAN adds FP32 values with the exact rounding error of each addition
+// (two-sum on the atomic's old value) kept in a second array.  The interior
+// is written once; the halo strips go to a buffer that k_merge_halo4 adds to
+// the neighbouring tiles in a fixed order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "erpp_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxTz = 4;         // z-planes per tile (units per piece)
+constexpr int kDenseTile = 1024;  // pieces above which a tile accumulates in FP32
+constexpr uint16_t kEmpty = 0xffffu;
+
+// Pieces per batch: smaller batches for the 16-float x-weight records keep
+// two blocks per SM.
+template <int XW>
+struct Batch {
+  static constexpr int kPB = XW <= 8 ? 256 : 128;
+  static constexpr int kUnits = kPB * kMaxTz;
+};
+
+// Piece record (from the binning): p, packed geometry, d0y, d0z.
+struct Piece4 {
+  int p;
+  int x0, y0, z0, lz, lx, ly;
+  float d0y, d0z;
+};
+
+__device__ __forceinline__ Piece4 unpack4(int4 r) {
+  Piece4 pc;
+  pc.p = r.x;
+  const uint32_t v = (uint32_t)r.y;
+  pc.x0 = (int)(v & 127u);
+  pc.y0 = (int)((v >> 7) & 63u);
+  pc.z0 = (int)((v >> 13) & 15u);
+  pc.lz = (int)((v >> 17) & 31u);
+  pc.lx = (int)((v >> 22) & 31u);
+  pc.ly = (int)(v >> 27);
+  pc.d0y = __int_as_float(r.z);
+  pc.d0z = __int_as_float(r.w);
+  return pc;
+}
+
+// ---- asynchronous global -> shared copies (cp.async) ----
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// ---- shared-memory accesses by 32-bit shared address, immediate offsets ----
+__device__ __forceinline__ unsigned shared_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+template <int OFF>
+__device__ __forceinline__ float lds_f32(unsigned a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1+%2];\n" : "=f"(v) : "r"(a), "n"(OFF));
+  return v;
+}
+template <int OFF>
+__device__ __forceinline__ void red_s32(unsigned a, int v) {
+  asm volatile("red.shared.add.s32 [%0+%1], %2;\n" ::"r"(a), "n"(OFF), "r"(v));
+}
+template <int OFF>
+__device__ __forceinline__ void red_f32(unsigned a, float v) {
+  asm volatile("red.shared.add.f32 [%0+%1], %2;\n" ::"r"(a), "n"(OFF), "f"(v));
+}
+template <int OFF>
+__device__ __forceinline__ float atom_f32(unsigned a, float v) {
+  float old;
+  asm volatile("atom.shared.add.f32 %0, [%1+%2], %3;\n" : "=f"(old) : "r"(a), "n"(OFF), "f"(v));
+  return old;
+}
+__device__ __forceinline__ void red_f32_at(unsigned a, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;\n" ::"r"(a), "f"(v));
+}
+
+// round(g w / 2^32) as one 32 x 32 -> 64-bit multiply-add (high word)
+__device__ __forceinline__ int mul_hi_round(int g, int w) {
+  long long r;
+  asm("mad.wide.s32 %0, %1, %2, %3;\n" : "=l"(r) : "r"(g), "r"(w), "l"(0x80000000LL));
+  return (int)(r >> 32);
+}
+
+// One row of a unit, slot Q onwards.  Gather: x_c += e_x(q) u_c(q) over the
+// row (words past the window are selected away, not scaled).  Scatter (fixed
+// point): u_c(q) += high word of G_c(q) W.  Scatter (FP32): u_c(q) += f_c w
+// e_x(q).  a0..a2: shared addresses of the row's first node per component.
+template <int Q, int XM, int LMIN>
+__device__ __forceinline__ void row_dot(unsigned a0, unsigned a1, unsigned a2, const float (&ex)[XM],
+                                        int lx, float& x0, float& x1, float& x2) {
+  if constexpr (Q < XM) {
+    const bool in = Q < LMIN || Q < lx;
+    const float v0 = lds_f32<4 * Q>(a0);
+    const float v1 = lds_f32<4 * Q>(a1);
+    const float v2 = lds_f32<4 * Q>(a2);
+    x0 = fmaf(ex[Q], in ? v0 : 0.f, x0);
+    x1 = fmaf(ex[Q], in ? v1 : 0.f, x1);
+    x2 = fmaf(ex[Q], in ? v2 : 0.f, x2);
+    row_dot<Q + 1, XM, LMIN>(a0, a1, a2, ex, lx, x0, x1, x2);
+  }
+}
+
+template <int Q, int XM, int LMIN>
+__device__ __forceinline__ void row_red_fixed(unsigned a0, unsigned a1, unsigned a2,
+                                              const int (&G0)[XM], const int (&G1)[XM],
+                                              const int (&G2)[XM], int W, int lx) {
+  if constexpr (Q < XM) {
+    if (Q < LMIN || Q < lx) {
+      red_s32<4 * Q>(a0, mul_hi_round(G0[Q], W));
+      red_s32<4 * Q>(a1, mul_hi_round(G1[Q], W));
+      red_s32<4 * Q>(a2, mul_hi_round(G2[Q], W));
+    }
+    row_red_fixed<Q + 1, XM, LMIN>(a0, a1, a2, G0, G1, G2, W, lx);
+  }
+}
+
+template <int Q, int XM, int LMIN>
+__device__ __forceinline__ void row_red_f32(unsigned a0, unsigned a1, unsigned a2,
+                                            const float (&ex)[XM], float f0, float f1, float f2,
+                                            float wy, int lx) {
+  if constexpr (Q < XM) {
+    if (Q < LMIN || Q < lx) {
+      const float wq = wy * ex[Q];
+      red_f32<4 * Q>(a0, f0 * wq);
+      red_f32<4 * Q>(a1, f1 * wq);
+      red_f32<4 * Q>(a2, f2 * wq);
+    }
+    row_red_f32<Q + 1, XM, LMIN>(a0, a1, a2, ex, f0, f1, f2, wy, lx);
+  }
+}
+
+// Compensated: the value the atomic returned gives the exact rounding error
+// of the addition (two-sum), added to the low-order array at offset lo.
+template <int OFF>
+__device__ __forceinline__ void two_sum_add(unsigned a, unsigned lo, float vv) {
+  const float old = atom_f32<OFF>(a, vv);
+  const float s = old + vv;
+  const float bp = s - old;
+  const float err = (old - (s - bp)) + (vv - bp);
+  red_f32<OFF>(lo, err);
+}
+
+template <int Q, int XM, int LMIN>
+__device__ __forceinline__ void row_red_kahan(unsigned a0, unsigned a1, unsigned a2, unsigned lo,
+                                              const float (&ex)[XM], float f0, float f1, float f2,
+                                              float wy, int lx) {
+  if constexpr (Q < XM) {
+    if (Q < LMIN || Q < lx) {
+      const float wq = wy * ex[Q];
+      two_sum_add<4 * Q>(a0, a0 + lo, f0 * wq);
+      two_sum_add<4 * Q>(a1, a1 + lo, f1 * wq);
+      two_sum_add<4 * Q>(a2, a2 + lo, f2 * wq);
+    }
+    row_red_kahan<Q + 1, XM, LMIN>(a0, a1, a2, lo, ex, f0, f1, f2, wy, lx);
+  }
+}
+
+// Dynamic shared memory of one block: the staged field (copies * plane
+// floats), then the batch's records, x-weights, force words (scatter), unit
+// words, schedule and piece accumulators (gather).
+template <int XW>
+struct Carve {
+  float* field;
+  int4* rec;
+  float* xwb;
+  float4* fsb;
+  uint32_t* unit;
+  uint16_t* sched;
+  float* pacc;
+};
+
+template <int XW>
+__host__ __device__ inline size_t carve_bytes(int plane, int copies, bool gather) {
+  constexpr int PB = Batch<XW>::kPB, NU = Batch<XW>::kUnits;
+  size_t b = (size_t)copies * plane * 4;
+  b += (size_t)PB * 16;          // rec
+  b += (size_t)PB * XW * 4;      // xwb
+  if (!gather) b += (size_t)PB * 16;  // fsb
+  b += (size_t)NU * 4;           // unit
+  b += (size_t)NU * 2;           // sched
+  b = (b + 15) & ~(size_t)15;
+  if (gather) b += (size_t)3 * PB * 4;  // pacc
+  return b;
+}
+
+template <int XW>
+__device__ inline Carve<XW> carve(unsigned char* base, int plane, int copies, bool gather) {
+  constexpr int PB = Batch<XW>::kPB, NU = Batch<XW>::kUnits;
+  Carve<XW> c;
+  size_t o = 0;
+  c.field = reinterpret_cast<float*>(base);
+  o += (size_t)copies * plane * 4;
+  c.rec = reinterpret_cast<int4*>(base + o);
+  o += (size_t)PB * 16;
+  c.xwb = reinterpret_cast<float*>(base + o);
+  o += (size_t)PB * XW * 4;
+  c.fsb = reinterpret_cast<float4*>(base + o);
+  if (!gather) o += (size_t)PB * 16;
+  c.unit = reinterpret_cast<uint32_t*>(base + o);
+  o += (size_t)NU * 4;
+  c.sched = reinterpret_cast<uint16_t*>(base + o);
+  o += (size_t)NU * 2;
+  o = (o + 15) & ~(size_t)15;
+  c.pacc = reinterpret_cast<float*>(base + o);
+  return c;
+}
+
+struct SchedState {
+  int cnt[32];
+  int vpre[33];
+  int nunits;
+  int novf;
+};
+
+__device__ __forceinline__ void tile_origin4(const erpp_kparams& kp, int tile, int b[3],
+                                             int ext[3], int t[3]) {
+  const int txy = kp.nt[0] * kp.nt[1];
+  t[2] = tile / txy;
+  const int r = tile - t[2] * txy;
+  t[1] = r / kp.nt[0];
+  t[0] = r - t[1] * kp.nt[0];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    b[a] = t[a] * kp.T[a];
+    ext[a] = min(b[a] + kp.T[a], kp.n[a]) - b[a];
+  }
+}
+
+// Issues the copies that stage the tile with its x/y halo (periodic wrap).
+// Columns outside [xoff - xhlo, xoff + ext_x + xhhi) are never read.
+__device__ void stage_tile4(const erpp_kparams& kp, const float* __restrict__ u, float* field,
+                            const int b[3], const int ext[3]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
+  const int ny_st = ext[1] + kp.yhlo + kp.yhhi;
+  const int hx = kp.xhlo + kp.xhhi;
+  // 16-byte chunks for the interior when rows and tile starts are aligned
+  const bool vec = (kp.n[0] & 3) == 0 && (ext[0] & 3) == 0 && (b[0] & 3) == 0 &&
+                   (((uintptr_t)u) & 15) == 0;
+  const int nvec = vec ? ext[0] >> 2 : 0;
+  const int nscal = (vec ? 0 : ext[0]) + hx;
+  const int jobs = nvec + nscal;
+  for (int c = 0; c < 3; ++c) {
+    for (int z = 0; z < ext[2]; ++z) {
+      const float* gplane = u + c * nn + (size_t)(b[2] + z) * kp.n[1] * kp.n[0];
+      float* splane = field + c * kp.plane + z * kp.pxy;
+      for (int y = warp; y < ny_st; y += kWarps) {
+        int gy = b[1] - kp.yhlo + y;
+        gy = gy < 0 ? gy + kp.n[1] : (gy >= kp.n[1] ? gy - kp.n[1] : gy);
+        const float* grow = gplane + (size_t)gy * kp.n[0];
+        float* srow = splane + y * kp.px;
+        for (int j = lane; j < jobs; j += 32) {
+          if (j < nvec) {
+            cp_async16(srow + kp.xoff + 4 * j, grow + b[0] + 4 * j);
+          } else {
+            const int s = j - nvec;  // scalar job: interior (non-vec) then halo
+            int xl, gx;
+            if (!vec && s < ext[0]) {
+              xl = kp.xoff + s;
+              gx = b[0] + s;
+            } else {
+              const int h = vec ? s : s - ext[0];
+              if (h < kp.xhlo) {
+                xl = kp.xoff - kp.xhlo + h;
+                gx = b[0] - kp.xhlo + h;
+              } else {
+                xl = kp.xoff + ext[0] + (h - kp.xhlo);
+                gx = b[0] + ext[0] + (h - kp.xhlo);
+              }
+              gx = gx < 0 ? gx + kp.n[0] : (gx >= kp.n[0] ? gx - kp.n[0] : gx);
+            }
+            cp_async4(srow + xl, grow + gx);
+          }
+        }
+      }
+    }
+  }
+}
+
+// Builds the unit schedule of pieces [0, np) (records in cv.rec).  Returns
+// the number of rounds.  Called by the whole block; synchronises.
+template <int XW>
+__device__ int build_schedule(const Carve<XW>& cv, SchedState& ss, int np) {
+  const int tid = threadIdx.x;
+  if (tid < 32) ss.cnt[tid] = 0;
+  if (tid == 0) {
+    ss.nunits = 0;
+    ss.novf = 0;
+  }
+  __syncthreads();
+  for (int k = tid; k < np; k += kThreads) {
+    const Piece4 pc = unpack4(cv.rec[k]);
+    const int ub = atomicAdd(&ss.nunits, pc.lz);
+    for (int z = 0; z < pc.lz; ++z) {
+      const int b0 = (pc.x0 + 16 * ((pc.y0 + pc.z0 + z) & 1)) & 31;
+      const int b1 = b0 ^ 16;  // rows rotated by one
+      const uint32_t rot = *((volatile int*)&ss.cnt[b1]) < *((volatile int*)&ss.cnt[b0]) ? 1u : 0u;
+      const int bucket = rot ? b1 : b0;
+      const int slot = atomicAdd(&ss.cnt[bucket], 1);
+      cv.unit[ub + z] = (uint32_t)k | ((uint32_t)z << 10) | ((uint32_t)bucket << 14) |
+                        ((uint32_t)min(slot, 4095) << 19) | (rot << 31);
+    }
+  }
+  __syncthreads();
+  const int U = ss.nunits;
+  const int R = (U + kThreads - 1) / kThreads;
+  const int cap = kWarps * R;
+  if (tid < 32) {
+    const int vac = max(0, cap - ss.cnt[tid]);
+    int incl = vac;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (tid >= o) incl += t;
+    }
+    ss.vpre[tid + 1] = incl;
+    if (tid == 0) ss.vpre[0] = 0;
+  }
+  for (int s = tid; s < R * kThreads; s += kThreads) cv.sched[s] = kEmpty;
+  __syncthreads();
+  for (int u = tid; u < U; u += kThreads) {
+    const uint32_t w = cv.unit[u];
+    int bucket = (int)((w >> 14) & 31u);
+    int slot = (int)((w >> 19) & 4095u);
+    if (slot >= cap) {
+      // overflow: the v-th free slot, free slots of each bucket in order
+      const int v = atomicAdd(&ss.novf, 1);
+      int lo = 0, hi = 32;  // bucket with vpre[b] <= v < vpre[b + 1]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (ss.vpre[mid] <= v) lo = mid; else hi = mid;
+      }
+      bucket = lo;
+      slot = cap - 1 - (v - ss.vpre[lo]);  // latest rounds first
+    }
+    cv.sched[(slot >> 3) * kThreads + (slot & 7) * 32 + bucket] = (uint16_t)u;
+  }
+  __syncthreads();
+  return R;
+}
+
+// Even split of a tile's pieces into batches of at most PB.
+__device__ __forceinline__ int batch_size(int total, int PB) {
+  const int nb = (total + PB - 1) / PB;
+  return (total + nb - 1) / nb;
+}
+
+// Stages the batch's records (and, through the particle index, its
+// x-weights and force words) into shared memory; asynchronous copies.
+template <int XW, bool FORCES>
+__device__ void stage_batch(const Carve<XW>& cv, const int4* __restrict__ entries, int b0, int np,
+                            const float* __restrict__ xw, const float4* __restrict__ fscat) {
+  for (int k = threadIdx.x; k < np; k += kThreads) {
+    const int4 r = __ldg(&entries[b0 + k]);
+    cv.rec[k] = r;
+    const float* src = xw + (size_t)r.x * XW;
+#pragma unroll
+    for (int j = 0; j < XW / 4; ++j) cp_async16(cv.xwb + k * XW + 4 * j, src + 4 * j);
+    if (FORCES) cp_async16(cv.fsb + k, fscat + r.x);
+  }
+}
+
+// One unit of a round: rows visited from row `rot` on, wrapping once.
+struct UnitRows {
+  int base;    // shared index of the unit's first node (row 0)
+  int ly, lx;
+  int rot;
+  float d0y, ezz;
+};
+
+// XM: longest x-window; LMIN: shortest (slots q >= LMIN are tested); XW:
+// x-weights stored per particle.
+template <int XM, int LMIN, int XW>
+__global__ void __launch_bounds__(kThreads, 2) k_gather4(
+    erpp_kparams kp, const float* __restrict__ u, const int32_t* __restrict__ start,
+    const int4* __restrict__ entries, int64_t ecap, const float* __restrict__ xw,
+    float* __restrict__ up_acc, int64_t acc_stride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SchedState ss;
+  constexpr int PB = Batch<XW>::kPB;
+  const int tile = blockIdx.x;
+  const int e0 = start[tile];
+  const int e1 = (int)min((int64_t)start[tile + 1], ecap);
+  if (e0 >= e1) return;
+  const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, 3, true);
+  int b[3], ext[3], tt[3];
+  tile_origin4(kp, tile, b, ext, tt);
+  stage_tile4(kp, u, cv.field, b, ext);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int plane = kp.plane, px = kp.px, pxy = kp.pxy;
+  const float by = kp.beta[1], bz = kp.beta[2];
+  const unsigned fbase = shared_addr(cv.field), pbase = shared_addr(cv.pacc);
+  const int bs = batch_size(e1 - e0, PB);
+  for (int b0 = e0; b0 < e1; b0 += bs) {
+    const int np = min(bs, e1 - b0);
+    stage_batch<XW, false>(cv, entries, b0, np, xw, nullptr);
+    for (int k = threadIdx.x; k < 3 * PB; k += kThreads) cv.pacc[k] = 0.f;
+    const int R = build_schedule<XW>(cv, ss, np);  // synchronises
+    cp_async_wait_all();                            // field (first batch), x-weights
+    __syncthreads();
+    for (int r = 0; r < R; ++r) {
+      const uint16_t ui = cv.sched[r * kThreads + warp * 32 + lane];
+      const bool active = ui != kEmpty;
+      UnitRows ur = {0, 0, 0, 0, 0.f, 0.f};
+      int k = 0;
+      float ex[XM];
+#pragma unroll
+      for (int q = 0; q < XM; ++q) ex[q] = 0.f;
+      if (active) {
+        const uint32_t w = cv.unit[ui];
+        k = (int)(w & 1023u);
+        const int z = (int)((w >> 10) & 15u);
+        const Piece4 pc = unpack4(cv.rec[k]);
+        const float4* xs = reinterpret_cast<const float4*>(cv.xwb + k * XW);
+#pragma unroll
+        for (int j = 0; j < (XM + 3) / 4; ++j) {
+          const float4 v = xs[j];
+          if (4 * j < XM) ex[4 * j] = v.x;
+          if (4 * j + 1 < XM) ex[4 * j + 1] = v.y;
+          if (4 * j + 2 < XM) ex[4 * j + 2] = v.z;
+          if (4 * j + 3 < XM) ex[4 * j + 3] = v.w;
+        }
+        ur.base = (pc.z0 + z) * pxy + pc.y0 * px + pc.x0;
+        ur.ly = pc.ly;
+        ur.lx = pc.lx;
+        ur.rot = (int)(w >> 31);
+        ur.d0y = pc.d0y;
+        const float dz = pc.d0z + (float)z;
+        ur.ezz = bz * dz * dz;
+      }
+      const int rows = __reduce_max_sync(0xffffffffu, (unsigned)ur.ly);
+      // Straight-line rows: rows past the unit's own length get weight 0,
+      // the rotated walk wraps by a select.  Empty lanes read from column
+      // `lane` (their own bucket) and their sums are dropped.
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      const unsigned pl4 = 4u * (unsigned)plane, px4 = 4u * (unsigned)px;
+      const unsigned abase = fbase + 4u * (unsigned)(active ? ur.base : lane);
+      const unsigned aend = abase + px4 * (unsigned)ur.ly;
+      unsigned ar = abase + px4 * (unsigned)ur.rot;
+      float dy = ur.d0y + (float)ur.rot;
+#pragma unroll 1
+      for (int t = 0; t < rows; ++t) {
+        const float e = exp2f(-fmaf(by * dy, dy, ur.ezz));
+        const float wr = t < ur.ly ? e : 0.f;
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+        row_dot<0, XM, LMIN>(ar, ar + pl4, ar + 2 * pl4, ex, ur.lx, x0, x1, x2);
+        a0 = fmaf(wr, x0, a0);
+        a1 = fmaf(wr, x1, a1);
+        a2 = fmaf(wr, x2, a2);
+        ar += px4;
+        dy += 1.f;
+        const bool wrap = ar == aend;
+        ar = wrap ? abase : ar;
+        dy = wrap ? ur.d0y : dy;
+      }
+      if (active) {
+        const unsigned pa = pbase + 4u * (unsigned)k;
+        red_f32_at(pa, a0);
+        red_f32_at(pa + 4u * PB, a1);
+        red_f32_at(pa + 8u * PB, a2);
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < np; k += kThreads) {
+      const int p = cv.rec[k].x;
+      atomicAdd(up_acc + p, cv.pacc[k]);
+      atomicAdd(up_acc + acc_stride + p, cv.pacc[PB + k]);
+      atomicAdd(up_acc + 2 * acc_stride + p, cv.pacc[2 * PB + k]);
+    }
+    __syncthreads();
+  }
+}
+
+// MODE 0: fixed point (FP32 atomics on dense tiles); MODE 1: compensated FP32.
+template <int XM, int LMIN, int XW, int MODE>
+__global__ void __launch_bounds__(kThreads, 2) k_scatter4(
+    erpp_kparams kp, float* __restrict__ S, float* __restrict__ halo,
+    const int32_t* __restrict__ start, const int4* __restrict__ entries, int64_t ecap,
+    const float* __restrict__ xw, const float4* __restrict__ fscat) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SchedState ss;
+  __shared__ float red[kWarps];
+  constexpr int PB = Batch<XW>::kPB;
+  const int tile = blockIdx.x;
+  const int e0 = start[tile];
+  const int e1 = (int)min((int64_t)start[tile + 1], ecap);
+  const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, MODE == 1 ? 6 : 3, false);
+  float* smem = cv.field;
+  int b[3], ext[3], tt[3];
+  tile_origin4(kp, tile, b, ext, tt);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int plane = kp.plane, px = kp.px, pxy = kp.pxy;
+  const bool any = e0 < e1;
+  const bool fixedp = MODE == 0 && (e1 - e0) <= kDenseTile;
+  float scale = 1.f, inv_scale = 1.f;
+  int* acc_i = reinterpret_cast<int*>(smem);
+  float* comp_lo = smem + 3 * plane;
+  if (any) {
+    const int total = (MODE == 1 ? 6 : 3) * plane;
+    float4* s4 = reinterpret_cast<float4*>(smem);
+    for (int k = threadIdx.x; k < total / 4; k += kThreads) s4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (fixedp) {
+      float bsum = 0.f;
+      for (int e = e0 + threadIdx.x; e < e1; e += kThreads)
+        bsum += __ldg(&fscat[__ldg(&entries[e].x)]).w;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+      if (lane == 0) red[warp] = bsum;
+    }
+    __syncthreads();
+    if (fixedp) {
+      float B = 0.f;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) B += red[w];
+      if (B > 0.f) {
+        int ex2;
+        frexpf(B, &ex2);  // B = m 2^ex2, m in [0.5, 1)
+        const int sh = min(30 - ex2, 120);
+        scale = ldexpf(1.f, sh);
+        // node sums are in units of scale / 2 (the row weight carries 2^31,
+        // the high word drops 2^32)
+        inv_scale = ldexpf(2.f, -sh);
+      }
+    }
+    const float by = kp.beta[1], bz = kp.beta[2];
+    const unsigned fbase = shared_addr(smem);
+    const int bs = batch_size(e1 - e0, PB);
+    for (int b0 = e0; b0 < e1; b0 += bs) {
+      const int np = min(bs, e1 - b0);
+      stage_batch<XW, true>(cv, entries, b0, np, xw, fscat);
+      const int R = build_schedule<XW>(cv, ss, np);  // synchronises
+      cp_async_wait_all();
+      __syncthreads();
+      for (int r = 0; r < R; ++r) {
+        const uint16_t ui = cv.sched[r * kThreads + warp * 32 + lane];
+        const bool active = ui != kEmpty;
+        UnitRows ur = {0, 0, 0, 0, 0.f, 0.f};
+        float ex[XM];
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+        int G0[XM], G1[XM], G2[XM];
+#pragma unroll
+        for (int q = 0; q < XM; ++q) {
+          ex[q] = 0.f;
+          G0[q] = G1[q] = G2[q] = 0;
+        }
+        if (active) {
+          const uint32_t w = cv.unit[ui];
+          const int k = (int)(w & 1023u);
+          const int z = (int)((w >> 10) & 15u);
+          const Piece4 pc = unpack4(cv.rec[k]);
+          const float4* xs = reinterpret_cast<const float4*>(cv.xwb + k * XW);
+#pragma unroll
+          for (int j = 0; j < (XM + 3) / 4; ++j) {
+            const float4 v = xs[j];
+            if (4 * j < XM) ex[4 * j] = v.x;
+            if (4 * j + 1 < XM) ex[4 * j + 1] = v.y;
+            if (4 * j + 2 < XM) ex[4 * j + 2] = v.z;
+            if (4 * j + 3 < XM) ex[4 * j + 3] = v.w;
+          }
+          ur.base = (pc.z0 + z) * pxy + pc.y0 * px + pc.x0;
+          ur.ly = pc.ly;
+          ur.lx = pc.lx;
+          ur.rot = (int)(w >> 31);
+          ur.d0y = pc.d0y;
+          const float dz = pc.d0z + (float)z;
+          const float wz = exp2f(-bz * dz * dz);
+          const float4 fv = cv.fsb[k];
+          f0 = fv.x * wz;
+          f1 = fv.y * wz;
+          f2 = fv.z * wz;
+          if (MODE == 0 && fixedp) {
+#pragma unroll
+            for (int q = 0; q < XM; ++q) {
+              G0[q] = __float2int_rn(f0 * scale * ex[q]);
+              G1[q] = __float2int_rn(f1 * scale * ex[q]);
+              G2[q] = __float2int_rn(f2 * scale * ex[q]);
+            }
+          }
+        }
+        const int rows = __reduce_max_sync(0xffffffffu, (unsigned)ur.ly);
+        // Rows as in the gather: straight line, weight 0 past the unit's
+        // length, rotated walk wrapping by a select; empty lanes add zeros at
+        // column `lane` (their own bucket).  Slots past the window are skipped.
+        const unsigned pl4 = 4u * (unsigned)plane, px4 = 4u * (unsigned)px;
+        const unsigned abase = fbase + 4u * (unsigned)(active ? ur.base : lane);
+        const unsigned aend = abase + px4 * (unsigned)ur.ly;
+        unsigned ar = abase + px4 * (unsigned)ur.rot;
+        float dy = ur.d0y + (float)ur.rot;
+        if (MODE == 0 && fixedp) {
+#pragma unroll 1
+          for (int t = 0; t < rows; ++t) {
+            const float e = exp2f(-by * dy * dy);
+            const int W = t < ur.ly ? __float2int_rn(e * 2147483648.f) : 0;
+            row_red_fixed<0, XM, LMIN>(ar, ar + pl4, ar + 2 * pl4, G0, G1, G2, W, ur.lx);
+            ar += px4;
+            dy += 1.f;
+            const bool wrap = ar == aend;
+            ar = wrap ? abase : ar;
+            dy = wrap ? ur.d0y : dy;
+          }
+        } else if (MODE == 0) {
+#pragma unroll 1
+          for (int t = 0; t < rows; ++t) {
+            const float e = exp2f(-by * dy * dy);
+            const float wy = t < ur.ly ? e : 0.f;
+            row_red_f32<0, XM, LMIN>(ar, ar + pl4, ar + 2 * pl4, ex, f0, f1, f2, wy, ur.lx);
+            ar += px4;
+            dy += 1.f;
+            const bool wrap = ar == aend;
+            ar = wrap ? abase : ar;
+            dy = wrap ? ur.d0y : dy;
+          }
+        } else {
+          const unsigned lo = 3u * pl4;  // the low-order array follows the three components
+#pragma unroll 1
+          for (int t = 0; t < rows; ++t) {
+            const float e = exp2f(-by * dy * dy);
+            const float wy = t < ur.ly ? e : 0.f;
+            row_red_kahan<0, XM, LMIN>(ar, ar + pl4, ar + 2 * pl4, lo, ex, f0, f1, f2, wy,
+                                       ur.lx);
+            ar += px4;
+            dy += 1.f;
+            const bool wrap = ar == aend;
+            ar = wrap ? abase : ar;
+            dy = wrap ? ur.d0y : dy;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // interior once (zeros for empty tiles); halo strips to the buffer:
+  // x-strips [3][T_z][T_y + hy][hx] (all staged rows), y-strips [3][T_z][hy][W]
+  const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
+  const int hx = kp.xhlo + kp.xhhi, hy = kp.yhlo + kp.yhhi;
+  const int ny_st = ext[1] + hy;
+  const int width = ext[0] + hx;
+  const int x_lo = kp.xoff - kp.xhlo;  // first staged column used
+  float* hxs = halo + (size_t)tile * kp.halo_per_tile;
+  float* hys = hxs + 3 * kp.T[2] * (kp.T[1] + hy) * hx;
+  for (int cc = 0; cc < 3; ++cc) {
+    for (int z = 0; z < ext[2]; ++z) {
+      for (int y = warp; y < ny_st; y += kWarps) {
+        const int so = cc * plane + z * pxy + y * px + x_lo;
+        const bool yint = y >= kp.yhlo && y < kp.yhlo + ext[1];
+        float* dst = S + cc * nn + ((size_t)(b[2] + z) * kp.n[1] + (b[1] + y - kp.yhlo)) * kp.n[0] +
+                     b[0];
+        float* xrow = hxs + (((size_t)cc * kp.T[2] + z) * (kp.T[1] + hy) + y) * hx;
+        const int yh = y < kp.yhlo ? y : y - ext[1];  // y-strip row when !yint
+        float* yrow = hys + (((size_t)cc * kp.T[2] + z) * hy + yh) * kp.T[0];
+        for (int xx = lane; xx < width; xx += 32) {
+          float val = 0.f;
+          if (any) {
+            if (MODE == 1)
+              val = smem[so + xx] + smem[3 * plane + so + xx];
+            else if (fixedp)
+              val = (float)acc_i[so + xx] * inv_scale;
+            else
+              val = smem[so + xx];
+          }
+          const bool xint = xx >= kp.xhlo && xx < kp.xhlo + ext[0];
+          if (xint && yint)
+            dst[xx - kp.xhlo] = val;
+          else if (!xint)
+            xrow[xx < kp.xhlo ? xx : xx - ext[0]] = val;
+          else
+            yrow[xx - kp.xhlo] = val;
+        }
+      }
+    }
+  }
+}
+
+// Adds the scatter's halo strips onto the tiles they belong to, in a fixed
+// order (deterministic): interior node (x, y) of a tile receives from the
+// x-neighbours' x-strips (same rows), the y-neighbours' y-strips (same
+// columns) and the diagonal neighbours' x-strips in their y-halo rows;
+// periodic in x and y.  One block per (tile, component, plane); only the rim
+// nodes (within xhhi / xhlo columns or yhhi / yhlo rows of the tile's edges)
+// are visited: whole rim rows, then the rim columns of the other rows.
+constexpr int kMergeThreads = 128;
+
+__global__ void __launch_bounds__(kMergeThreads) k_merge_halo4(erpp_kparams kp,
+                                                               float* __restrict__ S,
+                                                               const float* __restrict__ halo) {
+  const int hx = kp.xhlo + kp.xhhi, hy = kp.yhlo + kp.yhhi;
+  const int W = kp.T[0], Ty = kp.T[1];
+  const int tile = blockIdx.x;
+  const int cz = blockIdx.y;  // component * T_z + plane
+  int b[3], ext[3], t[3];
+  tile_origin4(kp, tile, b, ext, t);
+  const int z = cz % kp.T[2];
+  const int cc = cz / kp.T[2];
+  if (z >= ext[2]) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int nwarps = kMergeThreads / 32;
+  const int txy = kp.nt[0] * kp.nt[1];
+  const int txl = t[0] == 0 ? kp.nt[0] - 1 : t[0] - 1;
+  const int txr = t[0] == kp.nt[0] - 1 ? 0 : t[0] + 1;
+  const int tyl = t[1] == 0 ? kp.nt[1] - 1 : t[1] - 1;
+  const int tyr = t[1] == kp.nt[1] - 1 ? 0 : t[1] + 1;
+  auto tid = [&](int ax, int ay) { return (ay * kp.nt[0] + ax) + t[2] * txy; };
+  const int exty_l = min((tyl + 1) * Ty, kp.n[1]) - tyl * Ty;
+  // strips of this (component, plane) in each neighbour's halo block
+  const size_t xs0 = (size_t)cz * (Ty + hy) * hx;
+  const size_t ys0 = (size_t)3 * kp.T[2] * (Ty + hy) * hx + (size_t)cz * hy * W;
+  auto base = [&](int id) { return halo + (size_t)id * kp.halo_per_tile; };
+  const float* xL = base(tid(txl, t[1])) + xs0;   // right strip of the left tile
+  const float* xR = base(tid(txr, t[1])) + xs0;   // left strip of the right tile
+  const float* yB = base(tid(t[0], tyl)) + ys0;   // top strip of the lower tile
+  const float* yT = base(tid(t[0], tyr)) + ys0;   // bottom strip of the upper tile
+  const float* xLB = base(tid(txl, tyl)) + xs0;
+  const float* xRB = base(tid(txr, tyl)) + xs0;
+  const float* xLT = base(tid(txl, tyr)) + xs0;
+  const float* xRT = base(tid(txr, tyr)) + xs0;
+  const int xcut = ext[0] - kp.xhlo, ycut = ext[1] - kp.yhlo;
+  const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
+  float* splane = S + cc * nn + (size_t)(b[2] + z) * kp.n[1] * kp.n[0];
+  auto node = [&](int x, int y) {
+    const bool xl = x < kp.xhhi, xr = x >= xcut;
+    const bool yl = y < kp.yhhi, yr = y >= ycut;
+    float add = 0.f;
+    if (xl) add += xL[(y + kp.yhlo) * hx + kp.xhlo + x];
+    if (xr) add += xR[(y + kp.yhlo) * hx + x - xcut];
+    if (yl) add += yB[(kp.yhlo + y) * W + x];
+    if (yr) add += yT[(y - ycut) * W + x];
+    if (xl && yl) add += xLB[(exty_l + kp.yhlo + y) * hx + kp.xhlo + x];
+    if (xr && yl) add += xRB[(exty_l + kp.yhlo + y) * hx + x - xcut];
+    if (xl && yr) add += xLT[(y - ycut) * hx + kp.xhlo + x];
+    if (xr && yr) add += xRT[(y - ycut) * hx + x - xcut];
+    splane[(size_t)(b[1] + y) * kp.n[0] + b[0] + x] += add;
+  };
+  // rim rows (all rows when the tile is no taller than the halo)
+  const bool allrows = ext[1] < hy;
+  const int nrim = allrows ? ext[1] : hy;
+  for (int rr = warp; rr < nrim; rr += nwarps) {
+    const int y = allrows || rr < kp.yhhi ? rr : ycut + (rr - kp.yhhi);
+    for (int x = lane; x < ext[0]; x += 32) node(x, y);
+  }
+  if (allrows) return;
+  // rim columns of the remaining rows
+  const bool allcols = ext[0] < hx;
+  const int ncol = allcols ? ext[0] : hx;
+  for (int y = kp.yhhi + warp; y < ycut; y += nwarps)
+    for (int j = lane; j < ncol; j += 32)
+      node(allcols || j < kp.xhhi ? j : xcut + (j - kp.xhhi), y);
+}
+
+template <int XM, int LMIN, int XW>
+cudaError_t gather4(erpp_ctx* ctx, const float* u, cudaStream_t st) {
+  const erpp_kparams& kp = ctx->kp;
+  const size_t sm = carve_bytes<XW>(kp.plane, 3, true);
+  cudaError_t e = cudaFuncSetAttribute(k_gather4<XM, LMIN, XW>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_gather4<XM, LMIN, XW><<<kp.ntiles, kThreads, sm, st>>>(
+      kp, u, ctx->tile_start, ctx->entries, ctx->entries_cap, ctx->xw, ctx->up_acc, ctx->cap);
+  return cudaGetLastError();
+}
+
+template <int XM, int LMIN, int XW, int MODE>
+cudaError_t scatter4_mode(erpp_ctx* ctx, float* S, cudaStream_t st) {
+  const erpp_kparams& kp = ctx->kp;
+  const size_t sm = carve_bytes<XW>(kp.plane, MODE == 1 ? 6 : 3, false);
+  cudaError_t e = cudaFuncSetAttribute(k_scatter4<XM, LMIN, XW, MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_scatter4<XM, LMIN, XW, MODE><<<kp.ntiles, kThreads, sm, st>>>(
+      kp, S, ctx->halo, ctx->tile_start, ctx->entries, ctx->entries_cap, ctx->xw, ctx->fscat);
+  return cudaGetLastError();
+}
+
+template <int XM, int LMIN, int XW>
+cudaError_t scatter4(erpp_ctx* ctx, float* S, cudaStream_t st) {
+  return ctx->kp.kahan ? scatter4_mode<XM, LMIN, XW, 1>(ctx, S, st)
+                       : scatter4_mode<XM, LMIN, XW, 0>(ctx, S, st);
+}
+
+}  // namespace
+
+namespace erpp {
+
+// Window-length variants of the unit-schedule kernels: x-windows of 6-7 nodes
+// (cutoff 3 sigma_R at sigma_R = dx; 5-7 when rounding leaves c' just below 3)
+// and 9-10 nodes (sigma_R = 1.5 dx), else a generic form testing every slot.
+int variant4(const erpp_kparams& kp) {
+  if (kp.xxs <= 7 && kp.xlmin >= 6) return 0;
+  if (kp.xxs <= 7 && kp.xlmin >= 5) return 1;
+  if (kp.xxs <= 10 && kp.xlmin >= 9) return 2;
+  if (kp.xxs <= 10 && kp.xlmin >= 8) return 3;
+  return 4;
+}
+
+// Dynamic shared memory of the design-4 kernels (host side of the carve).
+size_t smem_bytes4(const erpp_kparams& kp, int copies, bool gather) {
+  return kp.xxs <= 8 ? carve_bytes<8>(kp.plane, copies, gather)
+                     : carve_bytes<16>(kp.plane, copies, gather);
+}
+
+cudaError_t launch_gather_f32_4(erpp_ctx* ctx, const float* u, cudaStream_t st) {
+  switch (variant4(ctx->kp)) {
+    case 0: return gather4<7, 6, 8>(ctx, u, st);
+    case 1: return gather4<7, 5, 8>(ctx, u, st);
+    case 2: return gather4<10, 9, 16>(ctx, u, st);
+    case 3: return gather4<10, 8, 16>(ctx, u, st);
+    default: return gather4<16, 1, 16>(ctx, u, st);
+  }
+}
+
+cudaError_t launch_scatter_f32_4(erpp_ctx* ctx, float* S, cudaStream_t st) {
+  cudaError_t e;
+  switch (variant4(ctx->kp)) {
+    case 0: e = scatter4<7, 6, 8>(ctx, S, st); break;
+    case 1: e = scatter4<7, 5, 8>(ctx, S, st); break;
+    case 2: e = scatter4<10, 9, 16>(ctx, S, st); break;
+    case 3: e = scatter4<10, 8, 16>(ctx, S, st); break;
+    default: e = scatter4<16, 1, 16>(ctx, S, st); break;
+  }
+  if (e != cudaSuccess) return e;
+  k_merge_halo4<<<dim3(ctx->kp.ntiles, 3 * ctx->kp.T[2]), kMergeThreads, 0, st>>>(ctx->kp, S,
+                                                                                 ctx->halo);
+  return cudaGetLastError();
+}
+
+}  // namespace erpp

@@ -63,6 +63,9 @@ CASES = [
     # nodes), two x-tiles of 64 and 8 nodes
     ("iso_72x40x20", rep(I.CFG_SMALL, n=(72, 40, 20), kmax=3.0,
                          L=(2 * math.pi, 2 * math.pi * 40 / 72, 2 * math.pi * 20 / 72)), 3000),
+    # y spacing a third of x: y-windows of 19 nodes, beyond the x/y-halo tiles
+    # (the kernels cut pieces in y and z instead)
+    ("fine_y_32x96x24", rep(I.CFG_SMALL, n=(32, 96, 24), kmax=3.0), 1500),
 ]
 
 
