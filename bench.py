@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kahan", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default tile shape instead of timing the candidates")
     ap.add_argument("--no-loop", action="store_true",
                     help="skip the closed-loop (coupling + fluid stand-in) timing")
     ap.add_argument("--workload", default="shear", choices=["shear", "cube256", "batched64"],
@@ -319,6 +321,13 @@ def main():
     nodes_per_step = 2 * stencil_nodes(st.x, w)
     stream = torch.cuda.current_stream()
 
+    # tile shape: time the candidates on this workload (a few steps each, on
+    # copies of the particle state) and keep the fastest
+    tiling = {"tiling": ctx.tiling()}
+    if not args.no_autotune:
+        from paper_1405_6969_gb300 import autotune
+        tiling = autotune.tune(ctx, u, ps, S=S, use_cache=False)
+
     # warm-up (the first step has no previous force to remove)
     for k in range(args.warmup):
         ctx.step(u, ps, S=S, first_step=(k == 0))
@@ -459,6 +468,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "coupled_loop": loop,
+            "tiling": tiling,
             "e2e": e2e,
             # bin count, three scan kernels, bin fill, gather, advance, scatter,
             # halo merge

@@ -96,6 +96,20 @@ namespace {
 
 bool valid_vec(const double* const v[3]) { return v && v[0] && v[1] && v[2]; }
 
+// Tile tables and scatter halo of the FP32 path, for the context's geometry.
+erpp_status alloc_tile_tables(erpp_ctx* c) {
+  if (c->fp64) return ERPP_OK;
+  const erpp_kparams& kp = c->kp;
+  const size_t nbins = (size_t)erpp::nbins(kp);
+  cudaError_t e = cudaMalloc(&c->tile_cnt, sizeof(int32_t) * nbins);
+  if (e == cudaSuccess) e = cudaMalloc(&c->tile_start, sizeof(int32_t) * (nbins + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&c->tile_cursor, sizeof(int32_t) * nbins);
+  if (e == cudaSuccess) e = cudaMalloc(&c->scan_tmp, sizeof(int32_t) * (nbins / 4096 + 1));
+  const size_t hb = (size_t)kp.ntiles * (size_t)kp.halo_per_tile;
+  if (e == cudaSuccess) e = cudaMalloc(&c->halo, sizeof(float) * hb);
+  return set_cuda_err(e);
+}
+
 erpp_status check_n(int64_t n) {
   if (n < 0 || n > ERPP_MAX_PARTICLES) return ERPP_EINVAL;
   return ERPP_OK;
@@ -240,20 +254,26 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
     k4.yhlo = (int)floor(kp.cp[1]);
     k4.yhhi = k4.yhlo + 1;
     const int hx = k4.xhlo + k4.xhhi, hy = k4.yhlo + k4.yhhi;
-    // x: W = 64 nodes (even split instead of a sliver narrower than the halo)
-    k4.T[0] = std::min(64, n[0]);
-    k4.nt[0] = (n[0] + k4.T[0] - 1) / k4.T[0];
-    if (k4.nt[0] > 1 && n[0] - (k4.nt[0] - 1) * k4.T[0] < hmax) {
-      k4.T[0] = (n[0] + k4.nt[0] - 1) / k4.nt[0];
-      k4.nt[0] = (n[0] + k4.T[0] - 1) / k4.T[0];
-    }
+    // Tile widths: the requested size (x: 64), raised to the halo depth so
+    // that halo strips reach only the neighbouring tiles; a last (ragged) tile
+    // thinner than that becomes an even split, else the tiles grow.
+    auto split = [&](int want, int n_axis, int depth, int* T, int* nt) {
+      int t = std::min(std::max(want, depth), n_axis);
+      int m = (n_axis + t - 1) / t;
+      if (m > 1 && n_axis - (m - 1) * t < depth) {
+        t = (n_axis + m - 1) / m;
+        m = (n_axis + t - 1) / t;
+      }
+      while (m > 1 && n_axis - (m - 1) * t < depth) {
+        ++t;
+        m = (n_axis + t - 1) / t;
+      }
+      *T = t;
+      *nt = m;
+    };
     const int ymax = std::max(k4.yhlo, k4.yhhi);
-    k4.T[1] = std::min(16, n[1]);
-    k4.nt[1] = (n[1] + k4.T[1] - 1) / k4.T[1];
-    if (k4.nt[1] > 1 && n[1] - (k4.nt[1] - 1) * k4.T[1] < ymax) {
-      k4.T[1] = (n[1] + k4.nt[1] - 1) / k4.nt[1];
-      k4.nt[1] = (n[1] + k4.T[1] - 1) / k4.T[1];
-    }
+    split(64, n[0], hmax, &k4.T[0], &k4.nt[0]);
+    split(c->tile_req[0] > 0 ? c->tile_req[0] : 16, n[1], ymax, &k4.T[1], &k4.nt[1]);
     const bool ok_x = k4.nt[0] == 1 || n[0] - (k4.nt[0] - 1) * k4.T[0] >= hmax;
     const bool ok_y = k4.nt[1] == 1 || n[1] - (k4.nt[1] - 1) * k4.T[1] >= ymax;
     k4.xoff = (k4.xhlo + 3) & ~3;
@@ -270,7 +290,7 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
       return std::max(erpp::smem_bytes4(t, copies, false), erpp::smem_bytes4(t, 3, true)) +
              1024;  // + static shared memory
     };
-    int tz = 4;
+    int tz = c->tile_req[1] > 0 ? c->tile_req[1] : 4;
     while (tz > 1 && smem(tz) > 227 * 1024) tz >>= 1;
     k4.T[2] = std::min(tz, n[2]);
     k4.nt[2] = (n[2] + k4.T[2] - 1) / k4.T[2];
@@ -279,7 +299,9 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
     const bool fits = smem(k4.T[2]) <= 227 * 1024;
     if (ok_x && ok_y && fits && nt4 <= (1 << 24) && k4.px <= 128 && k4.T[1] + hy <= 64) {
       k4.ntiles = (int)nt4;
-      k4.halo_per_tile = (int64_t)3 * k4.T[2] * ((int64_t)(k4.T[1] + hy) * hx + (int64_t)hy * k4.T[0]);
+      // x-strips, then y-strips from a 16-byte boundary; whole blocks of 4
+      k4.ystrip_off = ((int64_t)3 * k4.T[2] * (k4.T[1] + hy) * hx + 3) & ~(int64_t)3;
+      k4.halo_per_tile = (k4.ystrip_off + (int64_t)3 * k4.T[2] * hy * k4.T[0] + 3) & ~(int64_t)3;
       kp = k4;
       c->maxseg[1] = 1;
       c->maxseg[2] = max_pieces(n[2], kp.T[2], kp.hlo, kp.xs);
@@ -308,25 +330,16 @@ erpp_status erpp_init(const erpp_params* p, erpp_ctx** out) {
     free(c);
     return s0;
   }
-  const erpp_kparams& kp = c->kp;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->red, sizeof(double) * (6 * 304 + 8));
-  if (e == cudaSuccess && !c->fp64) {
-    const size_t nbins = (size_t)erpp::nbins(kp);
-    e = cudaMalloc(&c->tile_cnt, sizeof(int32_t) * nbins);
-    if (e == cudaSuccess) e = cudaMalloc(&c->tile_start, sizeof(int32_t) * (nbins + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&c->tile_cursor, sizeof(int32_t) * nbins);
-    if (e == cudaSuccess) e = cudaMalloc(&c->scan_tmp, sizeof(int32_t) * (nbins / 4096 + 1));
-    const size_t hb = (size_t)kp.ntiles * (size_t)kp.halo_per_tile;
-    if (e == cudaSuccess) e = cudaMalloc(&c->halo, sizeof(float) * hb);
-  }
-  if (e != cudaSuccess) {
-    erpp_status s = set_cuda_err(e);
+  erpp_status st = set_cuda_err(e);
+  if (st == ERPP_OK) st = alloc_tile_tables(c);
+  if (st != ERPP_OK) {
     erpp_destroy(c);
     cudaGetLastError();
-    return s;
+    return st;
   }
   *out = c;
   return ERPP_OK;
@@ -348,6 +361,43 @@ erpp_status erpp_destroy(erpp_ctx* c) {
   cudaFree(c->err);
   cudaFree(c->red);
   free(c);
+  return ERPP_OK;
+}
+
+erpp_status erpp_set_tiling(erpp_ctx* c, int32_t tile_y, int32_t tile_z) {
+  if (!c) return ERPP_EINVAL;
+  if (tile_y < 0 || tile_y > 32 || !(tile_z == 0 || tile_z == 1 || tile_z == 2 || tile_z == 4))
+    return ERPP_EINVAL;
+  erpp_ctx probe = *c;
+  probe.tile_req[0] = tile_y;
+  probe.tile_req[1] = tile_z;
+  erpp_status s = erpp::derive_ctx(&c->params, &probe);
+  if (s != ERPP_OK) return s;
+  // new geometry: tile tables, halo and piece records are reallocated
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return set_cuda_err(e);
+  free_scratch(c);
+  cudaFree(c->tile_cnt);
+  cudaFree(c->tile_start);
+  cudaFree(c->tile_cursor);
+  cudaFree(c->scan_tmp);
+  cudaFree(c->halo);
+  c->tile_cnt = c->tile_start = c->tile_cursor = c->scan_tmp = nullptr;
+  c->halo = nullptr;
+  c->tile_req[0] = tile_y;
+  c->tile_req[1] = tile_z;
+  c->kp = probe.kp;
+  for (int a = 0; a < 3; ++a) c->maxseg[a] = probe.maxseg[a];
+  c->xw_len = probe.xw_len;
+  return alloc_tile_tables(c);
+}
+
+erpp_status erpp_get_tiling(erpp_ctx* c, int32_t out[4]) {
+  if (!c || !out) return ERPP_EINVAL;
+  out[0] = c->kp.design;
+  out[1] = c->kp.T[0];
+  out[2] = c->kp.T[1];
+  out[3] = c->kp.T[2];
   return ERPP_OK;
 }
 

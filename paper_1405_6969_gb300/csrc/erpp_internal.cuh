@@ -64,6 +64,7 @@ struct erpp_kparams {
   int32_t xoff;      // design 4: staged column of the tile's first node
                      // (xhlo rounded up to a multiple of 4)
   int64_t halo_per_tile; // design 4: floats of one tile's scatter halo strips
+  int64_t ystrip_off;    // design 4: offset (floats) of the y-strips in them
   int32_t normalize, self_removal, kahan;
   double inv_dx[3];  // N / L
   double L[3];
@@ -88,6 +89,7 @@ struct erpp_ctx {
   int device;
   int fp64;
   int maxseg[3];          // most tiles one window can reach per axis
+  int tile_req[2];        // requested T_y, T_z of the x/y-halo tiles (0: default)
   // scratch (owned)
   int64_t cap;            // particle capacity of the per-particle arrays
   float4* geo_t;

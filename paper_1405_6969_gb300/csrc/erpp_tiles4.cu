@@ -695,40 +695,68 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter4(
   }
   // interior once (zeros for empty tiles); halo strips to the buffer:
   // x-strips [3][T_z][T_y + hy][hx] (all staged rows), y-strips [3][T_z][hy][W]
+  // (16-byte aligned).  Per staged row the lanes take jobs: 16-byte chunks
+  // of the interior columns (to S, or to the y-strip on a y-halo row) when
+  // everything is aligned, else single words; then the hx halo columns (to
+  // the x-strip).
   const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
   const int hx = kp.xhlo + kp.xhhi, hy = kp.yhlo + kp.yhhi;
   const int ny_st = ext[1] + hy;
-  const int width = ext[0] + hx;
-  const int x_lo = kp.xoff - kp.xhlo;  // first staged column used
   float* hxs = halo + (size_t)tile * kp.halo_per_tile;
-  float* hys = hxs + 3 * kp.T[2] * (kp.T[1] + hy) * hx;
+  float* hys = hxs + kp.ystrip_off;
+  const bool vec = (kp.n[0] & 3) == 0 && (ext[0] & 3) == 0 && (b[0] & 3) == 0 &&
+                   (kp.T[0] & 3) == 0 && (((uintptr_t)S) & 15) == 0 &&
+                   (((uintptr_t)halo) & 15) == 0;
+  const int nvec = vec ? ext[0] >> 2 : 0;
+  const int jobs = nvec + (vec ? 0 : ext[0]) + hx;
+  auto value = [&](int idx) -> float {
+    if (!any) return 0.f;
+    if (MODE == 1) return smem[idx] + smem[3 * plane + idx];
+    if (fixedp) return (float)acc_i[idx] * inv_scale;
+    return smem[idx];
+  };
   for (int cc = 0; cc < 3; ++cc) {
     for (int z = 0; z < ext[2]; ++z) {
       for (int y = warp; y < ny_st; y += kWarps) {
-        const int so = cc * plane + z * pxy + y * px + x_lo;
+        const int so = cc * plane + z * pxy + y * px;  // staged row start
         const bool yint = y >= kp.yhlo && y < kp.yhlo + ext[1];
-        float* dst = S + cc * nn + ((size_t)(b[2] + z) * kp.n[1] + (b[1] + y - kp.yhlo)) * kp.n[0] +
-                     b[0];
-        float* xrow = hxs + (((size_t)cc * kp.T[2] + z) * (kp.T[1] + hy) + y) * hx;
         const int yh = y < kp.yhlo ? y : y - ext[1];  // y-strip row when !yint
-        float* yrow = hys + (((size_t)cc * kp.T[2] + z) * hy + yh) * kp.T[0];
-        for (int xx = lane; xx < width; xx += 32) {
-          float val = 0.f;
-          if (any) {
-            if (MODE == 1)
-              val = smem[so + xx] + smem[3 * plane + so + xx];
-            else if (fixedp)
-              val = (float)acc_i[so + xx] * inv_scale;
-            else
-              val = smem[so + xx];
+        float* drow = yint ? S + cc * nn +
+                                 ((size_t)(b[2] + z) * kp.n[1] + (b[1] + y - kp.yhlo)) * kp.n[0] +
+                                 b[0]
+                           : hys + (((size_t)cc * kp.T[2] + z) * hy + yh) * kp.T[0];
+        float* xrow = hxs + (((size_t)cc * kp.T[2] + z) * (kp.T[1] + hy) + y) * hx;
+        for (int j = lane; j < jobs; j += 32) {
+          if (j < nvec) {
+            const int i0 = so + kp.xoff + 4 * j;
+            float4 v;
+            if (!any) {
+              v = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else if (MODE == 0 && fixedp) {
+              const int4 q = *reinterpret_cast<const int4*>(acc_i + i0);
+              v = make_float4((float)q.x * inv_scale, (float)q.y * inv_scale,
+                              (float)q.z * inv_scale, (float)q.w * inv_scale);
+            } else {
+              v = *reinterpret_cast<const float4*>(smem + i0);
+              if (MODE == 1) {
+                const float4 l = *reinterpret_cast<const float4*>(smem + 3 * plane + i0);
+                v.x += l.x;
+                v.y += l.y;
+                v.z += l.z;
+                v.w += l.w;
+              }
+            }
+            *reinterpret_cast<float4*>(drow + 4 * j) = v;
+          } else {
+            const int sj = j - nvec;
+            if (!vec && sj < ext[0]) {
+              drow[sj] = value(so + kp.xoff + sj);
+            } else {
+              const int h = vec ? sj : sj - ext[0];
+              const int col = h < kp.xhlo ? kp.xoff - kp.xhlo + h : kp.xoff + ext[0] + (h - kp.xhlo);
+              xrow[h] = value(so + col);
+            }
           }
-          const bool xint = xx >= kp.xhlo && xx < kp.xhlo + ext[0];
-          if (xint && yint)
-            dst[xx - kp.xhlo] = val;
-          else if (!xint)
-            xrow[xx < kp.xhlo ? xx : xx - ext[0]] = val;
-          else
-            yrow[xx - kp.xhlo] = val;
         }
       }
     }
@@ -742,7 +770,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter4(
 // periodic in x and y.  One block per (tile, component, plane); only the rim
 // nodes (within xhhi / xhlo columns or yhhi / yhlo rows of the tile's edges)
 // are visited: whole rim rows, then the rim columns of the other rows.
-constexpr int kMergeThreads = 128;
+constexpr int kMergeThreads = 256;
 
 __global__ void __launch_bounds__(kMergeThreads) k_merge_halo4(erpp_kparams kp,
                                                                float* __restrict__ S,
@@ -756,8 +784,6 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_halo4(erpp_kparams kp,
   const int z = cz % kp.T[2];
   const int cc = cz / kp.T[2];
   if (z >= ext[2]) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int nwarps = kMergeThreads / 32;
   const int txy = kp.nt[0] * kp.nt[1];
   const int txl = t[0] == 0 ? kp.nt[0] - 1 : t[0] - 1;
   const int txr = t[0] == kp.nt[0] - 1 ? 0 : t[0] + 1;
@@ -767,7 +793,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_halo4(erpp_kparams kp,
   const int exty_l = min((tyl + 1) * Ty, kp.n[1]) - tyl * Ty;
   // strips of this (component, plane) in each neighbour's halo block
   const size_t xs0 = (size_t)cz * (Ty + hy) * hx;
-  const size_t ys0 = (size_t)3 * kp.T[2] * (Ty + hy) * hx + (size_t)cz * hy * W;
+  const size_t ys0 = (size_t)kp.ystrip_off + (size_t)cz * hy * W;
   auto base = [&](int id) { return halo + (size_t)id * kp.halo_per_tile; };
   const float* xL = base(tid(txl, t[1])) + xs0;   // right strip of the left tile
   const float* xR = base(tid(txr, t[1])) + xs0;   // left strip of the right tile
@@ -794,20 +820,31 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_halo4(erpp_kparams kp,
     if (xr && yr) add += xRT[(y - ycut) * hx + x - xcut];
     splane[(size_t)(b[1] + y) * kp.n[0] + b[0] + x] += add;
   };
-  // rim rows (all rows when the tile is no taller than the halo)
+  // rim nodes as one flat list: whole rim rows (all rows when the tile is no
+  // taller than the halo), then the rim columns of the other rows (all
+  // columns when the tile is no wider than the halo)
   const bool allrows = ext[1] < hy;
   const int nrim = allrows ? ext[1] : hy;
-  for (int rr = warp; rr < nrim; rr += nwarps) {
-    const int y = allrows || rr < kp.yhhi ? rr : ycut + (rr - kp.yhhi);
-    for (int x = lane; x < ext[0]; x += 32) node(x, y);
-  }
-  if (allrows) return;
-  // rim columns of the remaining rows
   const bool allcols = ext[0] < hx;
   const int ncol = allcols ? ext[0] : hx;
-  for (int y = kp.yhhi + warp; y < ycut; y += nwarps)
-    for (int j = lane; j < ncol; j += 32)
-      node(allcols || j < kp.xhhi ? j : xcut + (j - kp.xhhi), y);
+  const int nmid = allrows ? 0 : ycut - kp.yhhi;
+  const int nA = nrim * ext[0];
+  const int total = nA + nmid * ncol;
+  for (int i = threadIdx.x; i < total; i += kMergeThreads) {
+    int x, y;
+    if (i < nA) {
+      const int rr = i / ext[0];
+      x = i - rr * ext[0];
+      y = allrows || rr < kp.yhhi ? rr : ycut + (rr - kp.yhhi);
+    } else {
+      const int k = i - nA;
+      const int yy = k / ncol;
+      const int j = k - yy * ncol;
+      y = kp.yhhi + yy;
+      x = allcols || j < kp.xhhi ? j : xcut + (j - kp.xhhi);
+    }
+    node(x, y);
+  }
 }
 
 template <int XM, int LMIN, int XW>

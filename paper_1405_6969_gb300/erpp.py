@@ -112,6 +112,7 @@ class Context:
         p = make_params(params, precision, normalize, self_removal, kahan)
         self.params = dict(params)
         self.precision = precision
+        self.kahan = bool(kahan)
         self.grid_dtype = torch.float32 if precision == "fp32" else torch.float64
         self.shape = (3, p.nz, p.ny, p.nx)
         h = ctypes.c_void_p()
@@ -197,6 +198,17 @@ class Context:
 
     def check(self, stream=None):
         _lib.check(self.lib.erpp_check(self._h, _stream(stream)), "erpp_check")
+
+    def set_tiling(self, tile_y=0, tile_z=0):
+        """Request T_y, T_z of the x/y-halo tiles (0 = default)."""
+        _lib.check(self.lib.erpp_set_tiling(self._h, int(tile_y), int(tile_z)),
+                   "erpp_set_tiling")
+
+    def tiling(self):
+        """(design, W, T_y, T_z) of the tiles in use."""
+        out = (ctypes.c_int32 * 4)()
+        _lib.check(self.lib.erpp_get_tiling(self._h, out), "erpp_get_tiling")
+        return tuple(int(v) for v in out)
 
     def profile_enable(self, enable=True):
         _lib.check(self.lib.erpp_profile_enable(self._h, int(bool(enable))),
