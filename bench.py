@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--kahan", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tile shape instead of timing the candidates")
+    ap.add_argument("--tiling", default=None,
+                    help="fixed tile shape TYxTZ (for example 32x2) instead of the autotuner")
     ap.add_argument("--no-loop", action="store_true",
                     help="skip the closed-loop (coupling + fluid stand-in) timing")
     ap.add_argument("--workload", default="shear", choices=["shear", "cube256", "batched64"],
@@ -324,7 +326,11 @@ def main():
     # tile shape: time the candidates on this workload (a few steps each, on
     # copies of the particle state) and keep the fastest
     tiling = {"tiling": ctx.tiling()}
-    if not args.no_autotune:
+    if args.tiling:
+        ty, tz = (int(v) for v in args.tiling.lower().split("x"))
+        ctx.set_tiling(ty, tz)
+        tiling = {"tile": (ty, tz), "tiling": ctx.tiling(), "ms": None, "cached": False}
+    elif not args.no_autotune:
         from paper_1405_6969_gb300 import autotune
         tiling = autotune.tune(ctx, u, ps, S=S, use_cache=False)
 
