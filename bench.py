@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tile shape instead of timing the candidates")
     ap.add_argument("--tiling", default=None,
-                    help="fixed tile shape TYxTZ (for example 32x2) instead of the autotuner")
+                    help="fixed tile shape TYxTZ[xTHREADS] (for example 32x2x256) instead of "
+                         "the autotuner")
     ap.add_argument("--no-loop", action="store_true",
                     help="skip the closed-loop (coupling + fluid stand-in) timing")
     ap.add_argument("--workload", default="shear", choices=["shear", "cube256", "batched64"],
@@ -284,7 +285,7 @@ def run_batched(args, ws, rank, local):
             "speedup_vs_fp64_plain_form": ms_f64 / ms_graph,
             "roofline": None, "cpu_baseline": None,
             "e2e": None,
-            "gpu_launches": 9 * len(made) * args.steps,
+            "gpu_launches": 10 * len(made) * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -327,9 +328,9 @@ def main():
     # copies of the particle state) and keep the fastest
     tiling = {"tiling": ctx.tiling()}
     if args.tiling:
-        ty, tz = (int(v) for v in args.tiling.lower().split("x"))
-        ctx.set_tiling(ty, tz)
-        tiling = {"tile": (ty, tz), "tiling": ctx.tiling(), "ms": None, "cached": False}
+        t = [int(v) for v in args.tiling.lower().split("x")] + [0]
+        ctx.set_tiling(t[0], t[1], t[2])
+        tiling = {"tile": tuple(t[:3]), "tiling": ctx.tiling(), "ms": None, "cached": False}
     elif not args.no_autotune:
         from paper_1405_6969_gb300 import autotune
         tiling = autotune.tune(ctx, u, ps, S=S, use_cache=False)
@@ -477,8 +478,8 @@ def main():
             "tiling": tiling,
             "e2e": e2e,
             # bin count, three scan kernels, bin fill, gather, advance, scatter,
-            # halo merge
-            "gpu_launches": 9 * args.steps,
+            # halo merge (two kernels with x/y-halo tiles, one otherwise)
+            "gpu_launches": (10 if ctx.tiling()[0] == 4 else 9) * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -286,17 +286,20 @@ erpp_status erpp_fluid_destroy(erpp_fluid* fluid);
 /* ---- Tiling (performance tuning; results do not depend on it beyond
  * floating-point summation order) ---------------------------------------
  * FP32 contexts whose windows span at most 16 nodes in x and y use tiles of
- * W x T_y x T_z nodes staged with x- and y-halos; the default is T_y = 16,
- * T_z = 4.  erpp_set_tiling requests T_y in 1..32 and T_z in {1, 2, 4}
- * (0 = default); T_z is reduced further when the staged tile would not fit in
- * shared memory.  Synchronises the device and frees the context's scratch
- * (reallocated on the next call); EINVAL for other values.  Contexts outside
- * that scope accept the call and keep their own tiling. */
-erpp_status erpp_set_tiling(erpp_ctx* ctx, int32_t tile_y, int32_t tile_z);
+ * W x T_y x T_z nodes staged with x- and y-halos, processed by one block of
+ * 256 or 512 threads; the default is T_y = 16, T_z = 4, 256 threads.
+ * erpp_set_tiling requests T_y in 1..32, T_z in {1, 2, 4} and threads in
+ * {256, 512} (0 = default each); T_y is raised to the halo depth and T_z
+ * reduced when the staged tile would not fit in shared memory.  Synchronises
+ * the device and frees the context's scratch (reallocated on the next call);
+ * EINVAL for other values.  Contexts outside that scope accept the call and
+ * keep their own tiling. */
+erpp_status erpp_set_tiling(erpp_ctx* ctx, int32_t tile_y, int32_t tile_z, int32_t threads);
 
 /* out[0] = tile design in use (4: x/y-halo tiles, 3: x-halo tiles cut in y
- * and z), out[1..3] = tile size W, T_y, T_z.  out is a HOST array of 4. */
-erpp_status erpp_get_tiling(erpp_ctx* ctx, int32_t out[4]);
+ * and z), out[1..3] = tile size W, T_y, T_z, out[4] = threads per block.
+ * out is a HOST array of 5. */
+erpp_status erpp_get_tiling(erpp_ctx* ctx, int32_t out[5]);
 
 /* Per-phase timing (a tracing aid, not part of the method).  After
  * erpp_profile_enable(ctx, 1) every erpp_step records CUDA events on its

@@ -1,10 +1,12 @@
 """Tile-shape autotuner for the FP32 coupling kernels.
 
-The FP32 gather and scatter run one thread block per grid tile of
-W x T_y x T_z nodes (x/y-halo tiles, ``erpp_set_tiling``).  Taller tiles
-stage fewer halo rows per node; flatter tiles need less shared memory (more
-blocks per SM) but cut more particle windows along z.  The best shape depends
-on the grid, the kernel width sigma_R / dx and the particle density, so it is
+The FP32 gather and scatter run one thread block (256 or 512 threads) per
+grid tile of W x T_y x T_z nodes (x/y-halo tiles, ``erpp_set_tiling``).
+Taller tiles stage fewer halo rows per node; flatter tiles need less shared
+memory (more blocks per SM) but cut more particle windows along z; more
+threads per block hide more latency but split a tile's units over more
+warps.  The best shape depends on the grid, the kernel width sigma_R / dx and
+the particle density, so it is
 measured: every candidate runs a few coupling steps (CUDA events, on copies of
 the particle state) and the fastest is applied and remembered in a JSON cache
 keyed by (grid, r_c / dx, particles per node class, options).  Host logic
@@ -17,7 +19,9 @@ import json
 import math
 import os
 
-CANDIDATES = ((16, 4), (8, 4), (16, 2), (32, 2), (8, 2), (32, 1), (16, 1))
+# (T_y, T_z, threads per block)
+CANDIDATES = ((16, 4, 256), (16, 2, 256), (32, 2, 256), (32, 1, 256), (8, 4, 256),
+              (16, 4, 512), (16, 2, 512), (32, 2, 512), (32, 1, 512), (8, 2, 512))
 
 
 def default_cache_path():
@@ -80,27 +84,27 @@ def tune(ctx, u, state, S=None, candidates=CANDIDATES, steps=5, warmup=2, cache_
          use_cache=True):
     """Choose and apply the fastest tile shape for this context and workload.
 
-    Returns {"tile": (T_y, T_z), "tiling": ctx.tiling(), "ms": {...} or None,
+    Returns {"tile": (T_y, T_z, threads), "tiling": ctx.tiling(), "ms": {...} or None,
     "cached": bool}.  Contexts without x/y-halo tiles are left unchanged."""
     if ctx.tiling()[0] != 4:
         return {"tile": None, "tiling": ctx.tiling(), "ms": None, "cached": False}
     path = cache_path or default_cache_path()
     key = workload_key(ctx.params, state.n, ctx.precision, getattr(ctx, "kahan", False))
     cache = load_cache(path) if use_cache else {}
-    if use_cache and key in cache:
-        ty, tz = cache[key]["tile"]
-        ctx.set_tiling(ty, tz)
-        return {"tile": (ty, tz), "tiling": ctx.tiling(), "ms": cache[key].get("ms"),
+    if use_cache and key in cache and len(cache[key].get("tile", ())) == 3:
+        ty, tz, nt = cache[key]["tile"]
+        ctx.set_tiling(ty, tz, nt)
+        return {"tile": (ty, tz, nt), "tiling": ctx.tiling(), "ms": cache[key].get("ms"),
                 "cached": True}
     S = ctx.new_grid() if S is None else S
     times = {}
-    for ty, tz in candidates:
-        ctx.set_tiling(ty, tz)
-        times[f"{ty}x{tz}"] = _time_steps(ctx, u, state, S, steps, warmup)
+    for ty, tz, nt in candidates:
+        ctx.set_tiling(ty, tz, nt)
+        times[f"{ty}x{tz}x{nt}"] = _time_steps(ctx, u, state, S, steps, warmup)
     best = min(times, key=times.get)
-    ty, tz = (int(v) for v in best.split("x"))
-    ctx.set_tiling(ty, tz)
+    ty, tz, nt = (int(v) for v in best.split("x"))
+    ctx.set_tiling(ty, tz, nt)
     if use_cache:
-        cache[key] = {"tile": [ty, tz], "ms": times}
+        cache[key] = {"tile": [ty, tz, nt], "ms": times}
         save_cache(path, cache)
-    return {"tile": (ty, tz), "tiling": ctx.tiling(), "ms": times, "cached": False}
+    return {"tile": (ty, tz, nt), "tiling": ctx.tiling(), "ms": times, "cached": False}

@@ -198,6 +198,16 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
   kp.self_s2 = (2.0 * p->nu) * (p->eps_R + p->dt) + (2.0 * p->nu) * p->eps_R;
   kp.self_pref = (float)(-(p->dt / p->rho_f) / pow(2.0 * kPi * kp.self_s2, 1.5));
   kp.self_inv_w = (float)(1.0 / sqrt(2.0 * kp.self_s2));
+  kp.drag_f = (float)(6.0 * kPi * kp.mu);
+  kp.rho_f_f = (float)p->rho_f;
+  kp.dt_f = (float)p->dt;
+  for (int a = 0; a < 3; ++a) {
+    kp.grav_f[a] = (float)p->gravity[a];
+    kp.halfL_f[a] = (float)(0.5 * L[a]);
+    // a float position at least 1e-4 L inside the box is certainly inside it
+    kp.wrap_lo_f[a] = (float)(1e-4 * L[a]);
+    kp.wrap_hi_f[a] = (float)((1.0 - 1e-4) * L[a]);
+  }
   const double log2e = 1.4426950408889634;
   for (int a = 0; a < 3; ++a) kp.beta[a] = (float)(log2e * kp.dx[a] * kp.dx[a] / (2.0 * sig2));
   kp.inv_rho_dV = (float)(1.0 / (p->rho_f * kp.dV));
@@ -276,6 +286,7 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
     split(c->tile_req[0] > 0 ? c->tile_req[0] : 16, n[1], ymax, &k4.T[1], &k4.nt[1]);
     const bool ok_x = k4.nt[0] == 1 || n[0] - (k4.nt[0] - 1) * k4.T[0] >= hmax;
     const bool ok_y = k4.nt[1] == 1 || n[1] - (k4.nt[1] - 1) * k4.T[1] >= ymax;
+    k4.nthreads = c->tile_req[2] == 512 ? 512 : 256;
     k4.xoff = (k4.xhlo + 3) & ~3;
     const int need = k4.xoff + k4.T[0] + k4.xhhi;
     k4.px = ((need + 15) / 32) * 32 + 16;  // >= xoff + W + xhhi, 16 (mod 32)
@@ -364,13 +375,15 @@ erpp_status erpp_destroy(erpp_ctx* c) {
   return ERPP_OK;
 }
 
-erpp_status erpp_set_tiling(erpp_ctx* c, int32_t tile_y, int32_t tile_z) {
+erpp_status erpp_set_tiling(erpp_ctx* c, int32_t tile_y, int32_t tile_z, int32_t threads) {
   if (!c) return ERPP_EINVAL;
-  if (tile_y < 0 || tile_y > 32 || !(tile_z == 0 || tile_z == 1 || tile_z == 2 || tile_z == 4))
+  if (tile_y < 0 || tile_y > 32 || !(tile_z == 0 || tile_z == 1 || tile_z == 2 || tile_z == 4) ||
+      !(threads == 0 || threads == 256 || threads == 512))
     return ERPP_EINVAL;
   erpp_ctx probe = *c;
   probe.tile_req[0] = tile_y;
   probe.tile_req[1] = tile_z;
+  probe.tile_req[2] = threads;
   erpp_status s = erpp::derive_ctx(&c->params, &probe);
   if (s != ERPP_OK) return s;
   // new geometry: tile tables, halo and piece records are reallocated
@@ -386,18 +399,20 @@ erpp_status erpp_set_tiling(erpp_ctx* c, int32_t tile_y, int32_t tile_z) {
   c->halo = nullptr;
   c->tile_req[0] = tile_y;
   c->tile_req[1] = tile_z;
+  c->tile_req[2] = threads;
   c->kp = probe.kp;
   for (int a = 0; a < 3; ++a) c->maxseg[a] = probe.maxseg[a];
   c->xw_len = probe.xw_len;
   return alloc_tile_tables(c);
 }
 
-erpp_status erpp_get_tiling(erpp_ctx* c, int32_t out[4]) {
+erpp_status erpp_get_tiling(erpp_ctx* c, int32_t out[5]) {
   if (!c || !out) return ERPP_EINVAL;
   out[0] = c->kp.design;
   out[1] = c->kp.T[0];
   out[2] = c->kp.T[1];
   out[3] = c->kp.T[2];
+  out[4] = c->kp.design == 4 ? c->kp.nthreads : 256;
   return ERPP_OK;
 }
 

@@ -61,6 +61,7 @@ struct erpp_kparams {
   int32_t design;    // 3: x-halo tiles, pieces cut in y and z (bucket bins);
                      // 4: x/y-halo tiles, pieces cut in z only, unit schedules
   int32_t yhlo, yhhi;// design 4: y-halo rows staged below / above a tile
+  int32_t nthreads;  // design 4: threads per block of the tile kernels (256, 512)
   int32_t xoff;      // design 4: staged column of the tile's first node
                      // (xhlo rounded up to a multiple of 4)
   int64_t halo_per_tile; // design 4: floats of one tile's scatter halo strips
@@ -81,6 +82,13 @@ struct erpp_kparams {
   float inv_rho_dV;  // 1 / (rho_f dV)
   float self_pref;   // -(dt/rho_f) (2 pi s2)^(-3/2)
   float self_inv_w;  // 1 / sqrt(2 s2)
+  // float copies for the FP32 drag and increment of the advance
+  float drag_f;      // 6 pi mu
+  float rho_f_f;     // rho_f
+  float dt_f;        // dt
+  float grav_f[3];   // gravity
+  float halfL_f[3];  // L / 2 (minimum-image pre-check)
+  float wrap_lo_f[3], wrap_hi_f[3];  // float bounds outside which wrapping cannot occur
 };
 
 struct erpp_ctx {
@@ -89,7 +97,7 @@ struct erpp_ctx {
   int device;
   int fp64;
   int maxseg[3];          // most tiles one window can reach per axis
-  int tile_req[2];        // requested T_y, T_z of the x/y-halo tiles (0: default)
+  int tile_req[3];        // requested T_y, T_z, threads of the x/y-halo tiles (0: default)
   // scratch (owned)
   int64_t cap;            // particle capacity of the per-particle arrays
   float4* geo_t;

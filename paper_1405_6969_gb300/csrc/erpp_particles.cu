@@ -121,32 +121,35 @@ __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, Par
     x[a] = P.x[a][i];
     v[a] = P.v[a][i];
   }
+  // F32: the gathered velocity and the self term are FP32 quantities; they
+  // are combined in FP32 and the particle velocity is subtracted in FP64.
   double up[3];
+  float upf[3] = {0.f, 0.f, 0.f};
   float norm = 0.f;
   if (FROM_ACC) {
     norm = erpp_norm(kp, geo_t[i], geo_c[i]);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) up[a] = (double)(up_acc[a * acc_stride + i] * norm);
-    up[0] += kp.shear_rate * x[1];
+    for (int a = 0; a < 3; ++a) upf[a] = up_acc[a * acc_stride + i] * norm;
   } else {
 #pragma unroll
     for (int a = 0; a < 3; ++a) up[a] = U.up[a][i];
   }
   double vs[3] = {0.0, 0.0, 0.0};
+  float vsf[3] = {0.f, 0.f, 0.f};
   if (kp.self_removal && !first_step) {
     double r[3], D[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      r[a] = min_image(x[a] - P.xp[a][i], kp.L[a]);
+      const double d = x[a] - P.xp[a][i];
+      // the exact minimum-image test only where the float difference is
+      // near half the box
+      r[a] = fabsf((float)d) > 0.99f * kp.halfL_f[a] ? min_image(d, kp.L[a]) : d;
       D[a] = P.D[a][i];
     }
     if (F32) {
       float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
       float Df[3] = {(float)D[0], (float)D[1], (float)D[2]};
-      float o[3];
-      self_velocity_f32(kp, rf, Df, o);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) vs[a] = (double)o[a];
+      self_velocity_f32(kp, rf, Df, vsf);
     } else {
       self_velocity_f64(kp, r, D, vs);
     }
@@ -155,20 +158,33 @@ __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, Par
   const double a_p = P.radius[i];
   const double rho = P.rho_p[i];
   double Dn[3];
+  float Dnf[3];
   if (F32) {
     const float af = (float)a_p, rf = (float)rho;
-    const float k_drag = (float)(6.0 * pi * kp.mu) * af;
+    const float k_drag = kp.drag_f * af;
     const float inv_m = 1.f / ((float)(4.0 / 3.0 * pi) * af * af * af * rf);
-    const float buoy = 1.f - (float)kp.rho_f / rf;
-    const float dtf = (float)kp.dt;
+    const float buoy = 1.f - kp.rho_f_f / rf;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const float slip = (float)((up[a] - vs[a]) - v[a]);
+      // tile gather: FP32 velocity, plus the mean shear at the particle;
+      // caller's FP64 velocity (shear included): subtract in FP64
+      double ut;
+      if (FROM_ACC) {
+        ut = (double)(upf[a] - vsf[a]);
+        if (a == 0) ut += kp.shear_rate * x[1];
+      } else {
+        ut = up[a] - (double)vsf[a];
+      }
+      const float slip = (float)(ut - v[a]);
       const float Df = k_drag * slip;
-      const float dv = dtf * (Df * inv_m + buoy * (float)kp.gravity[a]);
+      const float dv = kp.dt_f * (Df * inv_m + buoy * kp.grav_f[a]);
+      Dnf[a] = Df;
       Dn[a] = (double)Df;
       P.v[a][i] = v[a] + (double)dv;
-      P.x[a][i] = wrap_coord(x[a] + kp.dt * v[a], kp.L[a]);
+      double xn = x[a] + kp.dt * v[a];
+      const float xf = (float)xn;
+      if (!(xf > kp.wrap_lo_f[a] && xf < kp.wrap_hi_f[a])) xn = wrap_coord(xn, kp.L[a]);
+      P.x[a][i] = xn;
       P.xp[a][i] = x[a];
       P.D[a][i] = Dn[a];
     }
@@ -178,6 +194,7 @@ __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, Par
     const double buoy = 1.0 - kp.rho_f / rho;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
+      Dnf[a] = 0.f;
       double ut = up[a] - vs[a];
       Dn[a] = k_drag * (ut - v[a]);
       P.v[a][i] = v[a] + kp.dt * (Dn[a] / m_p + buoy * kp.gravity[a]);
@@ -188,7 +205,7 @@ __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, Par
   }
   if (fscat) {
     const float s = -norm * kp.inv_rho_dV;
-    const float f0 = s * (float)Dn[0], f1 = s * (float)Dn[1], f2 = s * (float)Dn[2];
+    const float f0 = s * Dnf[0], f1 = s * Dnf[1], f2 = s * Dnf[2];
     fscat[i] = make_float4(f0, f1, f2, fmaxf(fabsf(f0), fmaxf(fabsf(f1), fabsf(f2))));
   }
 }

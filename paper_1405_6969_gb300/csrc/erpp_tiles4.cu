@@ -51,8 +51,8 @@
 // component).  Tiles with more than 1024 pieces add FP32 values instead, and
 // ERPP_KAHAN adds FP32 values with the exact rounding error of each addition
 // (two-sum on the atomic's old value) kept in a second array.  The interior
-// is written once; the halo strips go to a buffer that k_merge_halo4 adds to
-// the neighbouring tiles in a fixed order.
+// is written once; the halo strips go to a buffer that k_merge_rows and
+// k_merge_cols add to the neighbouring tiles in a fixed order.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -61,8 +61,7 @@
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+// Threads per block of the tile kernels: 256 or 512 (a tiling option).
 constexpr int kMaxTz = 4;         // z-planes per tile (units per piece)
 constexpr int kDenseTile = 1024;  // pieces above which a tile accumulates in FP32
 constexpr uint16_t kEmpty = 0xffffu;
@@ -138,11 +137,16 @@ __device__ __forceinline__ void red_f32_at(unsigned a, float v) {
   asm volatile("red.shared.add.f32 [%0], %1;\n" ::"r"(a), "f"(v));
 }
 
-// round(g w / 2^32) as one 32 x 32 -> 64-bit multiply-add (high word)
+// round(g w / 2^32) = high word of g w + 2^31: the low word of the product
+// plus 2^31 (carry out), then the signed high word plus that carry.
 __device__ __forceinline__ int mul_hi_round(int g, int w) {
-  long long r;
-  asm("mad.wide.s32 %0, %1, %2, %3;\n" : "=l"(r) : "r"(g), "r"(w), "l"(0x80000000LL));
-  return (int)(r >> 32);
+  int hi;
+  asm("{\n\t.reg .u32 lo;\n\t"
+      "mad.lo.cc.u32 lo, %1, %2, 0x80000000;\n\t"
+      "madc.hi.s32 %0, %1, %2, 0;\n\t}\n"
+      : "=r"(hi)
+      : "r"(g), "r"(w));
+  return hi;
 }
 
 // One row of a unit, slot Q onwards.  Gather: x_c += e_x(q) u_c(q) over the
@@ -292,6 +296,7 @@ __device__ __forceinline__ void tile_origin4(const erpp_kparams& kp, int tile, i
 
 // Issues the copies that stage the tile with its x/y halo (periodic wrap).
 // Columns outside [xoff - xhlo, xoff + ext_x + xhhi) are never read.
+template <int NT>
 __device__ void stage_tile4(const erpp_kparams& kp, const float* __restrict__ u, float* field,
                             const int b[3], const int ext[3]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -308,7 +313,7 @@ __device__ void stage_tile4(const erpp_kparams& kp, const float* __restrict__ u,
     for (int z = 0; z < ext[2]; ++z) {
       const float* gplane = u + c * nn + (size_t)(b[2] + z) * kp.n[1] * kp.n[0];
       float* splane = field + c * kp.plane + z * kp.pxy;
-      for (int y = warp; y < ny_st; y += kWarps) {
+      for (int y = warp; y < ny_st; y += NT / 32) {
         int gy = b[1] - kp.yhlo + y;
         gy = gy < 0 ? gy + kp.n[1] : (gy >= kp.n[1] ? gy - kp.n[1] : gy);
         const float* grow = gplane + (size_t)gy * kp.n[0];
@@ -343,8 +348,9 @@ __device__ void stage_tile4(const erpp_kparams& kp, const float* __restrict__ u,
 
 // Builds the unit schedule of pieces [0, np) (records in cv.rec).  Returns
 // the number of rounds.  Called by the whole block; synchronises.
-template <int XW>
+template <int XW, int NT>
 __device__ int build_schedule(const Carve<XW>& cv, SchedState& ss, int np) {
+  constexpr int NW = NT / 32;
   const int tid = threadIdx.x;
   if (tid < 32) ss.cnt[tid] = 0;
   if (tid == 0) {
@@ -352,7 +358,7 @@ __device__ int build_schedule(const Carve<XW>& cv, SchedState& ss, int np) {
     ss.novf = 0;
   }
   __syncthreads();
-  for (int k = tid; k < np; k += kThreads) {
+  for (int k = tid; k < np; k += NT) {
     const Piece4 pc = unpack4(cv.rec[k]);
     const int ub = atomicAdd(&ss.nunits, pc.lz);
     for (int z = 0; z < pc.lz; ++z) {
@@ -367,8 +373,8 @@ __device__ int build_schedule(const Carve<XW>& cv, SchedState& ss, int np) {
   }
   __syncthreads();
   const int U = ss.nunits;
-  const int R = (U + kThreads - 1) / kThreads;
-  const int cap = kWarps * R;
+  const int R = (U + NT - 1) / NT;
+  const int cap = NW * R;
   if (tid < 32) {
     const int vac = max(0, cap - ss.cnt[tid]);
     int incl = vac;
@@ -380,9 +386,9 @@ __device__ int build_schedule(const Carve<XW>& cv, SchedState& ss, int np) {
     ss.vpre[tid + 1] = incl;
     if (tid == 0) ss.vpre[0] = 0;
   }
-  for (int s = tid; s < R * kThreads; s += kThreads) cv.sched[s] = kEmpty;
+  for (int s = tid; s < R * NT; s += NT) cv.sched[s] = kEmpty;
   __syncthreads();
-  for (int u = tid; u < U; u += kThreads) {
+  for (int u = tid; u < U; u += NT) {
     const uint32_t w = cv.unit[u];
     int bucket = (int)((w >> 14) & 31u);
     int slot = (int)((w >> 19) & 4095u);
@@ -397,7 +403,7 @@ __device__ int build_schedule(const Carve<XW>& cv, SchedState& ss, int np) {
       bucket = lo;
       slot = cap - 1 - (v - ss.vpre[lo]);  // latest rounds first
     }
-    cv.sched[(slot >> 3) * kThreads + (slot & 7) * 32 + bucket] = (uint16_t)u;
+    cv.sched[(slot / NW) * NT + (slot % NW) * 32 + bucket] = (uint16_t)u;
   }
   __syncthreads();
   return R;
@@ -411,10 +417,10 @@ __device__ __forceinline__ int batch_size(int total, int PB) {
 
 // Stages the batch's records (and, through the particle index, its
 // x-weights and force words) into shared memory; asynchronous copies.
-template <int XW, bool FORCES>
+template <int XW, bool FORCES, int NT>
 __device__ void stage_batch(const Carve<XW>& cv, const int4* __restrict__ entries, int b0, int np,
                             const float* __restrict__ xw, const float4* __restrict__ fscat) {
-  for (int k = threadIdx.x; k < np; k += kThreads) {
+  for (int k = threadIdx.x; k < np; k += NT) {
     const int4 r = __ldg(&entries[b0 + k]);
     cv.rec[k] = r;
     const float* src = xw + (size_t)r.x * XW;
@@ -434,8 +440,8 @@ struct UnitRows {
 
 // XM: longest x-window; LMIN: shortest (slots q >= LMIN are tested); XW:
 // x-weights stored per particle.
-template <int XM, int LMIN, int XW>
-__global__ void __launch_bounds__(kThreads, 2) k_gather4(
+template <int XM, int LMIN, int XW, int NT>
+__global__ void __launch_bounds__(NT, 2) k_gather4(
     erpp_kparams kp, const float* __restrict__ u, const int32_t* __restrict__ start,
     const int4* __restrict__ entries, int64_t ecap, const float* __restrict__ xw,
     float* __restrict__ up_acc, int64_t acc_stride) {
@@ -449,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_gather4(
   const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, 3, true);
   int b[3], ext[3], tt[3];
   tile_origin4(kp, tile, b, ext, tt);
-  stage_tile4(kp, u, cv.field, b, ext);
+  stage_tile4<NT>(kp, u, cv.field, b, ext);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int plane = kp.plane, px = kp.px, pxy = kp.pxy;
   const float by = kp.beta[1], bz = kp.beta[2];
@@ -457,13 +463,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_gather4(
   const int bs = batch_size(e1 - e0, PB);
   for (int b0 = e0; b0 < e1; b0 += bs) {
     const int np = min(bs, e1 - b0);
-    stage_batch<XW, false>(cv, entries, b0, np, xw, nullptr);
-    for (int k = threadIdx.x; k < 3 * PB; k += kThreads) cv.pacc[k] = 0.f;
-    const int R = build_schedule<XW>(cv, ss, np);  // synchronises
+    stage_batch<XW, false, NT>(cv, entries, b0, np, xw, nullptr);
+    for (int k = threadIdx.x; k < 3 * PB; k += NT) cv.pacc[k] = 0.f;
+    const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
     cp_async_wait_all();                            // field (first batch), x-weights
     __syncthreads();
     for (int r = 0; r < R; ++r) {
-      const uint16_t ui = cv.sched[r * kThreads + warp * 32 + lane];
+      const uint16_t ui = cv.sched[r * NT + warp * 32 + lane];
       const bool active = ui != kEmpty;
       UnitRows ur = {0, 0, 0, 0, 0.f, 0.f};
       int k = 0;
@@ -525,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_gather4(
       }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < np; k += kThreads) {
+    for (int k = threadIdx.x; k < np; k += NT) {
       const int p = cv.rec[k].x;
       atomicAdd(up_acc + p, cv.pacc[k]);
       atomicAdd(up_acc + acc_stride + p, cv.pacc[PB + k]);
@@ -536,14 +542,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_gather4(
 }
 
 // MODE 0: fixed point (FP32 atomics on dense tiles); MODE 1: compensated FP32.
-template <int XM, int LMIN, int XW, int MODE>
-__global__ void __launch_bounds__(kThreads, 2) k_scatter4(
+template <int XM, int LMIN, int XW, int MODE, int NT>
+__global__ void __launch_bounds__(NT, 2) k_scatter4(
     erpp_kparams kp, float* __restrict__ S, float* __restrict__ halo,
     const int32_t* __restrict__ start, const int4* __restrict__ entries, int64_t ecap,
     const float* __restrict__ xw, const float4* __restrict__ fscat) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SchedState ss;
-  __shared__ float red[kWarps];
+  constexpr int NW = NT / 32;
+  __shared__ float red[NW];
   constexpr int PB = Batch<XW>::kPB;
   const int tile = blockIdx.x;
   const int e0 = start[tile];
@@ -562,10 +569,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter4(
   if (any) {
     const int total = (MODE == 1 ? 6 : 3) * plane;
     float4* s4 = reinterpret_cast<float4*>(smem);
-    for (int k = threadIdx.x; k < total / 4; k += kThreads) s4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = threadIdx.x; k < total / 4; k += NT) s4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (fixedp) {
       float bsum = 0.f;
-      for (int e = e0 + threadIdx.x; e < e1; e += kThreads)
+      for (int e = e0 + threadIdx.x; e < e1; e += NT)
         bsum += __ldg(&fscat[__ldg(&entries[e].x)]).w;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
@@ -575,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter4(
     if (fixedp) {
       float B = 0.f;
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) B += red[w];
+      for (int w = 0; w < NW; ++w) B += red[w];
       if (B > 0.f) {
         int ex2;
         frexpf(B, &ex2);  // B = m 2^ex2, m in [0.5, 1)
@@ -591,12 +598,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter4(
     const int bs = batch_size(e1 - e0, PB);
     for (int b0 = e0; b0 < e1; b0 += bs) {
       const int np = min(bs, e1 - b0);
-      stage_batch<XW, true>(cv, entries, b0, np, xw, fscat);
-      const int R = build_schedule<XW>(cv, ss, np);  // synchronises
+      stage_batch<XW, true, NT>(cv, entries, b0, np, xw, fscat);
+      const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
       cp_async_wait_all();
       __syncthreads();
       for (int r = 0; r < R; ++r) {
-        const uint16_t ui = cv.sched[r * kThreads + warp * 32 + lane];
+        const uint16_t ui = cv.sched[r * NT + warp * 32 + lane];
         const bool active = ui != kEmpty;
         UnitRows ur = {0, 0, 0, 0, 0.f, 0.f};
         float ex[XM];
@@ -717,7 +724,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter4(
   };
   for (int cc = 0; cc < 3; ++cc) {
     for (int z = 0; z < ext[2]; ++z) {
-      for (int y = warp; y < ny_st; y += kWarps) {
+      for (int y = warp; y < ny_st; y += NW) {
         const int so = cc * plane + z * pxy + y * px;  // staged row start
         const bool yint = y >= kp.yhlo && y < kp.yhlo + ext[1];
         const int yh = y < kp.yhlo ? y : y - ext[1];  // y-strip row when !yint
@@ -763,118 +770,161 @@ __global__ void __launch_bounds__(kThreads, 2) k_scatter4(
   }
 }
 
-// Adds the scatter's halo strips onto the tiles they belong to, in a fixed
-// order (deterministic): interior node (x, y) of a tile receives from the
-// x-neighbours' x-strips (same rows), the y-neighbours' y-strips (same
-// columns) and the diagonal neighbours' x-strips in their y-halo rows;
-// periodic in x and y.  One block per (tile, component, plane); only the rim
-// nodes (within xhhi / xhlo columns or yhhi / yhlo rows of the tile's edges)
-// are visited: whole rim rows, then the rim columns of the other rows.
-constexpr int kMergeThreads = 256;
-
-__global__ void __launch_bounds__(kMergeThreads) k_merge_halo4(erpp_kparams kp,
-                                                               float* __restrict__ S,
-                                                               const float* __restrict__ halo) {
-  const int hx = kp.xhlo + kp.xhhi, hy = kp.yhlo + kp.yhhi;
-  const int W = kp.T[0], Ty = kp.T[1];
-  const int tile = blockIdx.x;
-  const int cz = blockIdx.y;  // component * T_z + plane
+// Adds the scatter's halo strips onto the tiles they belong to, in two
+// phases (stream order, each node updated by one thread per phase, so the
+// result is deterministic), one block per (tile, component, plane), periodic
+// in x and y:
+//   k_merge_rows: rows within yhhi / yhlo of the tile's lower / upper edge
+//     receive the y-strips of the lower / upper neighbour (whole rows, 16-byte
+//     chunks when aligned);
+//   k_merge_cols: columns within xhhi / xhlo of the left / right edge receive
+//     the x-strips of the left / right neighbour (same rows) and, in the rim
+//     rows, the x-strips of the diagonal neighbours (their y-halo rows).
+struct MergeTile {
   int b[3], ext[3], t[3];
-  tile_origin4(kp, tile, b, ext, t);
-  const int z = cz % kp.T[2];
-  const int cc = cz / kp.T[2];
-  if (z >= ext[2]) return;
-  const int txy = kp.nt[0] * kp.nt[1];
-  const int txl = t[0] == 0 ? kp.nt[0] - 1 : t[0] - 1;
-  const int txr = t[0] == kp.nt[0] - 1 ? 0 : t[0] + 1;
-  const int tyl = t[1] == 0 ? kp.nt[1] - 1 : t[1] - 1;
-  const int tyr = t[1] == kp.nt[1] - 1 ? 0 : t[1] + 1;
-  auto tid = [&](int ax, int ay) { return (ay * kp.nt[0] + ax) + t[2] * txy; };
-  const int exty_l = min((tyl + 1) * Ty, kp.n[1]) - tyl * Ty;
-  // strips of this (component, plane) in each neighbour's halo block
-  const size_t xs0 = (size_t)cz * (Ty + hy) * hx;
-  const size_t ys0 = (size_t)kp.ystrip_off + (size_t)cz * hy * W;
-  auto base = [&](int id) { return halo + (size_t)id * kp.halo_per_tile; };
-  const float* xL = base(tid(txl, t[1])) + xs0;   // right strip of the left tile
-  const float* xR = base(tid(txr, t[1])) + xs0;   // left strip of the right tile
-  const float* yB = base(tid(t[0], tyl)) + ys0;   // top strip of the lower tile
-  const float* yT = base(tid(t[0], tyr)) + ys0;   // bottom strip of the upper tile
-  const float* xLB = base(tid(txl, tyl)) + xs0;
-  const float* xRB = base(tid(txr, tyl)) + xs0;
-  const float* xLT = base(tid(txl, tyr)) + xs0;
-  const float* xRT = base(tid(txr, tyr)) + xs0;
-  const int xcut = ext[0] - kp.xhlo, ycut = ext[1] - kp.yhlo;
+  int cc, z;
+};
+
+__device__ __forceinline__ bool merge_tile(const erpp_kparams& kp, MergeTile& m) {
+  tile_origin4(kp, blockIdx.x, m.b, m.ext, m.t);
+  m.z = blockIdx.y % kp.T[2];
+  m.cc = blockIdx.y / kp.T[2];
+  return m.z < m.ext[2];
+}
+
+__device__ __forceinline__ int tile_id(const erpp_kparams& kp, int tx, int ty, int tz) {
+  return (tz * kp.nt[1] + ty) * kp.nt[0] + tx;
+}
+
+constexpr int kMergeThreads = 128;
+
+__global__ void __launch_bounds__(kMergeThreads) k_merge_rows(erpp_kparams kp, float* __restrict__ S,
+                                                              const float* __restrict__ halo) {
+  MergeTile m;
+  if (!merge_tile(kp, m)) return;
+  const int W = kp.T[0], hy = kp.yhlo + kp.yhhi;
+  const int tyl = m.t[1] == 0 ? kp.nt[1] - 1 : m.t[1] - 1;
+  const int tyr = m.t[1] == kp.nt[1] - 1 ? 0 : m.t[1] + 1;
+  const size_t ys = (size_t)kp.ystrip_off + (size_t)blockIdx.y * hy * W;
+  const float* yB = halo + (size_t)tile_id(kp, m.t[0], tyl, m.t[2]) * kp.halo_per_tile + ys;
+  const float* yT = halo + (size_t)tile_id(kp, m.t[0], tyr, m.t[2]) * kp.halo_per_tile + ys;
   const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
-  float* splane = S + cc * nn + (size_t)(b[2] + z) * kp.n[1] * kp.n[0];
-  auto node = [&](int x, int y) {
+  float* splane = S + m.cc * nn + (size_t)(m.b[2] + m.z) * kp.n[1] * kp.n[0] + m.b[0];
+  const int ycut = m.ext[1] - kp.yhlo;
+  // rim rows: [0, min(yhhi, ext)) and [max(ycut, yhhi), ext) (all rows when ext < hy)
+  const int na = min(kp.yhhi, m.ext[1]);
+  const int nb = m.ext[1] - max(ycut, na);
+  const int nrows = na + nb;
+  const bool vec = (W & 3) == 0 && (m.ext[0] & 3) == 0 && (kp.n[0] & 3) == 0 && (m.b[0] & 3) == 0 &&
+                   (((uintptr_t)S) & 15) == 0 && (((uintptr_t)halo) & 15) == 0;
+  const int per_row = vec ? m.ext[0] >> 2 : m.ext[0];
+  for (int i = threadIdx.x; i < nrows * per_row; i += kMergeThreads) {
+    const int r = i / per_row;
+    const int j = i - r * per_row;
+    const int y = r < na ? r : max(ycut, na) + (r - na);
+    const bool yl = y < kp.yhhi, yr = y >= ycut;
+    float* d = splane + (size_t)(m.b[1] + y) * kp.n[0];
+    if (vec) {
+      float4 v = reinterpret_cast<float4*>(d)[j];
+      if (yl) {
+        const float4 a = reinterpret_cast<const float4*>(yB + (kp.yhlo + y) * W)[j];
+        v.x += a.x; v.y += a.y; v.z += a.z; v.w += a.w;
+      }
+      if (yr) {
+        const float4 a = reinterpret_cast<const float4*>(yT + (y - ycut) * W)[j];
+        v.x += a.x; v.y += a.y; v.z += a.z; v.w += a.w;
+      }
+      reinterpret_cast<float4*>(d)[j] = v;
+    } else {
+      float v = d[j];
+      if (yl) v += yB[(kp.yhlo + y) * W + j];
+      if (yr) v += yT[(y - ycut) * W + j];
+      d[j] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kMergeThreads) k_merge_cols(erpp_kparams kp, float* __restrict__ S,
+                                                              const float* __restrict__ halo) {
+  MergeTile m;
+  if (!merge_tile(kp, m)) return;
+  const int hx = kp.xhlo + kp.xhhi, hy = kp.yhlo + kp.yhhi;
+  const int Ty = kp.T[1];
+  const int txl = m.t[0] == 0 ? kp.nt[0] - 1 : m.t[0] - 1;
+  const int txr = m.t[0] == kp.nt[0] - 1 ? 0 : m.t[0] + 1;
+  const int tyl = m.t[1] == 0 ? kp.nt[1] - 1 : m.t[1] - 1;
+  const int tyr = m.t[1] == kp.nt[1] - 1 ? 0 : m.t[1] + 1;
+  const size_t xs = (size_t)blockIdx.y * (Ty + hy) * hx;
+  auto strip = [&](int tx, int ty) {
+    return halo + (size_t)tile_id(kp, tx, ty, m.t[2]) * kp.halo_per_tile + xs;
+  };
+  const float* xL = strip(txl, m.t[1]);
+  const float* xR = strip(txr, m.t[1]);
+  const float* xLB = strip(txl, tyl);
+  const float* xRB = strip(txr, tyl);
+  const float* xLT = strip(txl, tyr);
+  const float* xRT = strip(txr, tyr);
+  const int exty_l = min((tyl + 1) * Ty, kp.n[1]) - tyl * Ty;
+  const int xcut = m.ext[0] - kp.xhlo, ycut = m.ext[1] - kp.yhlo;
+  const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
+  float* splane = S + m.cc * nn + (size_t)(m.b[2] + m.z) * kp.n[1] * kp.n[0] + m.b[0];
+  const bool allcols = m.ext[0] < hx;
+  const int ncol = allcols ? m.ext[0] : hx;
+  for (int i = threadIdx.x; i < m.ext[1] * ncol; i += kMergeThreads) {
+    const int y = i / ncol;
+    const int j = i - y * ncol;
+    const int x = allcols || j < kp.xhhi ? j : xcut + (j - kp.xhhi);
     const bool xl = x < kp.xhhi, xr = x >= xcut;
     const bool yl = y < kp.yhhi, yr = y >= ycut;
     float add = 0.f;
     if (xl) add += xL[(y + kp.yhlo) * hx + kp.xhlo + x];
     if (xr) add += xR[(y + kp.yhlo) * hx + x - xcut];
-    if (yl) add += yB[(kp.yhlo + y) * W + x];
-    if (yr) add += yT[(y - ycut) * W + x];
     if (xl && yl) add += xLB[(exty_l + kp.yhlo + y) * hx + kp.xhlo + x];
     if (xr && yl) add += xRB[(exty_l + kp.yhlo + y) * hx + x - xcut];
     if (xl && yr) add += xLT[(y - ycut) * hx + kp.xhlo + x];
     if (xr && yr) add += xRT[(y - ycut) * hx + x - xcut];
-    splane[(size_t)(b[1] + y) * kp.n[0] + b[0] + x] += add;
-  };
-  // rim nodes as one flat list: whole rim rows (all rows when the tile is no
-  // taller than the halo), then the rim columns of the other rows (all
-  // columns when the tile is no wider than the halo)
-  const bool allrows = ext[1] < hy;
-  const int nrim = allrows ? ext[1] : hy;
-  const bool allcols = ext[0] < hx;
-  const int ncol = allcols ? ext[0] : hx;
-  const int nmid = allrows ? 0 : ycut - kp.yhhi;
-  const int nA = nrim * ext[0];
-  const int total = nA + nmid * ncol;
-  for (int i = threadIdx.x; i < total; i += kMergeThreads) {
-    int x, y;
-    if (i < nA) {
-      const int rr = i / ext[0];
-      x = i - rr * ext[0];
-      y = allrows || rr < kp.yhhi ? rr : ycut + (rr - kp.yhhi);
-    } else {
-      const int k = i - nA;
-      const int yy = k / ncol;
-      const int j = k - yy * ncol;
-      y = kp.yhhi + yy;
-      x = allcols || j < kp.xhhi ? j : xcut + (j - kp.xhhi);
-    }
-    node(x, y);
+    if (xl || xr) splane[(size_t)(m.b[1] + y) * kp.n[0] + x] += add;
   }
 }
 
-template <int XM, int LMIN, int XW>
-cudaError_t gather4(erpp_ctx* ctx, const float* u, cudaStream_t st) {
+template <int XM, int LMIN, int XW, int NT>
+cudaError_t gather4_nt(erpp_ctx* ctx, const float* u, cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;
   const size_t sm = carve_bytes<XW>(kp.plane, 3, true);
-  cudaError_t e = cudaFuncSetAttribute(k_gather4<XM, LMIN, XW>,
+  cudaError_t e = cudaFuncSetAttribute(k_gather4<XM, LMIN, XW, NT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_gather4<XM, LMIN, XW><<<kp.ntiles, kThreads, sm, st>>>(
+  k_gather4<XM, LMIN, XW, NT><<<kp.ntiles, NT, sm, st>>>(
       kp, u, ctx->tile_start, ctx->entries, ctx->entries_cap, ctx->xw, ctx->up_acc, ctx->cap);
   return cudaGetLastError();
 }
 
-template <int XM, int LMIN, int XW, int MODE>
+template <int XM, int LMIN, int XW>
+cudaError_t gather4(erpp_ctx* ctx, const float* u, cudaStream_t st) {
+  return ctx->kp.nthreads == 512 ? gather4_nt<XM, LMIN, XW, 512>(ctx, u, st)
+                                 : gather4_nt<XM, LMIN, XW, 256>(ctx, u, st);
+}
+
+template <int XM, int LMIN, int XW, int MODE, int NT>
 cudaError_t scatter4_mode(erpp_ctx* ctx, float* S, cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;
   const size_t sm = carve_bytes<XW>(kp.plane, MODE == 1 ? 6 : 3, false);
-  cudaError_t e = cudaFuncSetAttribute(k_scatter4<XM, LMIN, XW, MODE>,
+  cudaError_t e = cudaFuncSetAttribute(k_scatter4<XM, LMIN, XW, MODE, NT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_scatter4<XM, LMIN, XW, MODE><<<kp.ntiles, kThreads, sm, st>>>(
+  k_scatter4<XM, LMIN, XW, MODE, NT><<<kp.ntiles, NT, sm, st>>>(
       kp, S, ctx->halo, ctx->tile_start, ctx->entries, ctx->entries_cap, ctx->xw, ctx->fscat);
   return cudaGetLastError();
 }
 
 template <int XM, int LMIN, int XW>
 cudaError_t scatter4(erpp_ctx* ctx, float* S, cudaStream_t st) {
-  return ctx->kp.kahan ? scatter4_mode<XM, LMIN, XW, 1>(ctx, S, st)
-                       : scatter4_mode<XM, LMIN, XW, 0>(ctx, S, st);
+  const bool big = ctx->kp.nthreads == 512;
+  if (ctx->kp.kahan)
+    return big ? scatter4_mode<XM, LMIN, XW, 1, 512>(ctx, S, st)
+               : scatter4_mode<XM, LMIN, XW, 1, 256>(ctx, S, st);
+  return big ? scatter4_mode<XM, LMIN, XW, 0, 512>(ctx, S, st)
+             : scatter4_mode<XM, LMIN, XW, 0, 256>(ctx, S, st);
 }
 
 }  // namespace
@@ -918,8 +968,9 @@ cudaError_t launch_scatter_f32_4(erpp_ctx* ctx, float* S, cudaStream_t st) {
     default: e = scatter4<16, 1, 16>(ctx, S, st); break;
   }
   if (e != cudaSuccess) return e;
-  k_merge_halo4<<<dim3(ctx->kp.ntiles, 3 * ctx->kp.T[2]), kMergeThreads, 0, st>>>(ctx->kp, S,
-                                                                                 ctx->halo);
+  const dim3 mg(ctx->kp.ntiles, 3 * ctx->kp.T[2]);
+  k_merge_rows<<<mg, kMergeThreads, 0, st>>>(ctx->kp, S, ctx->halo);
+  k_merge_cols<<<mg, kMergeThreads, 0, st>>>(ctx->kp, S, ctx->halo);
   return cudaGetLastError();
 }
 

@@ -199,14 +199,15 @@ class Context:
     def check(self, stream=None):
         _lib.check(self.lib.erpp_check(self._h, _stream(stream)), "erpp_check")
 
-    def set_tiling(self, tile_y=0, tile_z=0):
-        """Request T_y, T_z of the x/y-halo tiles (0 = default)."""
-        _lib.check(self.lib.erpp_set_tiling(self._h, int(tile_y), int(tile_z)),
+    def set_tiling(self, tile_y=0, tile_z=0, threads=0):
+        """Request T_y, T_z and threads per block of the x/y-halo tiles
+        (0 = default)."""
+        _lib.check(self.lib.erpp_set_tiling(self._h, int(tile_y), int(tile_z), int(threads)),
                    "erpp_set_tiling")
 
     def tiling(self):
-        """(design, W, T_y, T_z) of the tiles in use."""
-        out = (ctypes.c_int32 * 4)()
+        """(design, W, T_y, T_z, threads) of the tiles in use."""
+        out = (ctypes.c_int32 * 5)()
         _lib.check(self.lib.erpp_get_tiling(self._h, out), "erpp_get_tiling")
         return tuple(int(v) for v in out)
 

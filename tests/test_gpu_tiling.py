@@ -44,10 +44,11 @@ CASES = [
                                                  2 * math.pi * 30 / 48),
                                               cluster_std=0.4), 2500),
 ]
-TILES = [(16, 4), (8, 4), (16, 2), (32, 2), (8, 2), (32, 1), (5, 1), (32, 4)]
+TILES = [(16, 4, 256), (8, 4, 256), (16, 2, 256), (32, 2, 256), (8, 2, 256), (32, 1, 256),
+         (5, 1, 256), (32, 4, 256), (16, 4, 512), (32, 2, 512), (8, 2, 512), (32, 1, 512)]
 
 
-@pytest.mark.parametrize("tile", TILES, ids=[f"{a}x{b}" for a, b in TILES])
+@pytest.mark.parametrize("tile", TILES, ids=["x".join(map(str, t)) for t in TILES])
 @pytest.mark.parametrize("name,w,npart", CASES, ids=[c[0] for c in CASES])
 def test_step_every_tiling(erpp, oracle_lib, name, w, npart, tile):
     import torch
@@ -56,8 +57,8 @@ def test_step_every_tiling(erpp, oracle_lib, name, w, npart, tile):
     st = I.make_particles(w, field, n_particles=npart)
     ctx = erpp.Context(p, precision="fp32")
     ctx.set_tiling(*tile)
-    design, W, ty, tz = ctx.tiling()
-    assert design == 4
+    design, W, ty, tz, nt = ctx.tiling()
+    assert design == 4 and nt == tile[2]
     ps = erpp.ParticleState.from_numpy(st)
     S = ctx.step(cuda(grid, torch.float32), ps, first_step=False)
     ctx.check()
@@ -72,7 +73,7 @@ def test_set_tiling_rejects_and_keeps_working(erpp, oracle_lib):
     w = I.CFG_SMALL
     ctx = erpp.Context(w.params(), precision="fp32")
     before = ctx.tiling()
-    for bad in ((33, 4), (16, 3), (-1, 4)):
+    for bad in ((33, 4, 0), (16, 3, 0), (-1, 4, 0), (16, 4, 384)):
         with pytest.raises(erpp.ErppError):
             ctx.set_tiling(*bad)
     assert ctx.tiling() == before
