@@ -11,8 +11,11 @@
 // at x' = xoff (xhlo rounded up to a multiple of 4, so that the interior is
 // 16-byte aligned); PX and the plane pitch PXY are both 16 (mod 32), so node
 // (x', y', z') sits in shared-memory bank (x' + 16 (y' + z')) mod 32.
-// Staging uses asynchronous global-to-shared copies (16-byte chunks for the
-// aligned interior, 4-byte copies for the halo columns, periodic wrap).
+// Staging: a tile whose staged box needs no periodic wrap (and whose layout
+// has no plane padding) is loaded by one TMA copy of the 4D box
+// (x, y, z, component) of the field, completed on an mbarrier; the others use
+// asynchronous global-to-shared copies (16-byte chunks for the aligned
+// interior, 4-byte copies for the wrapped halo columns and rows).
 //
 // Units and buckets.  A unit is one z-plane of a piece: ly rows of lx nodes,
 // the same for every particle (lx, ly = the window lengths).  Walking its rows
@@ -53,9 +56,14 @@
 // (two-sum on the atomic's old value) kept in a second array.  The interior
 // is written once; the halo strips go to a buffer that k_merge_rows and
 // k_merge_cols add to the neighbouring tiles in a fixed order.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <string.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "erpp_internal.cuh"
 
@@ -108,6 +116,48 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
+
+// ---- TMA box load completed on an mbarrier (bounded wait) ----
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Waits for phase `parity` of the barrier, at most `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int limit) {
+  for (int i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+constexpr int kTmaWaitPolls = 1 << 22;
 
 // ---- shared-memory accesses by 32-bit shared address, immediate offsets ----
 __device__ __forceinline__ unsigned shared_addr(const void* p) {
@@ -442,11 +492,13 @@ struct UnitRows {
 // x-weights stored per particle.
 template <int XM, int LMIN, int XW, int NT>
 __global__ void __launch_bounds__(NT, 2) k_gather4(
-    erpp_kparams kp, const float* __restrict__ u, const int32_t* __restrict__ start,
-    const int4* __restrict__ entries, int64_t ecap, const float* __restrict__ xw,
-    float* __restrict__ up_acc, int64_t acc_stride) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+    erpp_kparams kp, const float* __restrict__ u, const __grid_constant__ CUtensorMap tmap,
+    int use_tma, const int32_t* __restrict__ start, const int4* __restrict__ entries,
+    int64_t ecap, const float* __restrict__ xw, float* __restrict__ up_acc, int64_t acc_stride,
+    uint32_t* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SchedState ss;
+  __shared__ __align__(8) uint64_t tma_bar;
   constexpr int PB = Batch<XW>::kPB;
   const int tile = blockIdx.x;
   const int e0 = start[tile];
@@ -455,7 +507,21 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
   const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, 3, true);
   int b[3], ext[3], tt[3];
   tile_origin4(kp, tile, b, ext, tt);
-  stage_tile4<NT>(kp, u, cv.field, b, ext);
+  // one TMA box when the staged rows need no periodic wrap
+  const int hy = kp.yhlo + kp.yhhi;
+  const int x0 = b[0] - kp.xoff, y0 = b[1] - kp.yhlo;
+  const bool tma = use_tma && x0 >= 0 && x0 + kp.px <= kp.n[0] && y0 >= 0 &&
+                   y0 + kp.T[1] + hy <= kp.n[1];
+  if (tma) {
+    if (threadIdx.x == 0) {
+      mbar_init(&tma_bar, 1);
+      mbar_expect_tx(&tma_bar, (unsigned)(3 * kp.plane * 4));
+      tma_load_4d(cv.field, &tmap, &tma_bar, x0, y0, b[2], 0);
+    }
+  } else {
+    stage_tile4<NT>(kp, u, cv.field, b, ext);
+  }
+  bool staged = false;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int plane = kp.plane, px = kp.px, pxy = kp.pxy;
   const float by = kp.beta[1], bz = kp.beta[2];
@@ -467,6 +533,15 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
     for (int k = threadIdx.x; k < 3 * PB; k += NT) cv.pacc[k] = 0.f;
     const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
     cp_async_wait_all();                            // field (first batch), x-weights
+    if (tma && !staged) {
+      staged = true;
+      if (!mbar_wait_bounded(&tma_bar, 0, kTmaWaitPolls)) {
+        // the copy did not complete: report, wait once more for it, give up
+        if (threadIdx.x == 0) erpp_set_err(err, ERPP_ERRBIT_TIMEOUT);
+        mbar_wait_bounded(&tma_bar, 0, kTmaWaitPolls);
+        return;
+      }
+    }
     __syncthreads();
     for (int r = 0; r < R; ++r) {
       const uint16_t ui = cv.sched[r * NT + warp * 32 + lane];
@@ -887,6 +962,44 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_cols(erpp_kparams kp, f
   }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null when unavailable.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of the field u for the staged box [PX x NY x T_z x 3] (the
+// shared layout without plane padding).  False when the layout or the
+// alignment does not allow it (the kernels then stage with cp.async).
+bool field_tensor_map(const erpp_kparams& kp, const float* u, CUtensorMap* map) {
+  const int ny_st = kp.T[1] + kp.yhlo + kp.yhhi;
+  if ((kp.n[0] & 3) || (kp.T[0] & 3) || (kp.xoff & 3) || kp.pxy != kp.px * ny_st ||
+      (((uintptr_t)u) & 15) || kp.px > 256 || ny_st > 256 || kp.T[2] > 256)
+    return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)kp.n[0], (cuuint64_t)kp.n[1], (cuuint64_t)kp.n[2], 3};
+  const cuuint64_t strides[3] = {(cuuint64_t)kp.n[0] * 4, (cuuint64_t)kp.n[0] * kp.n[1] * 4,
+                                 (cuuint64_t)kp.n[0] * kp.n[1] * kp.n[2] * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)kp.px, (cuuint32_t)ny_st, (cuuint32_t)kp.T[2], 3};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(u), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int XM, int LMIN, int XW, int NT>
 cudaError_t gather4_nt(erpp_ctx* ctx, const float* u, cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;
@@ -894,8 +1007,12 @@ cudaError_t gather4_nt(erpp_ctx* ctx, const float* u, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_gather4<XM, LMIN, XW, NT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_gather4<XM, LMIN, XW, NT><<<kp.ntiles, NT, sm, st>>>(
-      kp, u, ctx->tile_start, ctx->entries, ctx->entries_cap, ctx->xw, ctx->up_acc, ctx->cap);
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  const int use_tma = field_tensor_map(kp, u, &map) ? 1 : 0;
+  k_gather4<XM, LMIN, XW, NT><<<kp.ntiles, NT, sm, st>>>(kp, u, map, use_tma, ctx->tile_start,
+                                                         ctx->entries, ctx->entries_cap, ctx->xw,
+                                                         ctx->up_acc, ctx->cap, ctx->err);
   return cudaGetLastError();
 }
 

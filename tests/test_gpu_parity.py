@@ -66,6 +66,11 @@ CASES = [
     # y spacing a third of x: y-windows of 19 nodes, beyond the x/y-halo tiles
     # (the kernels cut pieces in y and z instead)
     ("fine_y_32x96x24", rep(I.CFG_SMALL, n=(32, 96, 24), kmax=3.0), 1500),
+    # large enough for tiles whose staged box needs no periodic wrap (staged
+    # by one TMA copy) next to wrapping ones
+    ("tma_256x64x16", rep(I.CFG_SMALL, n=(256, 64, 16), kmax=3.0,
+                          L=(2 * math.pi, 2 * math.pi * 64 / 256, 2 * math.pi * 16 / 256)),
+     20000),
 ]
 
 
