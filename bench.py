@@ -66,10 +66,8 @@ def parse():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1405_6969_gb300 import dist as D
+    return D.env()
 
 
 def measured_peaks():
@@ -219,8 +217,12 @@ def run_batched(args, ws, rank, local):
     """64 independent boxes: one replayed CUDA graph per step, against the
     same boxes as 64 plain launch sequences and against the plain FP64 form."""
     import torch
+    import torch.distributed as dist
     from paper_1405_6969_gb300 import Batch, ParticleState
-    boxes = I.batched_boxes(64, seed0=64 * rank)
+    from paper_1405_6969_gb300 import dist as D
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    boxes = I.batched_boxes(64, seed0=D.batched_seed0(rank))
     nodes_per_step = 0
     made = []
     for w in boxes:
@@ -243,6 +245,7 @@ def run_batched(args, ws, rank, local):
         for k in range(args.warmup):
             b.step(first_step=(k == 0), use_graph=use_graph)
         b.check()
+        D.barrier()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -251,10 +254,18 @@ def run_batched(args, ws, rank, local):
             b.step(use_graph=use_graph)
         e1.record(stream)
         torch.cuda.synchronize()
+        D.barrier()
         b.check()
-        return e0.elapsed_time(e1) / steps
+        return D.max_over_ranks(e0.elapsed_time(e1) / steps, device="cuda")
 
     b32 = batch("fp32")
+    tiles = None
+    if not args.no_autotune:
+        import collections
+        import tempfile
+        cache = os.path.join(tempfile.mkdtemp(), "tune.json")
+        tiles = collections.Counter("x".join(map(str, t)) if t else "x-halo"
+                                    for t in b32.autotune(cache_path=cache))
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
@@ -265,7 +276,7 @@ def run_batched(args, ws, rank, local):
     b64 = batch("fp64")
     ms_f64 = timed(b64, False, max(3, min(args.steps // 10, 10)))
     b64.close()
-    value = nodes_per_step / (ms_graph * 1e-3)
+    value = D.aggregate_rate(nodes_per_step, ws, ms_graph * 1e-3)
     if rank == 0:
         n_p = sum(w.n_particles for w, _, _ in made)
         line = {
@@ -283,12 +294,15 @@ def run_batched(args, ws, rank, local):
             "graph_speedup_vs_plain_launches": ms_eager / ms_graph,
             "fp64_plain_form_ms_per_step": ms_f64,
             "speedup_vs_fp64_plain_form": ms_f64 / ms_graph,
+            "tiles_per_box": dict(tiles) if tiles else None,
             "roofline": None, "cpu_baseline": None,
             "e2e": None,
             "gpu_launches": 10 * len(made) * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
 
 
 def main():
@@ -314,7 +328,8 @@ def main():
     libbuild.build()
 
     w = WORKLOAD if args.workload == "shear" else I.CFG_CUBE256
-    seed = rank
+    from paper_1405_6969_gb300 import dist as D
+    seed = D.box_seed(0, rank)
     grid64, _ = I.make_grid(w, seed=w.field_seed + seed)
     st = I.make_particles(w, None, seed=w.particle_seed + seed)
     u = torch.as_tensor(grid64, dtype=torch.float32).cuda().contiguous()

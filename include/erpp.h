@@ -249,6 +249,12 @@ erpp_status erpp_batch_init(int32_t nbox, const erpp_box_desc* boxes, erpp_batch
 erpp_status erpp_step_batched(erpp_batch* batch, int first_step, int use_graph,
                               erpp_stream stream);
 
+/* erpp_set_tiling for one box (0 <= box < nbox) of the batch; the box's
+ * scratch is reallocated at once and captured graphs are discarded (the next
+ * erpp_step_batched with a graph captures again). */
+erpp_status erpp_batch_set_tiling(erpp_batch* batch, int32_t box, int32_t tile_y,
+                                  int32_t tile_z, int32_t threads);
+
 /* erpp_check over every box: synchronises `stream`, returns the first error
  * found (and clears each box's error word). */
 erpp_status erpp_batch_check(erpp_batch* batch, erpp_stream stream);

@@ -86,6 +86,8 @@ _SIGS = {
     "erpp_batch_init": (_st, [ctypes.c_int32, ctypes.POINTER(BoxDesc), ctypes.POINTER(_vp)]),
     "erpp_step_batched": (_st, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
     "erpp_batch_check": (_st, [_vp, _vp]),
+    "erpp_batch_set_tiling": (_st, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_int32]),
     "erpp_batch_destroy": (_st, [_vp]),
     "erpp_set_tiling": (_st, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "erpp_get_tiling": (_st, [_vp, ctypes.POINTER(ctypes.c_int32)]),

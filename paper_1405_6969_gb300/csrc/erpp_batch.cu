@@ -172,6 +172,20 @@ erpp_status erpp_step_batched(erpp_batch* b, int first_step, int use_graph, erpp
   return cuda_status(cudaGraphLaunch(b->exec[fs], st));
 }
 
+erpp_status erpp_batch_set_tiling(erpp_batch* b, int32_t box, int32_t tile_y, int32_t tile_z,
+                                  int32_t threads) {
+  if (!b || box < 0 || box >= b->nbox) return ERPP_EINVAL;
+  erpp_status s = erpp_set_tiling(b->ctx[box], tile_y, tile_z, threads);
+  // scratch again now (never during a capture), and the graphs hold the old
+  // launch configuration
+  if (s == ERPP_OK) s = erpp::ensure_capacity(b->ctx[box], b->boxes[box].particles.n);
+  for (int k = 0; k < 2; ++k) {
+    if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+    b->exec[k] = nullptr;
+  }
+  return s;
+}
+
 erpp_status erpp_batch_check(erpp_batch* b, erpp_stream stream) {
   if (!b) return ERPP_EINVAL;
   erpp_status worst = ERPP_OK;

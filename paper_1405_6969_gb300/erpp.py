@@ -296,6 +296,32 @@ class Batch:
         h = ctypes.c_void_p()
         _lib.check(self.lib.erpp_batch_init(len(boxes), arr, ctypes.byref(h)), "erpp_batch_init")
         self._h = h
+        self._opts = dict(precision=precision, normalize=normalize, self_removal=self_removal,
+                          kahan=kahan)
+        self._boxes = list(boxes)
+
+    def set_tiling(self, box, tile_y=0, tile_z=0, threads=0):
+        _lib.check(self.lib.erpp_batch_set_tiling(self._h, int(box), int(tile_y), int(tile_z),
+                                                  int(threads)), "erpp_batch_set_tiling")
+
+    def autotune(self, steps=3, warmup=1, cache_path=None, use_cache=True):
+        """Tile shape per box: each box is tuned on a stand-alone context with
+        its own data (the autotuner's cache shares results between boxes of
+        the same class) and the choice is applied to the batch.  Returns the
+        chosen (T_y, T_z, threads) per box."""
+        from . import autotune
+        chosen = []
+        for i, (params, u, state, _S) in enumerate(self._boxes):
+            ctx = Context(params, **self._opts)
+            try:
+                r = autotune.tune(ctx, u, state, steps=steps, warmup=warmup,
+                                  cache_path=cache_path, use_cache=use_cache)
+            finally:
+                ctx.close()
+            if r["tile"] is not None:
+                self.set_tiling(i, *r["tile"])
+            chosen.append(r["tile"])
+        return chosen
 
     def step(self, first_step=False, use_graph=True, stream=None):
         _lib.check(self.lib.erpp_step_batched(self._h, int(bool(first_step)),

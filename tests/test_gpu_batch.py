@@ -134,3 +134,34 @@ def test_batch_rejects_bad_descriptors(erpp):
     bad = dict(w.params(), cutoff=40.0)  # 2 r_c beyond the box
     with pytest.raises(erpp.ErppError):
         erpp.Batch([(bad, u, ps, torch.empty_like(u))])
+
+
+def test_batch_autotune_keeps_results(erpp, oracle_lib, tmp_path):
+    """Per-box tile shapes chosen by the autotuner (graphs captured again
+    afterwards) give the same results as the oracle."""
+    boxes = small_boxes()
+    entries, refs = _build(erpp, "fp32", boxes)
+    batch = erpp.Batch(entries, precision="fp32")
+    batch.step(first_step=True)            # a graph captured with default tiles
+    chosen = batch.autotune(steps=1, warmup=1, cache_path=str(tmp_path / "t.json"))
+    assert len(chosen) == len(boxes)
+    batch.step(first_step=True)            # captured again with the new tiles
+    batch.step(first_step=False)
+    batch.check()                          # replays ran without device errors
+    batch.close()
+    # a fresh batch with the chosen shapes against the oracle, two steps
+    entries, refs = _build(erpp, "fp32", boxes)
+    batch = erpp.Batch(entries, precision="fp32")
+    for i, t in enumerate(chosen):
+        if t is not None:
+            batch.set_tiling(i, *t)
+    for k in range(2):
+        batch.step(first_step=(k == 0))
+        for (p, _, _, _), (grid, ref) in zip(entries, refs):
+            oracle_lib.step(p, grid, ref, first_step=(k == 0))
+    batch.check()
+    for (p, u, ps, S), (grid, ref), w in zip(entries, refs, boxes):
+        S_ref = oracle_lib.scatter(p, ref.x_prev, ref.D)
+        assert rel(S.cpu().numpy(), S_ref) < 1e-5, w.name
+        assert rel(ps.D.cpu().numpy(), ref.D) < 1e-5, w.name
+    batch.close()

@@ -188,6 +188,38 @@ def test_clustered_ten_steps(erpp, oracle_lib, precision):
     assert rel(ps.v.cpu().numpy(), ref.v) < tol
 
 
+@pytest.mark.parametrize("mode", ["fp32", "fp32_kahan", "fp64"])
+def test_clustered_full_size_error_report(erpp, oracle_lib, mode):
+    """The clustered FP32-versus-FP64 workload at full size: 128^3, 100k
+    particles in 50 clusters, sigma_R = 1.5 dx, mean shear 1, ten coupled
+    steps with the fluid frozen.  Prints the relative L2 error of every result
+    (source, forces, velocities, positions) against the FP64 oracle and holds
+    it to the tolerance of one step times the number of steps (errors
+    compound through the particle state)."""
+    w = I.CFG_CLUSTERED
+    p = w.params()
+    grid, st = _setup(w, w.n_particles)
+    precision = "fp64" if mode == "fp64" else "fp32"
+    ctx = erpp.Context(p, precision=precision, kahan=(mode == "fp32_kahan"))
+    ps = erpp.ParticleState.from_numpy(st)
+    u = grid_t(grid, precision)
+    ref = st.copy()
+    for k in range(10):
+        S = ctx.step(u, ps, first_step=(k == 0))
+        S_ref = oracle_lib.step(p, grid, ref, first_step=(k == 0))
+    ctx.check()
+    errs = {"S": rel(S.cpu().numpy(), S_ref), "D": rel(ps.D.cpu().numpy(), ref.D),
+            "v": rel(ps.v.cpu().numpy(), ref.v)}
+    dxp = np.abs(ps.x.cpu().numpy() - ref.x)
+    dxp = np.minimum(dxp, np.array(w.L)[:, None] - dxp)
+    errs["x_max_abs"] = float(dxp.max())
+    print(f"\nclustered 128^3 / 100k, 10 steps, {mode}: " +
+          ", ".join(f"{k} {v:.3e}" for k, v in errs.items()))
+    tol = 10 * TOL[precision]
+    assert errs["S"] < tol and errs["D"] < tol and errs["v"] < tol
+    assert errs["x_max_abs"] < (1e-12 if precision == "fp64" else 1e-9)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_momentum_conservation(erpp, oracle_lib, precision):
     w = rep(I.CFG_CLUSTERED, n=(72, 40, 20))
