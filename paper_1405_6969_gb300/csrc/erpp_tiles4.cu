@@ -26,8 +26,8 @@
 // by row in lockstep by the 32 lanes of a warp, never share a bank.  A unit
 // may start at its second row and end with its first (a rotation of its
 // rows), which moves it to bucket b ^ 16 (for an even ly without any cost; for
-// an odd ly its last row may share a bank); the schedule gives each unit the
-// less loaded of its two buckets.
+// an odd ly its last row may share a bank); the schedule splits the units of
+// every bucket pair evenly between its two buckets.
 //
 // Schedule.  Per batch of pieces the block builds a table
 // sched[round][warp][lane]: bucket b's k-th unit goes to lane b of warp k mod 8
@@ -324,6 +324,7 @@ __device__ inline Carve<XW> carve(unsigned char* base, int plane, int copies, bo
 }
 
 struct SchedState {
+  int pair[16];
   int cnt[32];
   int vpre[33];
   int nunits;
@@ -402,26 +403,32 @@ template <int XW, int NT>
 __device__ int build_schedule(const Carve<XW>& cv, SchedState& ss, int np) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x;
-  if (tid < 32) ss.cnt[tid] = 0;
+  if (tid < 16) ss.pair[tid] = 0;
   if (tid == 0) {
     ss.nunits = 0;
     ss.novf = 0;
   }
   __syncthreads();
+  // Buckets b and b ^ 16 form a pair (every unit can take either, by rotating
+  // its rows): the k-th unit of a pair goes to the lower bucket for even k and
+  // to the upper one for odd k, so a pair's units split evenly.
   for (int k = tid; k < np; k += NT) {
     const Piece4 pc = unpack4(cv.rec[k]);
     const int ub = atomicAdd(&ss.nunits, pc.lz);
     for (int z = 0; z < pc.lz; ++z) {
-      const int b0 = (pc.x0 + 16 * ((pc.y0 + pc.z0 + z) & 1)) & 31;
-      const int b1 = b0 ^ 16;  // rows rotated by one
-      const uint32_t rot = *((volatile int*)&ss.cnt[b1]) < *((volatile int*)&ss.cnt[b0]) ? 1u : 0u;
-      const int bucket = rot ? b1 : b0;
-      const int slot = atomicAdd(&ss.cnt[bucket], 1);
+      const int natural = (pc.x0 + 16 * ((pc.y0 + pc.z0 + z) & 1)) & 31;
+      const int pr = natural & 15;
+      const int idx = atomicAdd(&ss.pair[pr], 1);
+      const int bucket = pr + 16 * (idx & 1);
+      const uint32_t rot = bucket != natural ? 1u : 0u;
       cv.unit[ub + z] = (uint32_t)k | ((uint32_t)z << 10) | ((uint32_t)bucket << 14) |
-                        ((uint32_t)min(slot, 4095) << 19) | (rot << 31);
+                        ((uint32_t)min(idx >> 1, 4095) << 19) | (rot << 31);
     }
   }
   __syncthreads();
+  if (tid < 32) ss.cnt[tid] = (ss.pair[tid & 15] + (tid < 16 ? 1 : 0)) >> 1;
+  // Rounds: the fewest that hold every unit (measured faster than one more
+  // round that would leave no bucket overflowing)
   const int U = ss.nunits;
   const int R = (U + NT - 1) / NT;
   const int cap = NW * R;
