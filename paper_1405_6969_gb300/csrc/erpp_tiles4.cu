@@ -116,6 +116,20 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
+// Shared-memory writes of this thread made visible to the asynchronous proxy
+// (bulk copies issued after the next barrier read them).
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// Bulk copy shared -> global (both 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_store_s2g(void* dst, unsigned src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n"
+               :: "l"(dst), "r"(src), "r"(bytes) : "memory");
+}
+// Waits until this thread's bulk copies have read their shared-memory source.
+__device__ __forceinline__ void bulk_commit_wait_read() {
+  asm volatile("cp.async.bulk.commit_group;\n\tcp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
 
 // ---- TMA box load completed on an mbarrier (bounded wait) ----
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -648,10 +662,12 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
   float scale = 1.f, inv_scale = 1.f;
   int* acc_i = reinterpret_cast<int*>(smem);
   float* comp_lo = smem + 3 * plane;
-  if (any) {
+  {
     const int total = (MODE == 1 ? 6 : 3) * plane;
     float4* s4 = reinterpret_cast<float4*>(smem);
     for (int k = threadIdx.x; k < total / 4; k += NT) s4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (any) {
     if (fixedp) {
       float bsum = 0.f;
       for (int e = e0 + threadIdx.x; e < e1; e += NT)
@@ -784,10 +800,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
   }
   // interior once (zeros for empty tiles); halo strips to the buffer:
   // x-strips [3][T_z][T_y + hy][hx] (all staged rows), y-strips [3][T_z][hy][W]
-  // (16-byte aligned).  Per staged row the lanes take jobs: 16-byte chunks
-  // of the interior columns (to S, or to the y-strip on a y-halo row) when
-  // everything is aligned, else single words; then the hx halo columns (to
-  // the x-strip).
+  // (16-byte aligned).
   const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
   const int hx = kp.xhlo + kp.xhhi, hy = kp.yhlo + kp.yhhi;
   const int ny_st = ext[1] + hy;
@@ -796,6 +809,70 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
   const bool vec = (kp.n[0] & 3) == 0 && (ext[0] & 3) == 0 && (b[0] & 3) == 0 &&
                    (kp.T[0] & 3) == 0 && (((uintptr_t)S) & 15) == 0 &&
                    (((uintptr_t)halo) & 15) == 0;
+  if (vec && hx <= 16) {
+    // Aligned rows: the final values are formed in place, then every staged
+    // row's interior columns leave by one bulk asynchronous copy (to S, or to
+    // the y-strip on a y-halo row) and the hx halo columns of all rows by
+    // plain stores (to the x-strip, contiguous per component and plane).
+    float4* s4 = reinterpret_cast<float4*>(smem);
+    if (any && (MODE == 1 || fixedp)) {
+      const int total4 = 3 * plane / 4;
+      for (int k = threadIdx.x; k < total4; k += NT) {
+        float4 v;
+        if (MODE == 1) {
+          v = s4[k];
+          const float4 l = s4[total4 + k];
+          v.x += l.x;
+          v.y += l.y;
+          v.z += l.z;
+          v.w += l.w;
+        } else {
+          const int4 q = reinterpret_cast<const int4*>(smem)[k];
+          v = make_float4((float)q.x * inv_scale, (float)q.y * inv_scale, (float)q.z * inv_scale,
+                          (float)q.w * inv_scale);
+        }
+        s4[k] = v;
+      }
+    }
+    fence_proxy_async_shared();
+    __syncthreads();
+    const unsigned fbase = shared_addr(smem);
+    const int nrow = 3 * ext[2] * ny_st;
+    bool issued = false;
+    for (int r = threadIdx.x; r < nrow; r += NT) {
+      const int cz = r / ny_st;
+      const int y = r - cz * ny_st;
+      const int cc = cz / ext[2];
+      const int z = cz - cc * ext[2];
+      const int so = cc * plane + z * pxy + y * px + kp.xoff;
+      const bool yint = y >= kp.yhlo && y < kp.yhlo + ext[1];
+      const int yh = y < kp.yhlo ? y : y - ext[1];
+      float* drow = yint ? S + cc * nn +
+                               ((size_t)(b[2] + z) * kp.n[1] + (b[1] + y - kp.yhlo)) * kp.n[0] +
+                               b[0]
+                         : hys + (((size_t)cc * kp.T[2] + z) * hy + yh) * kp.T[0];
+      bulk_store_s2g(drow, fbase + 4u * (unsigned)so, 4u * (unsigned)ext[0]);
+      issued = true;
+    }
+    if (issued) bulk_commit_wait_read();
+    const int rpw = 32 / hx;  // staged rows per warp pass
+    const int rsub = lane / hx, h = lane - rsub * hx;
+    const int col = h < kp.xhlo ? kp.xoff - kp.xhlo + h : kp.xoff + ext[0] + (h - kp.xhlo);
+    if (rsub < rpw) {
+      for (int cc = 0; cc < 3; ++cc) {
+        for (int z = 0; z < ext[2]; ++z) {
+          const float* srow = smem + cc * plane + z * pxy + col;
+          float* xs = hxs + ((size_t)cc * kp.T[2] + z) * (kp.T[1] + hy) * hx + h;
+          for (int y = warp * rpw + rsub; y < ny_st; y += NW * rpw) xs[y * hx] = srow[y * px];
+        }
+      }
+    }
+    return;
+  }
+  // General rows: per staged row the lanes take jobs: 16-byte chunks of the
+  // interior columns (to S, or to the y-strip on a y-halo row) when
+  // everything is aligned, else single words; then the hx halo columns (to
+  // the x-strip).
   const int nvec = vec ? ext[0] >> 2 : 0;
   const int jobs = nvec + (vec ? 0 : ext[0]) + hx;
   auto value = [&](int idx) -> float {

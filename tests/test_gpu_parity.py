@@ -71,6 +71,10 @@ CASES = [
     ("tma_256x64x16", rep(I.CFG_SMALL, n=(256, 64, 16), kmax=3.0,
                           L=(2 * math.pi, 2 * math.pi * 64 / 256, 2 * math.pi * 16 / 256)),
      20000),
+    # rows of an odd number of nodes: no 16-byte row alignment, so the tile
+    # kernels stage and write out word by word
+    ("odd_x_45x30x20", rep(I.CFG_SMALL, n=(45, 30, 20), kmax=3.0,
+                           L=(2 * math.pi, 2 * math.pi * 30 / 45, 2 * math.pi * 20 / 45)), 1500),
 ]
 
 
