@@ -172,6 +172,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return false;
 }
 constexpr int kTmaWaitPolls = 1 << 22;
+// Bulk copy global -> shared completed on an mbarrier (both 16-byte aligned,
+// bytes a multiple of 16).
+__device__ __forceinline__ void bulk_load_g2s(unsigned dst, const void* src, unsigned bytes,
+                                              unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
 
 // ---- shared-memory accesses by 32-bit shared address, immediate offsets ----
 __device__ __forceinline__ unsigned shared_addr(const void* p) {
@@ -411,6 +420,44 @@ __device__ void stage_tile4(const erpp_kparams& kp, const float* __restrict__ u,
   }
 }
 
+// Bytes that stage_tile_rows copies for a tile: every staged row in full.
+__device__ __forceinline__ unsigned tile_rows_bytes(const erpp_kparams& kp, const int ext[3]) {
+  return 4u * (unsigned)(3 * ext[2] * (ext[1] + kp.yhlo + kp.yhhi) * kp.px);
+}
+
+// Stages the tile with its x/y halo by bulk copies, one per staged row and
+// periodic segment of it (the rows' px columns start at x = b_x - xoff), all
+// completing on `bar`, whose expected bytes are already set.  Needs rows of
+// a multiple of 4 floats and a 16-byte aligned field.
+template <int NT>
+__device__ void stage_tile_rows(const erpp_kparams& kp, const float* __restrict__ u, float* field,
+                                const int b[3], const int ext[3], uint64_t* bar) {
+  const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
+  const int ny_st = ext[1] + kp.yhlo + kp.yhhi;
+  const int nrow = 3 * ext[2] * ny_st;
+  const unsigned fbase = smem_u32(field), mb = smem_u32(bar);
+  int gx0 = (b[0] - kp.xoff) % kp.n[0];
+  gx0 = gx0 < 0 ? gx0 + kp.n[0] : gx0;
+  for (int r = threadIdx.x; r < nrow; r += NT) {
+    const int cz = r / ny_st;
+    const int y = r - cz * ny_st;
+    const int cc = cz / ext[2];
+    const int z = cz - cc * ext[2];
+    int gy = b[1] - kp.yhlo + y;
+    gy = gy < 0 ? gy + kp.n[1] : (gy >= kp.n[1] ? gy - kp.n[1] : gy);
+    const float* grow = u + cc * nn + ((size_t)(b[2] + z) * kp.n[1] + gy) * kp.n[0];
+    unsigned dst = fbase + 4u * (unsigned)(cc * kp.plane + z * kp.pxy + y * kp.px);
+    int gx = gx0, left = kp.px;
+    while (left > 0) {
+      const int seg = min(left, kp.n[0] - gx);
+      bulk_load_g2s(dst, grow + gx, 4u * (unsigned)seg, mb);
+      dst += 4u * (unsigned)seg;
+      left -= seg;
+      gx = 0;
+    }
+  }
+}
+
 // Builds the unit schedule of pieces [0, np) (records in cv.rec).  Returns
 // the number of rounds.  Called by the whole block; synchronises.
 template <int XW, int NT>
@@ -533,13 +580,23 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
   const int x0 = b[0] - kp.xoff, y0 = b[1] - kp.yhlo;
   const bool tma = use_tma && x0 >= 0 && x0 + kp.px <= kp.n[0] && y0 >= 0 &&
                    y0 + kp.T[1] + hy <= kp.n[1];
-  if (tma) {
-    if (threadIdx.x == 0) {
-      mbar_init(&tma_bar, 1);
+  // otherwise bulk row copies when rows are whole 16-byte chunks, else
+  // word-level asynchronous copies
+  const bool rows = !tma && (kp.n[0] & 3) == 0 && (b[0] & 3) == 0 && (kp.xoff & 3) == 0 &&
+                    (kp.px & 3) == 0 && (((uintptr_t)u) & 15) == 0;
+  if (threadIdx.x == 0 && (tma || rows)) {
+    mbar_init(&tma_bar, 1);
+    if (tma) {
       mbar_expect_tx(&tma_bar, (unsigned)(3 * kp.plane * 4));
       tma_load_4d(cv.field, &tmap, &tma_bar, x0, y0, b[2], 0);
+    } else {
+      mbar_expect_tx(&tma_bar, tile_rows_bytes(kp, ext));
     }
-  } else {
+  }
+  if (rows) {
+    __syncthreads();  // the barrier is initialised and expects the bytes
+    stage_tile_rows<NT>(kp, u, cv.field, b, ext, &tma_bar);
+  } else if (!tma) {
     stage_tile4<NT>(kp, u, cv.field, b, ext);
   }
   bool staged = false;
@@ -554,7 +611,7 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
     for (int k = threadIdx.x; k < 3 * PB; k += NT) cv.pacc[k] = 0.f;
     const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
     cp_async_wait_all();                            // field (first batch), x-weights
-    if (tma && !staged) {
+    if ((tma || rows) && !staged) {
       staged = true;
       if (!mbar_wait_bounded(&tma_bar, 0, kTmaWaitPolls)) {
         // the copy did not complete: report, wait once more for it, give up

@@ -73,6 +73,12 @@ CASES = [
      20000),
     # rows of an odd number of nodes: no 16-byte row alignment, so the tile
     # kernels stage and write out word by word
+    # sigma_R = 1.5 dx: x-tiles of 34 nodes (the second starts off a 16-byte
+    # boundary and is staged word by word, the first by bulk row copies)
+    ("split_x_68x24x20_sigma1.5", rep(I.CFG_CLUSTERED, n=(68, 24, 20), n_particles=2000,
+                                      cluster_std=0.3, kmax=3.0,
+                                      L=(2 * math.pi, 2 * math.pi * 24 / 68,
+                                         2 * math.pi * 20 / 68)), 2000),
     ("odd_x_45x30x20", rep(I.CFG_SMALL, n=(45, 30, 20), kmax=3.0,
                            L=(2 * math.pi, 2 * math.pi * 30 / 45, 2 * math.pi * 20 / 45)), 1500),
 ]
