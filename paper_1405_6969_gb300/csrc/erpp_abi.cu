@@ -47,6 +47,7 @@ void free_scratch(erpp_ctx* c) {
   cudaFree(c->up_acc);
   cudaFree(c->fscat);
   cudaFree(c->entries);
+  cudaFree(c->piece_slot);
   cudaFree(c->up64);
   c->geo_t = nullptr;
   c->geo_c = nullptr;
@@ -54,6 +55,7 @@ void free_scratch(erpp_ctx* c) {
   c->up_acc = nullptr;
   c->fscat = nullptr;
   c->entries = nullptr;
+  c->piece_slot = nullptr;
   c->up64 = nullptr;
   c->cap = 0;
   c->entries_cap = 0;
@@ -80,6 +82,7 @@ erpp_status ensure_capacity(erpp_ctx* c, int64_t n) {
     if (e == cudaSuccess) e = cudaMalloc(&c->up_acc, sizeof(float) * 3 * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->fscat, sizeof(float4) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->entries, sizeof(int4) * (size_t)ecap);
+    if (e == cudaSuccess) e = cudaMalloc(&c->piece_slot, sizeof(int32_t) * (size_t)ecap);
     c->entries_cap = ecap;
   }
   if (e != cudaSuccess) {
@@ -103,7 +106,6 @@ erpp_status alloc_tile_tables(erpp_ctx* c) {
   const size_t nbins = (size_t)erpp::nbins(kp);
   cudaError_t e = cudaMalloc(&c->tile_cnt, sizeof(int32_t) * nbins);
   if (e == cudaSuccess) e = cudaMalloc(&c->tile_start, sizeof(int32_t) * (nbins + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&c->tile_cursor, sizeof(int32_t) * nbins);
   if (e == cudaSuccess) e = cudaMalloc(&c->scan_tmp, sizeof(int32_t) * (nbins / 4096 + 1));
   const size_t hb = (size_t)kp.ntiles * (size_t)kp.halo_per_tile;
   if (e == cudaSuccess) e = cudaMalloc(&c->halo, sizeof(float) * hb);
@@ -366,7 +368,6 @@ erpp_status erpp_destroy(erpp_ctx* c) {
   free_scratch(c);
   cudaFree(c->tile_cnt);
   cudaFree(c->tile_start);
-  cudaFree(c->tile_cursor);
   cudaFree(c->scan_tmp);
   cudaFree(c->halo);
   cudaFree(c->err);
@@ -392,10 +393,9 @@ erpp_status erpp_set_tiling(erpp_ctx* c, int32_t tile_y, int32_t tile_z, int32_t
   free_scratch(c);
   cudaFree(c->tile_cnt);
   cudaFree(c->tile_start);
-  cudaFree(c->tile_cursor);
   cudaFree(c->scan_tmp);
   cudaFree(c->halo);
-  c->tile_cnt = c->tile_start = c->tile_cursor = c->scan_tmp = nullptr;
+  c->tile_cnt = c->tile_start = c->scan_tmp = nullptr;
   c->halo = nullptr;
   c->tile_req[0] = tile_y;
   c->tile_req[1] = tile_z;

@@ -7,8 +7,10 @@
 // piece is written, grouped by tile, so that the gather and the scatter can
 // both work on one staged tile per thread block.
 //
-// Passes: k_bin_count (geometry per particle + per-tile piece counts),
-// k_scan (exclusive scan of the counts), k_bin_fill (place the entries).
+// Passes: k_bin_count (geometry per particle; each piece takes the next
+// place in its bin with one atomic increment of the bin's count and keeps
+// it), k_scan (exclusive scan of the counts), k_bin_fill (each piece's record
+// written at its bin's start plus its place, no atomics).
 #include <cuda_runtime.h>
 
 #include "erpp_internal.cuh"
@@ -78,7 +80,8 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
                             const double* __restrict__ x1, const double* __restrict__ x2,
                             float4* __restrict__ geo_t, int4* __restrict__ geo_c,
                             float* __restrict__ xw, int xw_len, float* __restrict__ up_acc,
-                            int64_t acc_stride, int32_t* __restrict__ tile_cnt, uint32_t* err) {
+                            int64_t acc_stride, int32_t* __restrict__ tile_cnt,
+                            int32_t* __restrict__ slot, int ms, uint32_t* err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double xv[3] = {x0[i], x1[i], x2[i]};
@@ -87,21 +90,28 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
     up_acc[acc_stride + i] = 0.f;
     up_acc[2 * acc_stride + i] = 0.f;
   }
+  // 0 <= x < L on the bit patterns (non-negative doubles order as
+  // integers; -0 is in range, NaN is not)
   bool ok = true;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) ok = ok && (xv[a] >= 0.0) && (xv[a] < kp.L[a]);
+  for (int a = 0; a < 3; ++a) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(xv[a]);
+    ok = ok && (bits < (unsigned long long)__double_as_longlong(kp.L[a]) || (bits << 1) == 0ull);
+  }
   int c[3], off[3], nw[3], jlo[3];
   float t[3];
   if (ok) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double s, lo, hi;
-      erpp_axis_window(xv[a], kp.inv_dx[a], kp.cp[a], &s, &lo, &hi);
-      double fl = floor(s);
-      int ci = (int)fl;
-      off[a] = (int)lo - ci;
-      nw[a] = (int)hi - (int)lo + 1;
-      t[a] = (float)__dadd_rn(s, -fl);
+      // the FP64 window of erpp_axis_window, with each rounding to an
+      // integer done by the conversion itself
+      const double s = __dmul_rn(xv[a], kp.inv_dx[a]);
+      int ci = __double2int_rd(s);
+      const int lo = __double2int_ru(__dadd_rn(s, -kp.cp[a]));
+      const int hi = __double2int_rd(__dadd_rn(s, kp.cp[a]));
+      off[a] = lo - ci;
+      nw[a] = hi - lo + 1;
+      t[a] = __double2float_rn(__dadd_rn(s, -(double)ci));
       // s can round up to exactly N for x just below L: the cell is then the
       // first one of the next image, which is the same node set shifted by N.
       if (ci >= kp.n[a]) ci -= kp.n[a];
@@ -144,15 +154,26 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
     }
     xw4[k] = make_float4(v[0], v[1], v[2], v[3]);
   }
+  int k = 0;
+  auto place = [&](int bin) {
+    const int v = atomicAdd(&tile_cnt[bin], 1);
+    if (k < ms)
+      slot[(int64_t)k * n + i] = v;
+    else
+      erpp_set_err(err, ERPP_ERRBIT_BOUNDS);
+    ++k;
+  };
   if (kp.design == 4)
-    for_each_piece4(kp, c, jlo, nw, [&](int tile, int, int, int) { atomicAdd(&tile_cnt[tile], 1); });
+    for_each_piece4(kp, c, jlo, nw, [&](int tile, int, int, int) { place(tile); });
   else
-    for_each_piece(kp, c[0], jlo, nw, [&](int bin, const PieceSeg&) { atomicAdd(&tile_cnt[bin], 1); });
+    for_each_piece(kp, c[0], jlo, nw, [&](int bin, const PieceSeg&) { place(bin); });
 }
 
-// Writes one record per piece, at its place in the (tile, bucket) order.
+// Writes one record per piece, at its bin's start plus the place the piece
+// took in k_bin_count (pieces visited in the same order).
 __global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict__ geo_t,
-                           const int4* __restrict__ geo_c, int32_t* __restrict__ cursor,
+                           const int4* __restrict__ geo_c, const int32_t* __restrict__ start,
+                           const int32_t* __restrict__ slot, int ms,
                            int4* __restrict__ entries, int64_t cap, uint32_t* err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -167,6 +188,12 @@ __global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict_
     jlo[a] = c[a] + erpp_geo_off(pack, a);
     nw[a] = erpp_geo_nw(pack, a);
   }
+  int k = 0;
+  auto place = [&](int bin) -> int64_t {
+    const int64_t pos = k < ms ? (int64_t)start[bin] + slot[(int64_t)k * n + i] : cap;
+    ++k;
+    return pos;
+  };
   if (kp.design == 4) {
     // record: {p, x0 | y0 << 7 | z0 << 13 | lz << 17 | lx << 22 | ly << 27,
     //          d0y bits, d0z bits}: x0, y0 the staged x/y index of the
@@ -181,7 +208,7 @@ __global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict_
     for_each_piece4(kp, c, jlo, nw, [&](int tile, int jz, int ez, int z0) {
       const float d0z = (float)(jz - c[2]) - gt.z;
       const uint32_t pk = fixed | ((uint32_t)z0 << 13) | ((uint32_t)(ez - jz + 1) << 17);
-      const int pos = atomicAdd(&cursor[tile], 1);
+      const int64_t pos = place(tile);
       if (pos < cap)
         entries[pos] = make_int4((int)i, (int)pk, __float_as_int(d0y), __float_as_int(d0z));
       else
@@ -198,7 +225,7 @@ __global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict_
     const int ly = sg.ey - sg.jy + 1, lz = sg.ez - sg.jz + 1;
     const float d0y = (float)(sg.jy - c[1]) - gt.y;
     const float d0z = (float)(sg.jz - c[2]) - gt.z;
-    const int pos = atomicAdd(&cursor[bin], 1);
+    const int64_t pos = place(bin);
     if (pos < cap)
       entries[pos] = make_int4((int)i, base | (nw[0] << 17) | (ly << 22) | (lz << 27),
                                __float_as_int(d0y), __float_as_int(d0z));
@@ -278,13 +305,11 @@ __global__ void k_scan_top(int32_t* __restrict__ chunk_tot, int nchunks, int32_t
   if (threadIdx.x == 0) start[nbins] = carry;
 }
 
-__global__ void k_scan_add(int32_t* __restrict__ start, int32_t* __restrict__ cursor,
-                           const int32_t* __restrict__ chunk_off, int nbins) {
+__global__ void k_scan_add(int32_t* __restrict__ start, const int32_t* __restrict__ chunk_off,
+                           int nbins) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nbins) return;
-  const int32_t v = start[i] + chunk_off[i / kScanChunk];
-  start[i] = v;
-  cursor[i] = v;
+  start[i] += chunk_off[i / kScanChunk];
 }
 
 }  // namespace
@@ -295,23 +320,24 @@ cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bo
                           cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;
   const int nbins = erpp::nbins(kp);
+  const int ms = ctx->maxseg[0] * ctx->maxseg[1] * ctx->maxseg[2];
   cudaError_t e = cudaMemsetAsync(ctx->tile_cnt, 0, sizeof(int32_t) * nbins, st);
   if (e != cudaSuccess) return e;
   if (n > 0) {
     int blocks = (int)((n + 255) / 256);
     k_bin_count<<<blocks, 256, 0, st>>>(kp, n, x[0], x[1], x[2], ctx->geo_t, ctx->geo_c,
                                         ctx->xw, ctx->xw_len, zero_acc ? ctx->up_acc : nullptr,
-                                        ctx->cap, ctx->tile_cnt, ctx->err);
+                                        ctx->cap, ctx->tile_cnt, ctx->piece_slot, ms, ctx->err);
   }
   const int nchunks = (nbins + kScanChunk - 1) / kScanChunk;
   k_scan_local<<<nchunks, 1024, 0, st>>>(ctx->tile_cnt, ctx->tile_start, ctx->scan_tmp, nbins);
   k_scan_top<<<1, 1024, 0, st>>>(ctx->scan_tmp, nchunks, ctx->tile_start, nbins);
-  k_scan_add<<<(nbins + 255) / 256, 256, 0, st>>>(ctx->tile_start, ctx->tile_cursor, ctx->scan_tmp,
-                                                 nbins);
+  k_scan_add<<<(nbins + 255) / 256, 256, 0, st>>>(ctx->tile_start, ctx->scan_tmp, nbins);
   if (n > 0) {
     int blocks = (int)((n + 255) / 256);
-    k_bin_fill<<<blocks, 256, 0, st>>>(kp, n, ctx->geo_t, ctx->geo_c, ctx->tile_cursor,
-                                       ctx->entries, ctx->entries_cap, ctx->err);
+    k_bin_fill<<<blocks, 256, 0, st>>>(kp, n, ctx->geo_t, ctx->geo_c, ctx->tile_start,
+                                       ctx->piece_slot, ms, ctx->entries, ctx->entries_cap,
+                                       ctx->err);
   }
   return cudaGetLastError();
 }

@@ -112,7 +112,7 @@ struct erpp_ctx {
   float* halo;            // scatter x-halo columns, [ntiles][3][T_z][T_y][xhlo + xhhi]
   int32_t* tile_cnt;      // [32 ntiles]: pieces per (tile, bucket) bin
   int32_t* tile_start;    // [32 ntiles + 1]
-  int32_t* tile_cursor;   // [32 ntiles]
+  int32_t* piece_slot;    // [maxseg product][cap]: each piece's place in its bin
   int32_t* scan_tmp;      // [ceil(32 ntiles / 4096)] chunk totals of the scan
   uint32_t* err;          // device error word
   double* red;            // reduction scratch

@@ -32,8 +32,8 @@ constexpr size_t kOffEntries = kOffXw + align256(4 * 16 * kNoallocParticles);
 constexpr int64_t kNoallocBins = 32 * kNoallocTiles;  // (tile, bucket) bins
 constexpr size_t kOffCnt = kOffEntries + align256(16 * kNoallocPieces);
 constexpr size_t kOffStart = kOffCnt + align256(4 * kNoallocBins);
-constexpr size_t kOffCursor = kOffStart + align256(4 * (kNoallocBins + 1));
-constexpr size_t kOffScan = kOffCursor + align256(4 * kNoallocBins);
+constexpr size_t kOffSlot = kOffStart + align256(4 * (kNoallocBins + 1));
+constexpr size_t kOffScan = kOffSlot + align256(4 * kNoallocPieces);
 constexpr size_t kOffErr = kOffScan + align256(4 * (kNoallocBins / 4096 + 1));
 constexpr size_t kScratchBytes = kOffErr + 256;
 
@@ -92,7 +92,7 @@ extern "C" erpp_status erpp_interpolate_noalloc(const erpp_params* params, const
   c.xw = reinterpret_cast<float*>(base + kOffXw);
   c.tile_cnt = reinterpret_cast<int32_t*>(base + kOffCnt);
   c.tile_start = reinterpret_cast<int32_t*>(base + kOffStart);
-  c.tile_cursor = reinterpret_cast<int32_t*>(base + kOffCursor);
+  c.piece_slot = reinterpret_cast<int32_t*>(base + kOffSlot);
   c.scan_tmp = reinterpret_cast<int32_t*>(base + kOffScan);
   c.err = reinterpret_cast<uint32_t*>(base + kOffErr);
   cudaStream_t st = (cudaStream_t)stream;
