@@ -255,6 +255,10 @@ erpp_status erpp_step_batched(erpp_batch* batch, int first_step, int use_graph,
 erpp_status erpp_batch_set_tiling(erpp_batch* batch, int32_t box, int32_t tile_y,
                                   int32_t tile_z, int32_t threads);
 
+/* erpp_get_tiling of box `box` (0 <= box < nbox, else ERPP_EINVAL); out is a
+ * HOST array of 5. */
+erpp_status erpp_batch_get_tiling(erpp_batch* batch, int32_t box, int32_t out[5]);
+
 /* erpp_check over every box: synchronises `stream`, returns the first error
  * found (and clears each box's error word). */
 erpp_status erpp_batch_check(erpp_batch* batch, erpp_stream stream);

@@ -186,6 +186,11 @@ erpp_status erpp_batch_set_tiling(erpp_batch* b, int32_t box, int32_t tile_y, in
   return s;
 }
 
+erpp_status erpp_batch_get_tiling(erpp_batch* b, int32_t box, int32_t out[5]) {
+  if (!b || !out || box < 0 || box >= b->nbox) return ERPP_EINVAL;
+  return erpp_get_tiling(b->ctx[box], out);
+}
+
 erpp_status erpp_batch_check(erpp_batch* b, erpp_stream stream) {
   if (!b) return ERPP_EINVAL;
   erpp_status worst = ERPP_OK;

@@ -304,6 +304,13 @@ class Batch:
         _lib.check(self.lib.erpp_batch_set_tiling(self._h, int(box), int(tile_y), int(tile_z),
                                                   int(threads)), "erpp_batch_set_tiling")
 
+    def tiling(self, box):
+        """erpp_get_tiling of one box: (design, W, T_y, T_z, threads)."""
+        out = (ctypes.c_int32 * 5)()
+        _lib.check(self.lib.erpp_batch_get_tiling(self._h, int(box), out),
+                   "erpp_batch_get_tiling")
+        return tuple(int(v) for v in out)
+
     def autotune(self, steps=3, warmup=1, cache_path=None, use_cache=True):
         """Tile shape per box: each box is tuned on a stand-alone context with
         its own data (the autotuner's cache shares results between boxes of

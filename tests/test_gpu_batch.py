@@ -87,6 +87,8 @@ def test_batched_step_matches_oracle(erpp, oracle_lib, precision, use_graph):
         for (p, _, _, _), (grid, ref) in zip(entries, refs):
             oracle_lib.step(p, grid, ref, first_step=(k == 0))
     batch.check()
+    tilings = [batch.tiling(i) for i in range(len(boxes))]
+    assert all(t[0] in (3, 4) for t in tilings)
     tol = TOL[precision]
     for (p, u, ps, S), (grid, ref), w in zip(entries, refs, boxes):
         S_ref = oracle_lib.scatter(p, ref.x_prev, ref.D)

@@ -125,6 +125,25 @@ def test_scatter_source(erpp, oracle_lib, precision, name, w, npart):
     assert rel(S.cpu().numpy(), ref) < TOL[precision]
 
 
+@pytest.mark.parametrize("name,w,npart", CASES, ids=[c[0] for c in CASES])
+def test_scatter_reproducible(erpp, name, w, npart):
+    """Repeated FP32 scatters of the same cloud are bit-identical: pieces land
+    in their tiles in a different order each time, but the fixed-point sums do
+    not depend on it and every halo node is merged in a fixed order, whichever
+    block merges it."""
+    import torch
+    p = w.params()
+    _, st = _setup(w, npart)
+    D = I.make_forces(npart, 1.0, seed=11)
+    ctx = erpp.Context(p, precision="fp32")
+    x, Dt = cuda(st.x), cuda(D)
+    S1 = ctx.scatter_source(x, Dt).clone()
+    for _ in range(3):
+        S2 = ctx.scatter_source(x, Dt)
+        ctx.check()
+        assert torch.equal(S1, S2)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("name,w,npart", CASES, ids=[c[0] for c in CASES])
 def test_interpolate(erpp, oracle_lib, precision, name, w, npart):
