@@ -988,26 +988,15 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
 
 // Adds the scatter's halo strips onto the tiles they belong to, in two
 // phases (stream order, each node updated by one thread per phase, so the
-// result is deterministic), one block per (tile, component, plane), periodic
-// in x and y:
+// result is deterministic), one block per tile, periodic in x and y:
 //   k_merge_rows: rows within yhhi / yhlo of the tile's lower / upper edge
 //     receive the y-strips of the lower / upper neighbour (whole rows, 16-byte
 //     chunks when aligned);
 //   k_merge_cols: columns within xhhi / xhlo of the left / right edge receive
 //     the x-strips of the left / right neighbour (same rows) and, in the rim
 //     rows, the x-strips of the diagonal neighbours (their y-halo rows).
-struct MergeTile {
-  int b[3], ext[3], t[3];
-  int cc, z;
-};
-
-__device__ __forceinline__ bool merge_tile(const erpp_kparams& kp, MergeTile& m) {
-  tile_origin4(kp, blockIdx.x, m.b, m.ext, m.t);
-  m.z = blockIdx.y % kp.T[2];
-  m.cc = blockIdx.y / kp.T[2];
-  return m.z < m.ext[2];
-}
-
+// A thread keeps one (row, chunk) or (row, column) job for every component
+// and plane of the tile, so the index arithmetic is done once per job.
 __device__ __forceinline__ int tile_id(const erpp_kparams& kp, int tx, int ty, int tz) {
   return (tz * kp.nt[1] + ty) * kp.nt[0] + tx;
 }
@@ -1016,90 +1005,108 @@ constexpr int kMergeThreads = 128;
 
 __global__ void __launch_bounds__(kMergeThreads) k_merge_rows(erpp_kparams kp, float* __restrict__ S,
                                                               const float* __restrict__ halo) {
-  MergeTile m;
-  if (!merge_tile(kp, m)) return;
+  int b[3], ext[3], t[3];
+  tile_origin4(kp, blockIdx.x, b, ext, t);
   const int W = kp.T[0], hy = kp.yhlo + kp.yhhi;
-  const int tyl = m.t[1] == 0 ? kp.nt[1] - 1 : m.t[1] - 1;
-  const int tyr = m.t[1] == kp.nt[1] - 1 ? 0 : m.t[1] + 1;
-  const size_t ys = (size_t)kp.ystrip_off + (size_t)blockIdx.y * hy * W;
-  const float* yB = halo + (size_t)tile_id(kp, m.t[0], tyl, m.t[2]) * kp.halo_per_tile + ys;
-  const float* yT = halo + (size_t)tile_id(kp, m.t[0], tyr, m.t[2]) * kp.halo_per_tile + ys;
+  const int tyl = t[1] == 0 ? kp.nt[1] - 1 : t[1] - 1;
+  const int tyr = t[1] == kp.nt[1] - 1 ? 0 : t[1] + 1;
+  const float* hB = halo + (size_t)tile_id(kp, t[0], tyl, t[2]) * kp.halo_per_tile + kp.ystrip_off;
+  const float* hT = halo + (size_t)tile_id(kp, t[0], tyr, t[2]) * kp.halo_per_tile + kp.ystrip_off;
   const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
-  float* splane = S + m.cc * nn + (size_t)(m.b[2] + m.z) * kp.n[1] * kp.n[0] + m.b[0];
-  const int ycut = m.ext[1] - kp.yhlo;
+  const size_t nxy = (size_t)kp.n[0] * kp.n[1];
+  const int ycut = ext[1] - kp.yhlo;
   // rim rows: [0, min(yhhi, ext)) and [max(ycut, yhhi), ext) (all rows when ext < hy)
-  const int na = min(kp.yhhi, m.ext[1]);
-  const int nb = m.ext[1] - max(ycut, na);
-  const int nrows = na + nb;
-  const bool vec = (W & 3) == 0 && (m.ext[0] & 3) == 0 && (kp.n[0] & 3) == 0 && (m.b[0] & 3) == 0 &&
+  const int na = min(kp.yhhi, ext[1]);
+  const int nb = ext[1] - max(ycut, na);
+  const bool vec = (W & 3) == 0 && (ext[0] & 3) == 0 && (kp.n[0] & 3) == 0 && (b[0] & 3) == 0 &&
                    (((uintptr_t)S) & 15) == 0 && (((uintptr_t)halo) & 15) == 0;
-  const int per_row = vec ? m.ext[0] >> 2 : m.ext[0];
-  for (int i = threadIdx.x; i < nrows * per_row; i += kMergeThreads) {
+  const int per_row = vec ? ext[0] >> 2 : ext[0];
+  const int njobs = (na + nb) * per_row;
+  const size_t qstride = (size_t)hy * W;  // one component-plane of the y-strips
+  for (int i = threadIdx.x; i < njobs; i += kMergeThreads) {
     const int r = i / per_row;
     const int j = i - r * per_row;
     const int y = r < na ? r : max(ycut, na) + (r - na);
     const bool yl = y < kp.yhhi, yr = y >= ycut;
-    float* d = splane + (size_t)(m.b[1] + y) * kp.n[0];
-    if (vec) {
-      float4 v = reinterpret_cast<float4*>(d)[j];
-      if (yl) {
-        const float4 a = reinterpret_cast<const float4*>(yB + (kp.yhlo + y) * W)[j];
-        v.x += a.x; v.y += a.y; v.z += a.z; v.w += a.w;
+    float* drow = S + (size_t)b[2] * nxy + (size_t)(b[1] + y) * kp.n[0] + b[0];
+    const float* brow = hB + (size_t)(kp.yhlo + y) * W;
+    const float* trow = hT + (size_t)(y - ycut) * W;
+    for (int cc = 0; cc < 3; ++cc) {
+      for (int z = 0; z < ext[2]; ++z) {
+        float* d = drow + cc * nn + z * nxy;
+        const size_t q = (size_t)(cc * kp.T[2] + z) * qstride;
+        if (vec) {
+          float4 v = reinterpret_cast<float4*>(d)[j];
+          if (yl) {
+            const float4 a = reinterpret_cast<const float4*>(brow + q)[j];
+            v.x += a.x; v.y += a.y; v.z += a.z; v.w += a.w;
+          }
+          if (yr) {
+            const float4 a = reinterpret_cast<const float4*>(trow + q)[j];
+            v.x += a.x; v.y += a.y; v.z += a.z; v.w += a.w;
+          }
+          reinterpret_cast<float4*>(d)[j] = v;
+        } else {
+          float v = d[j];
+          if (yl) v += brow[q + j];
+          if (yr) v += trow[q + j];
+          d[j] = v;
+        }
       }
-      if (yr) {
-        const float4 a = reinterpret_cast<const float4*>(yT + (y - ycut) * W)[j];
-        v.x += a.x; v.y += a.y; v.z += a.z; v.w += a.w;
-      }
-      reinterpret_cast<float4*>(d)[j] = v;
-    } else {
-      float v = d[j];
-      if (yl) v += yB[(kp.yhlo + y) * W + j];
-      if (yr) v += yT[(y - ycut) * W + j];
-      d[j] = v;
     }
   }
 }
 
 __global__ void __launch_bounds__(kMergeThreads) k_merge_cols(erpp_kparams kp, float* __restrict__ S,
                                                               const float* __restrict__ halo) {
-  MergeTile m;
-  if (!merge_tile(kp, m)) return;
+  int b[3], ext[3], t[3];
+  tile_origin4(kp, blockIdx.x, b, ext, t);
   const int hx = kp.xhlo + kp.xhhi, hy = kp.yhlo + kp.yhhi;
   const int Ty = kp.T[1];
-  const int txl = m.t[0] == 0 ? kp.nt[0] - 1 : m.t[0] - 1;
-  const int txr = m.t[0] == kp.nt[0] - 1 ? 0 : m.t[0] + 1;
-  const int tyl = m.t[1] == 0 ? kp.nt[1] - 1 : m.t[1] - 1;
-  const int tyr = m.t[1] == kp.nt[1] - 1 ? 0 : m.t[1] + 1;
-  const size_t xs = (size_t)blockIdx.y * (Ty + hy) * hx;
+  const int txl = t[0] == 0 ? kp.nt[0] - 1 : t[0] - 1;
+  const int txr = t[0] == kp.nt[0] - 1 ? 0 : t[0] + 1;
+  const int tyl = t[1] == 0 ? kp.nt[1] - 1 : t[1] - 1;
+  const int tyr = t[1] == kp.nt[1] - 1 ? 0 : t[1] + 1;
   auto strip = [&](int tx, int ty) {
-    return halo + (size_t)tile_id(kp, tx, ty, m.t[2]) * kp.halo_per_tile + xs;
+    return halo + (size_t)tile_id(kp, tx, ty, t[2]) * kp.halo_per_tile;
   };
-  const float* xL = strip(txl, m.t[1]);
-  const float* xR = strip(txr, m.t[1]);
-  const float* xLB = strip(txl, tyl);
-  const float* xRB = strip(txr, tyl);
-  const float* xLT = strip(txl, tyr);
-  const float* xRT = strip(txr, tyr);
   const int exty_l = min((tyl + 1) * Ty, kp.n[1]) - tyl * Ty;
-  const int xcut = m.ext[0] - kp.xhlo, ycut = m.ext[1] - kp.yhlo;
+  const int xcut = ext[0] - kp.xhlo, ycut = ext[1] - kp.yhlo;
   const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
-  float* splane = S + m.cc * nn + (size_t)(m.b[2] + m.z) * kp.n[1] * kp.n[0] + m.b[0];
-  const bool allcols = m.ext[0] < hx;
-  const int ncol = allcols ? m.ext[0] : hx;
-  for (int i = threadIdx.x; i < m.ext[1] * ncol; i += kMergeThreads) {
+  const size_t nxy = (size_t)kp.n[0] * kp.n[1];
+  const bool allcols = ext[0] < hx;
+  const int ncol = allcols ? ext[0] : hx;
+  const size_t qstride = (size_t)(Ty + hy) * hx;  // one component-plane of the x-strips
+  for (int i = threadIdx.x; i < ext[1] * ncol; i += kMergeThreads) {
     const int y = i / ncol;
     const int j = i - y * ncol;
     const int x = allcols || j < kp.xhhi ? j : xcut + (j - kp.xhhi);
     const bool xl = x < kp.xhhi, xr = x >= xcut;
+    if (!(xl || xr)) continue;
     const bool yl = y < kp.yhhi, yr = y >= ycut;
-    float add = 0.f;
-    if (xl) add += xL[(y + kp.yhlo) * hx + kp.xhlo + x];
-    if (xr) add += xR[(y + kp.yhlo) * hx + x - xcut];
-    if (xl && yl) add += xLB[(exty_l + kp.yhlo + y) * hx + kp.xhlo + x];
-    if (xr && yl) add += xRB[(exty_l + kp.yhlo + y) * hx + x - xcut];
-    if (xl && yr) add += xLT[(y - ycut) * hx + kp.xhlo + x];
-    if (xr && yr) add += xRT[(y - ycut) * hx + x - xcut];
-    if (xl || xr) splane[(size_t)(m.b[1] + y) * kp.n[0] + x] += add;
+    // offsets of this node's entries in the six strips (same for every plane)
+    const int cl = kp.xhlo + x, cr = x - xcut;
+    const float* pL = strip(txl, t[1]) + (y + kp.yhlo) * hx + cl;
+    const float* pR = strip(txr, t[1]) + (y + kp.yhlo) * hx + cr;
+    const float* pLB = strip(txl, tyl) + (exty_l + kp.yhlo + y) * hx + cl;
+    const float* pRB = strip(txr, tyl) + (exty_l + kp.yhlo + y) * hx + cr;
+    const float* pLT = strip(txl, tyr) + (y - ycut) * hx + cl;
+    const float* pRT = strip(txr, tyr) + (y - ycut) * hx + cr;
+    float* drow = S + (size_t)b[2] * nxy + (size_t)(b[1] + y) * kp.n[0] + b[0] + x;
+    for (int cc = 0; cc < 3; ++cc) {
+      for (int z = 0; z < ext[2]; ++z) {
+        const size_t q = (size_t)(cc * kp.T[2] + z) * qstride;
+        float add = 0.f;
+        if (xl) add += pL[q];
+        if (xr) add += pR[q];
+        if (xl && yl) add += pLB[q];
+        if (xr && yl) add += pRB[q];
+        if (xl && yr) add += pLT[q];
+        if (xr && yr) add += pRT[q];
+        float* d = drow + cc * nn + z * nxy;
+        *d += add;
+      }
+    }
   }
 }
 
@@ -1226,9 +1233,8 @@ cudaError_t launch_scatter_f32_4(erpp_ctx* ctx, float* S, cudaStream_t st) {
     default: e = scatter4<16, 1, 16>(ctx, S, st); break;
   }
   if (e != cudaSuccess) return e;
-  const dim3 mg(ctx->kp.ntiles, 3 * ctx->kp.T[2]);
-  k_merge_rows<<<mg, kMergeThreads, 0, st>>>(ctx->kp, S, ctx->halo);
-  k_merge_cols<<<mg, kMergeThreads, 0, st>>>(ctx->kp, S, ctx->halo);
+  k_merge_rows<<<ctx->kp.ntiles, kMergeThreads, 0, st>>>(ctx->kp, S, ctx->halo);
+  k_merge_cols<<<ctx->kp.ntiles, kMergeThreads, 0, st>>>(ctx->kp, S, ctx->halo);
   return cudaGetLastError();
 }
 
