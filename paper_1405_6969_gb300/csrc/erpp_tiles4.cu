@@ -533,13 +533,18 @@ __device__ __forceinline__ int batch_size(int total, int PB) {
   return (total + nb - 1) / nb;
 }
 
-// Stages the batch's records (and, through the particle index, its
-// x-weights and force words) into shared memory; asynchronous copies.
-template <int XW, bool FORCES, int NT>
-__device__ void stage_batch(const Carve<XW>& cv, const int4* __restrict__ entries, int b0, int np,
-                            const float* __restrict__ xw, const float4* __restrict__ fscat) {
-  for (int k = threadIdx.x; k < np; k += NT) {
-    const int4 r = __ldg(&entries[b0 + k]);
+// A batch holds at most one piece per thread (PB <= threads per block):
+// thread k loads record k of the batch (issued early, so that its latency
+// overlaps other work), then stages it and, through the particle index, its
+// x-weights and force word into shared memory (asynchronous copies).
+__device__ __forceinline__ int4 load_rec(const int4* __restrict__ entries, int b0, int np) {
+  return threadIdx.x < np ? __ldg(&entries[b0 + threadIdx.x]) : make_int4(0, 0, 0, 0);
+}
+template <int XW, bool FORCES>
+__device__ void stage_batch(const Carve<XW>& cv, int4 r, int np, const float* __restrict__ xw,
+                            const float4* __restrict__ fscat) {
+  const int k = threadIdx.x;
+  if (k < np) {
     cv.rec[k] = r;
     const float* src = xw + (size_t)r.x * XW;
 #pragma unroll
@@ -568,6 +573,7 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
   __shared__ SchedState ss;
   __shared__ __align__(8) uint64_t tma_bar;
   constexpr int PB = Batch<XW>::kPB;
+  static_assert(PB <= NT, "a batch holds at most one piece per thread");
   const int tile = blockIdx.x;
   const int e0 = start[tile];
   const int e1 = (int)min((int64_t)start[tile + 1], ecap);
@@ -580,6 +586,8 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
   const int x0 = b[0] - kp.xoff, y0 = b[1] - kp.yhlo;
   const bool tma = use_tma && x0 >= 0 && x0 + kp.px <= kp.n[0] && y0 >= 0 &&
                    y0 + kp.T[1] + hy <= kp.n[1];
+  const int bs = batch_size(e1 - e0, PB);
+  const int4 rfirst = load_rec(entries, e0, min(bs, e1 - e0));
   // otherwise bulk row copies when rows are whole 16-byte chunks, else
   // word-level asynchronous copies
   const bool rows = !tma && (kp.n[0] & 3) == 0 && (b[0] & 3) == 0 && (kp.xoff & 3) == 0 &&
@@ -604,10 +612,9 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
   const int plane = kp.plane, px = kp.px, pxy = kp.pxy;
   const float by = kp.beta[1], bz = kp.beta[2];
   const unsigned fbase = shared_addr(cv.field), pbase = shared_addr(cv.pacc);
-  const int bs = batch_size(e1 - e0, PB);
   for (int b0 = e0; b0 < e1; b0 += bs) {
     const int np = min(bs, e1 - b0);
-    stage_batch<XW, false, NT>(cv, entries, b0, np, xw, nullptr);
+    stage_batch<XW, false>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, xw, nullptr);
     for (int k = threadIdx.x; k < 3 * PB; k += NT) cv.pacc[k] = 0.f;
     const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
     cp_async_wait_all();                            // field (first batch), x-weights
@@ -700,11 +707,12 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
     erpp_kparams kp, float* __restrict__ S, float* __restrict__ halo,
     const int32_t* __restrict__ start, const int4* __restrict__ entries, int64_t ecap,
     const float* __restrict__ xw, const float4* __restrict__ fscat) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SchedState ss;
   constexpr int NW = NT / 32;
   __shared__ float red[NW];
   constexpr int PB = Batch<XW>::kPB;
+  static_assert(PB <= NT, "a batch holds at most one piece per thread");
   const int tile = blockIdx.x;
   const int e0 = start[tile];
   const int e1 = (int)min((int64_t)start[tile + 1], ecap);
@@ -716,47 +724,58 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
   const int plane = kp.plane, px = kp.px, pxy = kp.pxy;
   const bool any = e0 < e1;
   const bool fixedp = MODE == 0 && (e1 - e0) <= kDenseTile;
+  const int bs = any ? batch_size(e1 - e0, PB) : 1;
+  const int4 rfirst = load_rec(entries, e0, min(bs, e1 - e0));  // overlaps the clearing
   float scale = 1.f, inv_scale = 1.f;
   int* acc_i = reinterpret_cast<int*>(smem);
-  float* comp_lo = smem + 3 * plane;
   {
     const int total = (MODE == 1 ? 6 : 3) * plane;
     float4* s4 = reinterpret_cast<float4*>(smem);
     for (int k = threadIdx.x; k < total / 4; k += NT) s4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   if (any) {
-    if (fixedp) {
-      float bsum = 0.f;
-      for (int e = e0 + threadIdx.x; e < e1; e += NT)
-        bsum += __ldg(&fscat[__ldg(&entries[e].x)]).w;
+    // Fixed-point scale from the tile's force bound B = sum of max |f| over
+    // its pieces: B = m 2^ex2 (m in [0.5, 1)) gives contributions below
+    // 2^30 in magnitude.  A tile of one batch sums B from the staged forces,
+    // a larger one by a pass over its entries first.
+    const bool single = (e1 - e0) <= PB;
+    auto set_scale = [&](float part) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
-      if (lane == 0) red[warp] = bsum;
-    }
-    __syncthreads();
-    if (fixedp) {
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) red[warp] = part;
+      __syncthreads();
       float B = 0.f;
 #pragma unroll
       for (int w = 0; w < NW; ++w) B += red[w];
       if (B > 0.f) {
         int ex2;
-        frexpf(B, &ex2);  // B = m 2^ex2, m in [0.5, 1)
+        frexpf(B, &ex2);
         const int sh = min(30 - ex2, 120);
         scale = ldexpf(1.f, sh);
         // node sums are in units of scale / 2 (the row weight carries 2^31,
         // the high word drops 2^32)
         inv_scale = ldexpf(2.f, -sh);
       }
+    };
+    if (fixedp && !single) {
+      float bsum = 0.f;
+      for (int e = e0 + threadIdx.x; e < e1; e += NT)
+        bsum += __ldg(&fscat[__ldg(&entries[e].x)]).w;
+      set_scale(bsum);
     }
     const float by = kp.beta[1], bz = kp.beta[2];
     const unsigned fbase = shared_addr(smem);
-    const int bs = batch_size(e1 - e0, PB);
     for (int b0 = e0; b0 < e1; b0 += bs) {
       const int np = min(bs, e1 - b0);
-      stage_batch<XW, true, NT>(cv, entries, b0, np, xw, fscat);
+      stage_batch<XW, true>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, xw, fscat);
       const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
       cp_async_wait_all();
       __syncthreads();
+      if (fixedp && single) {
+        float bsum = 0.f;
+        for (int k = threadIdx.x; k < np; k += NT) bsum += cv.fsb[k].w;
+        set_scale(bsum);
+      }
       for (int r = 0; r < R; ++r) {
         const uint16_t ui = cv.sched[r * NT + warp * 32 + lane];
         const bool active = ui != kEmpty;
