@@ -259,6 +259,11 @@ erpp_status erpp_batch_set_tiling(erpp_batch* batch, int32_t box, int32_t tile_y
  * HOST array of 5. */
 erpp_status erpp_batch_get_tiling(erpp_batch* batch, int32_t box, int32_t out[5]);
 
+/* Sum over the boxes of erpp_last_step_launches: the kernels of one batched
+ * step (a captured graph replays the sequences recorded at capture), written
+ * to the HOST int *n. */
+erpp_status erpp_batch_last_step_launches(erpp_batch* batch, int32_t* n);
+
 /* erpp_check over every box: synchronises `stream`, returns the first error
  * found (and clears each box's error word). */
 erpp_status erpp_batch_check(erpp_batch* batch, erpp_stream stream);
@@ -310,6 +315,11 @@ erpp_status erpp_set_tiling(erpp_ctx* ctx, int32_t tile_y, int32_t tile_z, int32
  * and z), out[1..3] = tile size W, T_y, T_z, out[4] = threads per block.
  * out is a HOST array of 5. */
 erpp_status erpp_get_tiling(erpp_ctx* ctx, int32_t out[5]);
+
+/* Number of kernels the most recent erpp_step on ctx launched (0 before the
+ * first; memsets and event records are not kernels), written to the HOST
+ * int *n.  A tracing aid for launch-count accounting. */
+erpp_status erpp_last_step_launches(erpp_ctx* ctx, int32_t* n);
 
 /* Per-phase timing (a tracing aid, not part of the method).  After
  * erpp_profile_enable(ctx, 1) every erpp_step records CUDA events on its

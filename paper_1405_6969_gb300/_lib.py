@@ -91,6 +91,8 @@ _SIGS = {
     "erpp_batch_destroy": (_st, [_vp]),
     "erpp_set_tiling": (_st, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "erpp_get_tiling": (_st, [_vp, ctypes.POINTER(ctypes.c_int32)]),
+    "erpp_last_step_launches": (_st, [_vp, ctypes.POINTER(ctypes.c_int32)]),
+    "erpp_batch_last_step_launches": (_st, [_vp, ctypes.POINTER(ctypes.c_int32)]),
     "erpp_batch_get_tiling": (_st, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "erpp_fluid_init": (_st, [ctypes.POINTER(Params), ctypes.POINTER(_vp)]),
     "erpp_fluid_stokes_step": (_st, [_vp, _vp, _vp, _vp]),

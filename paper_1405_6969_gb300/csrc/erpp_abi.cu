@@ -517,6 +517,7 @@ erpp_status erpp_step(erpp_ctx* c, const void* u, const erpp_particles* P, void*
   const double* const xprev[3] = {P->x_prev[0], P->x_prev[1], P->x_prev[2]};
   const double* const Dv[3] = {P->D[0], P->D[1], P->D[2]};
   cudaError_t e;
+  c->launches = 0;
   if (c->fp64) {
     double* up[3] = {c->up64, c->up64 + c->cap, c->up64 + 2 * c->cap};
     e = erpp::launch_gather_f64(c, (const double*)u, n, xin, up, st);
@@ -537,7 +538,14 @@ erpp_status erpp_step(erpp_ctx* c, const void* u, const erpp_particles* P, void*
     if (e == cudaSuccess) e = erpp::launch_scatter_f32(c, (float*)S, st);
     if (ev) cudaEventRecord(ev[4], st);
   }
+  c->last_step_launches = c->launches;
   return set_cuda_err(e);
+}
+
+erpp_status erpp_last_step_launches(erpp_ctx* c, int32_t* n) {
+  if (!c || !n) return ERPP_EINVAL;
+  *n = c->last_step_launches;
+  return ERPP_OK;
 }
 
 erpp_status erpp_profile_enable(erpp_ctx* c, int enable) {

@@ -191,6 +191,18 @@ erpp_status erpp_batch_get_tiling(erpp_batch* b, int32_t box, int32_t out[5]) {
   return erpp_get_tiling(b->ctx[box], out);
 }
 
+erpp_status erpp_batch_last_step_launches(erpp_batch* b, int32_t* n) {
+  if (!b || !n) return ERPP_EINVAL;
+  int32_t total = 0;
+  for (int i = 0; i < b->nbox; ++i) {
+    int32_t k = 0;
+    erpp_last_step_launches(b->ctx[i], &k);
+    total += k;
+  }
+  *n = total;
+  return ERPP_OK;
+}
+
 erpp_status erpp_batch_check(erpp_batch* b, erpp_stream stream) {
   if (!b) return ERPP_EINVAL;
   erpp_status worst = ERPP_OK;

@@ -325,16 +325,19 @@ cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bo
   if (e != cudaSuccess) return e;
   if (n > 0) {
     int blocks = (int)((n + 255) / 256);
+    ++ctx->launches;
     k_bin_count<<<blocks, 256, 0, st>>>(kp, n, x[0], x[1], x[2], ctx->geo_t, ctx->geo_c,
                                         ctx->xw, ctx->xw_len, zero_acc ? ctx->up_acc : nullptr,
                                         ctx->cap, ctx->tile_cnt, ctx->piece_slot, ms, ctx->err);
   }
   const int nchunks = (nbins + kScanChunk - 1) / kScanChunk;
+  ctx->launches += 3;
   k_scan_local<<<nchunks, 1024, 0, st>>>(ctx->tile_cnt, ctx->tile_start, ctx->scan_tmp, nbins);
   k_scan_top<<<1, 1024, 0, st>>>(ctx->scan_tmp, nchunks, ctx->tile_start, nbins);
   k_scan_add<<<(nbins + 255) / 256, 256, 0, st>>>(ctx->tile_start, ctx->scan_tmp, nbins);
   if (n > 0) {
     int blocks = (int)((n + 255) / 256);
+    ++ctx->launches;
     k_bin_fill<<<blocks, 256, 0, st>>>(kp, n, ctx->geo_t, ctx->geo_c, ctx->tile_start,
                                        ctx->piece_slot, ms, ctx->entries, ctx->entries_cap,
                                        ctx->err);

@@ -148,6 +148,7 @@ cudaError_t launch_gather_f64(erpp_ctx* ctx, const double* u, int64_t n,
                               const double* const x[3], double* const up[3], cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int blocks = (int)((n + kWarps - 1) / kWarps);
+  ++ctx->launches;
   k_gather_f64<<<blocks, kWarps * 32, 0, st>>>(ctx->kp, n, x[0], x[1], x[2], u, up[0], up[1],
                                                up[2], ctx->err);
   return cudaGetLastError();
@@ -162,6 +163,7 @@ cudaError_t launch_scatter_f64(erpp_ctx* ctx, int64_t n, const double* const x[3
   if (e != cudaSuccess) return e;
   if (n <= 0) return cudaSuccess;
   int blocks = (int)((n + kWarps - 1) / kWarps);
+  ++ctx->launches;
   k_scatter_f64<<<blocks, kWarps * 32, 0, st>>>(kp, n, x[0], x[1], x[2], D[0], D[1], D[2],
                                                 fscale, S, ctx->err);
   return cudaGetLastError();

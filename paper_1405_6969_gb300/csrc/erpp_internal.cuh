@@ -98,6 +98,8 @@ struct erpp_ctx {
   int fp64;
   int maxseg[3];          // most tiles one window can reach per axis
   int tile_req[3];        // requested T_y, T_z, threads of the x/y-halo tiles (0: default)
+  int launches;           // kernels launched since erpp_step began (counted at each launch)
+  int last_step_launches; // kernels the most recent erpp_step launched
   // scratch (owned)
   int64_t cap;            // particle capacity of the per-particle arrays
   float4* geo_t;

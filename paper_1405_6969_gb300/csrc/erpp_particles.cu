@@ -354,6 +354,7 @@ cudaError_t launch_advance(erpp_ctx* ctx, const erpp_particles* P, const double*
   int blocks = (int)((n + 255) / 256);
   float4* fs = write_fscat ? ctx->fscat : nullptr;
   const bool f32 = !ctx->fp64;
+  ++ctx->launches;
   if (from_acc) {
     k_advance<true, true><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, ctx->up_acc, ctx->cap,
                                                   ctx->geo_t, ctx->geo_c, fs, first_step);

@@ -485,6 +485,7 @@ cudaError_t gather_xm(erpp_ctx* ctx, const float* u, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_gather_f32<XM, LMIN, XW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
+  ++ctx->launches;
   k_gather_f32<XM, LMIN, XW><<<kp.ntiles, kThreads, sm, st>>>(
       kp, u, ctx->tile_start, ctx->entries, ctx->entries_cap, ctx->xw, ctx->up_acc, ctx->cap);
   return cudaGetLastError();
@@ -497,6 +498,7 @@ cudaError_t scatter_xm(erpp_ctx* ctx, float* S, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_scatter_f32<XM, LMIN, XW, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
+  ++ctx->launches;
   k_scatter_f32<XM, LMIN, XW, MODE><<<kp.ntiles, kThreads, sm, st>>>(
       kp, S, ctx->halo, ctx->tile_start, ctx->entries, ctx->entries_cap, ctx->xw, ctx->fscat);
   return cudaGetLastError();
@@ -553,6 +555,7 @@ cudaError_t launch_scatter_f32(erpp_ctx* ctx, float* S, cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;
   const int64_t total = 3LL * kp.T[2] * kp.T[1] * (kp.xhlo + kp.xhhi) * kp.ntiles;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  ++ctx->launches;
   k_merge_halo<<<blocks, 256, 0, st>>>(kp, S, ctx->halo);
   return cudaGetLastError();
 }

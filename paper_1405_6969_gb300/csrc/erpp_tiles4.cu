@@ -1177,6 +1177,7 @@ cudaError_t gather4_nt(erpp_ctx* ctx, const float* u, cudaStream_t st) {
   CUtensorMap map;
   memset(&map, 0, sizeof(map));
   const int use_tma = field_tensor_map(kp, u, &map) ? 1 : 0;
+  ++ctx->launches;
   k_gather4<XM, LMIN, XW, NT><<<kp.ntiles, NT, sm, st>>>(kp, u, map, use_tma, ctx->tile_start,
                                                          ctx->entries, ctx->entries_cap, ctx->xw,
                                                          ctx->up_acc, ctx->cap, ctx->err);
@@ -1196,6 +1197,7 @@ cudaError_t scatter4_mode(erpp_ctx* ctx, float* S, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_scatter4<XM, LMIN, XW, MODE, NT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
+  ++ctx->launches;
   k_scatter4<XM, LMIN, XW, MODE, NT><<<kp.ntiles, NT, sm, st>>>(
       kp, S, ctx->halo, ctx->tile_start, ctx->entries, ctx->entries_cap, ctx->xw, ctx->fscat);
   return cudaGetLastError();
@@ -1252,6 +1254,7 @@ cudaError_t launch_scatter_f32_4(erpp_ctx* ctx, float* S, cudaStream_t st) {
     default: e = scatter4<16, 1, 16>(ctx, S, st); break;
   }
   if (e != cudaSuccess) return e;
+  ctx->launches += 2;
   k_merge_rows<<<ctx->kp.ntiles, kMergeThreads, 0, st>>>(ctx->kp, S, ctx->halo);
   k_merge_cols<<<ctx->kp.ntiles, kMergeThreads, 0, st>>>(ctx->kp, S, ctx->halo);
   return cudaGetLastError();

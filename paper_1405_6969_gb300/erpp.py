@@ -211,6 +211,13 @@ class Context:
         _lib.check(self.lib.erpp_get_tiling(self._h, out), "erpp_get_tiling")
         return tuple(int(v) for v in out)
 
+    def last_step_launches(self):
+        """Kernels the most recent step launched."""
+        n = ctypes.c_int32(0)
+        _lib.check(self.lib.erpp_last_step_launches(self._h, ctypes.byref(n)),
+                   "erpp_last_step_launches")
+        return int(n.value)
+
     def profile_enable(self, enable=True):
         _lib.check(self.lib.erpp_profile_enable(self._h, int(bool(enable))),
                    "erpp_profile_enable")
@@ -303,6 +310,14 @@ class Batch:
     def set_tiling(self, box, tile_y=0, tile_z=0, threads=0):
         _lib.check(self.lib.erpp_batch_set_tiling(self._h, int(box), int(tile_y), int(tile_z),
                                                   int(threads)), "erpp_batch_set_tiling")
+
+    def last_step_launches(self):
+        """Kernels of one batched step (the boxes' most recent step sequences,
+        the ones a captured graph replays)."""
+        n = ctypes.c_int32(0)
+        _lib.check(self.lib.erpp_batch_last_step_launches(self._h, ctypes.byref(n)),
+                   "erpp_batch_last_step_launches")
+        return int(n.value)
 
     def tiling(self, box):
         """erpp_get_tiling of one box: (design, W, T_y, T_z, threads)."""

@@ -145,6 +145,26 @@ def test_scatter_reproducible(erpp, name, w, npart):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_step_launch_count(erpp, precision):
+    """The library's own count of the kernels one step launches: FP32 =
+    binning (count, three scan kernels, fill) + gather + advance + scatter +
+    one or two halo merge kernels; FP64 plain form = gather + advance +
+    scatter."""
+    w = CASES[0][1]
+    grid, st = _setup(w, CASES[0][2])
+    ctx = erpp.Context(w.params(), precision=precision)
+    assert ctx.last_step_launches() == 0
+    ps = erpp.ParticleState.from_numpy(st)
+    ctx.step(grid_t(grid, precision), ps, first_step=True)
+    ctx.check()
+    n = ctx.last_step_launches()
+    if precision == "fp64":
+        assert n == 3
+    else:
+        assert n in (9, 10)  # two merge kernels with x/y-halo tiles, one otherwise
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("name,w,npart", CASES, ids=[c[0] for c in CASES])
 def test_interpolate(erpp, oracle_lib, precision, name, w, npart):
     p = w.params()
