@@ -169,6 +169,25 @@ erpp_status erpp_gather_backward(erpp_ctx* ctx, int64_t n, const double* const x
 erpp_status erpp_step(erpp_ctx* ctx, const void* u, const erpp_particles* P, void* S,
                       int first_step, erpp_stream stream);
 
+/* erpp_step on HOST data: u, S and every array of P (n doubles per
+ * component, radius and rho_p included) are host memory, page-locked for the
+ * copies to run asynchronously (pageable memory works, without overlap).
+ * The call copies u and P in once the work already on `stream` is done,
+ * runs the step on streams of its own and copies S (overwritten) and P's
+ * x, v, x_prev, D (updated) back, then returns without waiting: the host
+ * arrays must stay untouched, and the results are valid only after
+ * erpp_step_host_wait(ctx, s) and a synchronisation of s.  Successive calls
+ * overlap their copies with the neighbouring steps' computation (device
+ * staging in two slots, owned by the context: 2 x (2 grids + 14 n doubles));
+ * a call's particle upload waits for the previous call's particle download,
+ * the host arrays being the state of record.  The Python binding's
+ * Context.step_host is the user entry point. */
+erpp_status erpp_step_host(erpp_ctx* ctx, const void* u, const erpp_particles* P, void* S,
+                           int first_step, erpp_stream stream);
+/* Makes `stream` wait until every erpp_step_host call on ctx so far has
+ * copied its results back. */
+erpp_status erpp_step_host_wait(erpp_ctx* ctx, erpp_stream stream);
+
 /* Momentum bookkeeping (the impulse of Sec. 3.1): out[0..2] = dV sum_j S[c][j]
  * and out[3..5] = -(1/rho_f) sum_i M_i D[c][i], M_i the discrete kernel mass
  * (1 when normalised); both summed in FP64.  out is a HOST array of 6

@@ -77,6 +77,8 @@ _SIGS = {
     "erpp_particle_advance": (_st, [_vp, _dp3, ctypes.POINTER(Particles), ctypes.c_int, _vp]),
     "erpp_scatter_source": (_st, [_vp, _i64, _dp3, _dp3, _vp, _vp]),
     "erpp_step": (_st, [_vp, _vp, ctypes.POINTER(Particles), _vp, ctypes.c_int, _vp]),
+    "erpp_step_host": (_st, [_vp, _vp, ctypes.POINTER(Particles), _vp, ctypes.c_int, _vp]),
+    "erpp_step_host_wait": (_st, [_vp, _vp]),
     "erpp_momentum": (_st, [_vp, _vp, _i64, _dp3, _dp3, _dp, _vp]),
     "erpp_check": (_st, [_vp, _vp]),
     "erpp_debug_windows": (_st, [_vp, _i64, _dp3, _vp, _vp, _vp]),

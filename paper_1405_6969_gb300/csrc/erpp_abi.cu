@@ -361,6 +361,7 @@ erpp_status erpp_init(const erpp_params* p, erpp_ctx** out) {
 erpp_status erpp_destroy(erpp_ctx* c) {
   if (!c) return ERPP_OK;
   cudaDeviceSynchronize();
+  erpp::free_host_pipe(c);
   if (c->prof_ev) {
     for (int k = 0; k < kProfSets * 5; ++k) cudaEventDestroy(c->prof_ev[k]);
     free(c->prof_ev);
@@ -509,8 +510,16 @@ erpp_status erpp_step(erpp_ctx* c, const void* u, const erpp_particles* P, void*
     for (int a = 0; a < 3; ++a)
       if (!P->x[a] || !P->v[a] || !P->x_prev[a] || !P->D[a]) return ERPP_EINVAL;
   }
+  return erpp::step_device(c, u, P, S, first_step, (cudaStream_t)stream, nullptr);
+}
+
+}  // extern "C"
+
+namespace erpp {
+
+erpp_status step_device(erpp_ctx* c, const void* u, const erpp_particles* P, void* S,
+                        int first_step, cudaStream_t st, cudaEvent_t after_advance) {
   const int64_t n = P->n;
-  cudaStream_t st = (cudaStream_t)stream;
   erpp_status s = erpp::ensure_capacity(c, n);
   if (s) return s;
   const double* const xin[3] = {P->x[0], P->x[1], P->x[2]};
@@ -523,6 +532,7 @@ erpp_status erpp_step(erpp_ctx* c, const void* u, const erpp_particles* P, void*
     e = erpp::launch_gather_f64(c, (const double*)u, n, xin, up, st);
     const double* const upc[3] = {up[0], up[1], up[2]};
     if (e == cudaSuccess) e = erpp::launch_advance(c, P, upc, false, false, first_step, st);
+    if (e == cudaSuccess && after_advance) e = cudaEventRecord(after_advance, st);
     if (e == cudaSuccess)
       e = erpp::launch_scatter_f64(c, n, xprev, Dv, -1.0 / c->params.rho_f, (double*)S, st);
   } else {
@@ -534,6 +544,7 @@ erpp_status erpp_step(erpp_ctx* c, const void* u, const erpp_particles* P, void*
     if (e == cudaSuccess) e = erpp::launch_gather_f32(c, (const float*)u, n, st);
     if (ev) cudaEventRecord(ev[2], st);
     if (e == cudaSuccess) e = erpp::launch_advance(c, P, nullptr, true, true, first_step, st);
+    if (e == cudaSuccess && after_advance) e = cudaEventRecord(after_advance, st);
     if (ev) cudaEventRecord(ev[3], st);
     if (e == cudaSuccess) e = erpp::launch_scatter_f32(c, (float*)S, st);
     if (ev) cudaEventRecord(ev[4], st);
@@ -541,6 +552,10 @@ erpp_status erpp_step(erpp_ctx* c, const void* u, const erpp_particles* P, void*
   c->last_step_launches = c->launches;
   return set_cuda_err(e);
 }
+
+}  // namespace erpp
+
+extern "C" {
 
 erpp_status erpp_last_step_launches(erpp_ctx* c, int32_t* n) {
   if (!c || !n) return ERPP_EINVAL;

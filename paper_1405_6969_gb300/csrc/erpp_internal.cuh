@@ -98,6 +98,7 @@ struct erpp_ctx {
   int fp64;
   int maxseg[3];          // most tiles one window can reach per axis
   int tile_req[3];        // requested T_y, T_z, threads of the x/y-halo tiles (0: default)
+  struct erpp_host_pipe* hp;  // erpp_step_host staging and streams (lazily created)
   int launches;           // kernels launched since erpp_step began (counted at each launch)
   int last_step_launches; // kernels the most recent erpp_step launched
   // scratch (owned)
@@ -134,6 +135,12 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c);
 erpp_status ensure_capacity(erpp_ctx* c, int64_t n);  // may allocate (synchronous)
 int xw_len(const erpp_kparams& kp);
 inline int nbins(const erpp_kparams& kp) { return kp.design == 4 ? kp.ntiles : kp.ntiles * 32; }
+// The coupling step of erpp_step (arguments already checked); records
+// after_advance (when not null) on st once the particles are advanced.
+erpp_status step_device(erpp_ctx* c, const void* u, const erpp_particles* P, void* S,
+                        int first_step, cudaStream_t st, cudaEvent_t after_advance);
+// Frees the host-data pipeline of erpp_step_host (synchronises the device).
+void free_host_pipe(erpp_ctx* c);
 cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bool zero_acc,
                           cudaStream_t st);
 cudaError_t launch_gather_f32(erpp_ctx* ctx, const float* u, int64_t n, cudaStream_t st);

@@ -21,9 +21,17 @@ def _dptr(t):
     return ctypes.cast(ctypes.c_void_p(t.data_ptr()), _lib._dp)
 
 
-def _vec3(t):
-    """[3, n] float64 CUDA tensor -> double*[3]."""
-    _require(t, torch.float64, 2)
+def _require_host(t, dtype, ndim):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("expected a host (CPU) tensor")
+    if t.dtype != dtype or t.dim() != ndim or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} tensor of rank {ndim}, "
+                        f"got {t.dtype} {tuple(t.shape)}")
+
+
+def _vec3(t, host=False):
+    """[3, n] float64 CUDA (or, host=True, CPU) tensor -> double*[3]."""
+    (_require_host if host else _require)(t, torch.float64, 2)
     assert t.shape[0] == 3
     n = t.shape[1]
     base = t.data_ptr()
@@ -66,15 +74,22 @@ class ParticleState:
         return ParticleState(f(st.x), f(st.v), f(st.x_prev), f(st.D), f(st.radius),
                              f(st.rho_p))
 
-    def to_c(self):
+    def to_c(self, host=False):
+        """erpp_particles of the arrays (CUDA tensors; CPU ones with host=True)."""
         P = _lib.Particles()
         P.n = self.n
-        P.x, P.v = _vec3(self.x), _vec3(self.v)
-        P.x_prev, P.D = _vec3(self.x_prev), _vec3(self.D)
-        _require(self.radius, torch.float64, 1)
-        _require(self.rho_p, torch.float64, 1)
+        P.x, P.v = _vec3(self.x, host), _vec3(self.v, host)
+        P.x_prev, P.D = _vec3(self.x_prev, host), _vec3(self.D, host)
+        req = _require_host if host else _require
+        req(self.radius, torch.float64, 1)
+        req(self.rho_p, torch.float64, 1)
         P.radius, P.rho_p = _dptr(self.radius), _dptr(self.rho_p)
         return P
+
+    def pinned(self):
+        """Copy of the state in page-locked host memory."""
+        return ParticleState(*(t.detach().cpu().pin_memory() for t in
+                               (self.x, self.v, self.x_prev, self.D, self.radius, self.rho_p)))
 
 
 def make_params(params, precision="fp32", normalize=True, self_removal=True, kahan=False):
@@ -188,6 +203,26 @@ class Context:
         _lib.check(self.lib.erpp_step(self._h, self._grid(u), ctypes.byref(P), self._grid(S),
                                       int(bool(first_step)), _stream(stream)), "erpp_step")
         return S
+
+    def step_host(self, u, state, S, first_step=False, stream=None):
+        """erpp_step_host: u, S and the ParticleState on the host (CPU tensors,
+        page-locked for overlap, e.g. state.pinned()).  Returns once the copies
+        and the step are enqueued; call step_host_wait() and synchronise the
+        stream before reading S or the state."""
+        for g in (u, S):
+            _require_host(g, self.grid_dtype, 4)
+            if tuple(g.shape) != self.shape:
+                raise ValueError(f"grid shape {tuple(g.shape)} != {self.shape}")
+        P = state.to_c(host=True)
+        _lib.check(self.lib.erpp_step_host(self._h, ctypes.c_void_p(u.data_ptr()), ctypes.byref(P),
+                                           ctypes.c_void_p(S.data_ptr()),
+                                           int(bool(first_step)), _stream(stream)),
+                   "erpp_step_host")
+        return S
+
+    def step_host_wait(self, stream=None):
+        """Makes the stream wait for every step_host call so far."""
+        _lib.check(self.lib.erpp_step_host_wait(self._h, _stream(stream)), "erpp_step_host_wait")
 
     def momentum(self, S, x, D, stream=None):
         out = (ctypes.c_double * 6)()
