@@ -159,6 +159,25 @@ def algorithmic_bytes(w, n_p):
             "step": 24 * w.n_nodes + 208 * n_p}
 
 
+def captured_traffic(w, kernel, tiling):
+    """DRAM bytes (read + write) per launch of the dominant phase from the ncu
+    capture summarised in profiles/, when it was taken on this workload, tile
+    shape and kernel source; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "erpp_step_shear512_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        with open(os.path.join(ROOT, d["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, ValueError, KeyError):
+        return None
+    if (d.get("workload") != w.name or kernel != "scatter" or sha != d.get("source_sha256")
+            or list(tiling[2:5]) != list(d.get("tiling", []))):
+        return None
+    return d["traffic_bytes"]
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -395,7 +414,8 @@ def main():
     peak, peak_kind = measured_peaks()
     achieved = alg[dom] / (per[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "unit": "GB/s", "frac": achieved / peak,
+                "traffic": captured_traffic(w, dom, ctx.tiling()),
                 "peak_kind": peak_kind}
     step_gbs = alg["step"] / (ms_per_step * 1e-3) / 1e9
 
