@@ -266,7 +266,11 @@ def test_clustered_full_size_error_report(erpp, oracle_lib, mode):
           ", ".join(f"{k} {v:.3e}" for k, v in errs.items()))
     tol = 10 * TOL[precision]
     assert errs["S"] < tol and errs["D"] < tol and errs["v"] < tol
-    assert errs["x_max_abs"] < (1e-12 if precision == "fp64" else 1e-9)
+    # positions integrate the velocities in FP64: over the ten steps their
+    # error is at most steps * dt * (velocity tolerance) * max |v|
+    # (FP64: a few ulps of the coordinates)
+    vmax = float(np.abs(ref.v).max())
+    assert errs["x_max_abs"] < max(10 * p["dt"] * TOL[precision] * vmax, 1e-12)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
