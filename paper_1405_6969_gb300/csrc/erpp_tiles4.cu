@@ -13,9 +13,11 @@
 // (x', y', z') sits in shared-memory bank (x' + 16 (y' + z')) mod 32.
 // Staging: a tile whose staged box needs no periodic wrap (and whose layout
 // has no plane padding) is loaded by one TMA copy of the 4D box
-// (x, y, z, component) of the field, completed on an mbarrier; the others use
-// asynchronous global-to-shared copies (16-byte chunks for the aligned
-// interior, 4-byte copies for the wrapped halo columns and rows).
+// (x, y, z, component) of the field, completed on an mbarrier; a wrapping tile
+// with 16-byte aligned rows by one bulk copy per staged row and periodic
+// segment (same mbarrier); any other by 4-byte asynchronous copies.  Each
+// thread's record of the first batch is loaded before the staging is issued,
+// so that the two latencies overlap.
 //
 // Units and buckets.  A unit is one z-plane of a piece: ly rows of lx nodes,
 // the same for every particle (lx, ly = the window lengths).  Walking its rows
@@ -29,11 +31,12 @@
 // an odd ly its last row may share a bank); the schedule splits the units of
 // every bucket pair evenly between its two buckets.
 //
-// Schedule.  Per batch of pieces the block builds a table
-// sched[round][warp][lane]: bucket b's k-th unit goes to lane b of warp k mod 8
-// in round k / 8, for R = ceil(units / 256) rounds; units beyond a bucket's 8R
-// slots fill the free slots of other buckets, last rounds first (those lanes
-// then share banks with the slot's own bucket).  Every warp runs its R rounds
+// Schedule.  Per batch of pieces (at most one per thread) the block builds a
+// table sched[round][warp][lane]: bucket b's k-th unit goes to lane b of warp
+// k mod NW in round k / NW (NW warps per block), for the fewest rounds R that
+// hold every unit; units beyond a bucket's NW R slots fill the free slots of
+// other buckets, last rounds first (those lanes then share banks with the
+// slot's own bucket).  Every warp runs its R rounds
 // independently; in a round all lanes walk their units' rows together (the
 // longest window of the round), so a unit switch is a few shared-memory reads
 // per lane.  The batch's piece records and x-weights are staged in shared
@@ -51,11 +54,15 @@
 // max|f| (no sum can overflow).  Per unit G = round(f e_x e_z 2^30 / B) per
 // component and x-slot, per row W = round(e_y 2^31), and each node receives
 // the high word of G W + 2^31 (one wide multiply-add and one atomic per node
-// component).  Tiles with more than 1024 pieces add FP32 values instead, and
-// ERPP_KAHAN adds FP32 values with the exact rounding error of each addition
-// (two-sum on the atomic's old value) kept in a second array.  The interior
-// is written once; the halo strips go to a buffer that k_merge_rows and
-// k_merge_cols add to the neighbouring tiles in a fixed order.
+// component).  A tile of one batch sums B from its staged forces, a larger
+// one by a pass over its entries first.  Tiles with more than 1024 pieces add
+// FP32 values instead, and ERPP_KAHAN adds FP32 values with the exact rounding
+// error of each addition (two-sum on the atomic's old value) kept in a second
+// array.  The final values are formed in shared memory and every staged row
+// leaves by one bulk asynchronous copy (interior rows to S, y-halo rows to a
+// strip buffer), the x-halo columns by plain stores; k_merge_rows and
+// k_merge_cols then add the strips to the neighbouring tiles in a fixed
+// order.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
