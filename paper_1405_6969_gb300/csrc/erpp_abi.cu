@@ -186,7 +186,6 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
   kp.hlo = (int)floor(cpmax);
   kp.xs = (int)floor(2.0 * cpmax + 1e-6) + 1;
   if (kp.hlo > 15 || kp.xs > 31) return ERPP_EINVAL;  // windows of at most 31 nodes
-  kp.rows = 32 / kp.xs;
   kp.dV = kp.dx[0] * kp.dx[1] * kp.dx[2];
   kp.rho_f = p->rho_f;
   kp.nu = p->nu;
@@ -246,7 +245,6 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
   }
   if (ntiles > (1 << 24)) return ERPP_EINVAL;
   kp.ntiles = (int)ntiles;
-  kp.rows = 0;
   kp.pxy = kp.px * kp.T[1];
   kp.plane = kp.pxy * kp.T[2];
   if ((size_t)kp.plane * 6 * sizeof(float) > 227 * 1024) return ERPP_EINVAL;

@@ -55,7 +55,6 @@ struct erpp_kparams {
   int32_t xs;        // longest window, floor(2 c') + 1 (all axes)
   int32_t xhlo, xhhi;// x-halo columns staged below / above a tile
   int32_t xlmin, xxs; // shortest / longest x-window (floor(2 c'_x), floor(2 c'_x) + 1)
-  int32_t rows;      // (unused by the lane-per-piece kernels)
   int32_t px, pxy;   // shared-memory pitches (floats) of one tile
   int32_t plane;     // floats per component of one tile = pxy * T_z
   int32_t design;    // 3: x-halo tiles, pieces cut in y and z (bucket bins);
