@@ -245,3 +245,43 @@ def scatter_nodes(p, x, D, nodes):
                                      nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                      _ptr(out)), "scatter_nodes")
     return out
+
+
+def step_threads(p, u, state, nthreads, first_step=False):
+    """The same step as ``step``, on ``nthreads`` host threads.
+
+    The particles are split into contiguous chunks and each thread runs the
+    unchanged oracle step on its chunk into a source of its own (the C calls
+    release the interpreter lock); the partial sources are then summed by the
+    threads over z-slabs.  Particle results equal those of ``step`` exactly
+    (every particle is updated on its own); the source differs only in the
+    order of its FP64 sums.  Used to time the oracle on all host cores."""
+    import concurrent.futures as cf
+    p = _params(p)
+    u = _f64(u, _grid_shape(p))
+    n = state.n
+    nthreads = max(1, min(int(nthreads), n)) if n else 1
+    cuts = [n * k // nthreads for k in range(nthreads + 1)]
+    names = ("x", "v", "x_prev", "D", "radius", "rho_p")
+    chunks = []
+    for k in range(nthreads):
+        a, b = cuts[k], cuts[k + 1]
+        chunks.append(type(state)(*(np.ascontiguousarray(getattr(state, m)[..., a:b])
+                                    for m in names)))
+    with cf.ThreadPoolExecutor(nthreads) as ex:
+        parts = list(ex.map(lambda c: step(p, u, c, first_step=first_step), chunks))
+        S = parts[0]
+        nz = S.shape[1]
+        zc = [nz * k // nthreads for k in range(nthreads + 1)]
+
+        def reduce_slab(k):
+            sl = slice(zc[k], zc[k + 1])
+            for part in parts[1:]:
+                np.add(S[:, sl], part[:, sl], out=S[:, sl])
+
+        list(ex.map(reduce_slab, range(nthreads)))
+    for k, c in enumerate(chunks):
+        a, b = cuts[k], cuts[k + 1]
+        for m in ("x", "v", "x_prev", "D"):
+            getattr(state, m)[..., a:b] = getattr(c, m)
+    return S
