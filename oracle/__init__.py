@@ -99,6 +99,8 @@ def _load():
                 f.restype = ctypes.c_int
             lib.orc_self_velocity.argtypes = [P, i64, d, d, d]
             lib.orc_self_velocity.restype = None
+            lib.orc_self_velocity_s2.argtypes = [P, ctypes.c_double, i64, d, d, d]
+            lib.orc_self_velocity_s2.restype = None
             _lib = lib
     return _lib
 
@@ -161,13 +163,17 @@ def gather(p, x, u):
     return up
 
 
-def self_velocity(p, r, D):
-    """Closed-form self disturbance v_self(r; D) [3, n]."""
+def self_velocity(p, r, D, s2=None):
+    """Closed-form self disturbance v_self(r; D) [3, n]; by default at the
+    variance the matching kernel gather sees, else at ``s2``."""
     p = _params(p)
     r, D = _f64(r), _f64(D)
     out = np.empty_like(r)
-    _load().orc_self_velocity(ctypes.byref(p), r.shape[1], _ptr(r), _ptr(D),
-                              _ptr(out))
+    if s2 is None:
+        _load().orc_self_velocity(ctypes.byref(p), r.shape[1], _ptr(r), _ptr(D), _ptr(out))
+    else:
+        _load().orc_self_velocity_s2(ctypes.byref(p), float(s2), r.shape[1], _ptr(r),
+                                     _ptr(D), _ptr(out))
     return out
 
 

@@ -30,6 +30,8 @@
  *   orc_scatter        S_j = -(1/rho_f) sum_p D_p W_p(j)          (Sec. 2.4, Eq. ns_regularized_filtered)
  *   orc_gather         u_p = sum_j dV W_p(j) u_j + shear y_p e_x   (matching kernel gather, Sec. 2.5)
  *   orc_self_velocity  closed-form regularised self disturbance    (App. A.5, Eq. disturbance_velo)
+ *   orc_self_velocity_s2  the same at a given variance s2 (a point-value gather
+ *                      sees it at 2 nu (eps_R + dt), without the gather's sigma_R^2)
  *   orc_advance        self removal, Stokes drag, explicit Euler   (Sec. 2.5, Eqs. particle_motion, force_stokes_drag)
  *   orc_step           gather + advance + scatter                  (Sec. 2.4-2.5)
  *   orc_momentum       grid and particle momentum of the source   (impulse, Sec. 3.1)
@@ -273,13 +275,10 @@ static double orc_F(double eta) {
  * prefactor -dt/rho_f that Eq. pseudo_velo_num carries:
  *   v(r) = -(dt/rho_f) (2 pi s2)^(-3/2) { [e^(-eta^2) - F] D - (D.rhat)[e^(-eta^2) - 3F] rhat },
  *   eta = |r| / sqrt(2 s2).
- * s2 is the variance of the disturbance as seen by the gather:
- *   s2 = 2 nu (eps_R + dt)  (forcing diffused one step, App. A.5)
- *      + sigma_R^2           (the kernel gather filters it once more).
+ * s2 is the variance of the disturbance as seen by the gather (below).
  * r [3][n] and D [3][n] in, out [3][n]. */
-void orc_self_velocity(const orc_params* p, int64_t n, const double* r, const double* D,
-                       double* out) {
-  double s2 = (2.0 * p->nu) * (p->eps_R + p->dt) + (2.0 * p->nu) * p->eps_R;
+void orc_self_velocity_s2(const orc_params* p, double s2, int64_t n, const double* r,
+                          const double* D, double* out) {
   double pref = -(p->dt / p->rho_f) / pow(2.0 * ORC_PI * s2, 1.5);
   for (int64_t i = 0; i < n; ++i) {
     double rv[3], Dv[3];
@@ -300,6 +299,15 @@ void orc_self_velocity(const orc_params* p, int64_t n, const double* r, const do
     for (int a = 0; a < 3; ++a)
       out[(size_t)a * n + i] = pref * ((e - F) * Dv[a] - Ddotr * (e - 3.0 * F) * rh[a]);
   }
+}
+
+/* The disturbance as the matching kernel gather sees it:
+ *   s2 = 2 nu (eps_R + dt)  (forcing diffused one step, App. A.5)
+ *      + sigma_R^2           (the kernel gather filters it once more). */
+void orc_self_velocity(const orc_params* p, int64_t n, const double* r, const double* D,
+                       double* out) {
+  double s2 = (2.0 * p->nu) * (p->eps_R + p->dt) + (2.0 * p->nu) * p->eps_R;
+  orc_self_velocity_s2(p, s2, n, r, D, out);
 }
 
 static double orc_min_image(double d, double L) {
