@@ -58,6 +58,8 @@ def parse():
                          "the autotuner")
     ap.add_argument("--no-loop", action="store_true",
                     help="skip the closed-loop (coupling + fluid stand-in) timing")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the timing of the PIC and point-value-gather steps")
     ap.add_argument("--workload", default="shear", choices=["shear", "cube256", "batched64"],
                     help="shear: 512x256x256 box (the benchmark); cube256: 256^3, 1M "
                          "particles (profiling case); batched64: 64 independent boxes "
@@ -464,6 +466,36 @@ def main():
         del u_loop
         fl.close()
 
+    # the same workload with the other weights (ERPP_PIC: trilinear source and
+    # gather, 8 + 8 nodes per particle; ERPP_POINT_GATHER: 4-point Lagrange
+    # gather, 64 nodes, and the Gaussian source)
+    variants = None
+    if not args.no_variants:
+        variants = {}
+        for kind in ("pic", "point"):
+            vctx = Context(w.params(), precision="fp32", weights=kind)
+            vps = ParticleState.from_numpy(st)
+            for k in range(3):
+                vctx.step(u, vps, S=S, first_step=(k == 0))
+            torch.cuda.synchronize()
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            n_var = 50
+            v0.record(stream)
+            for _ in range(n_var):
+                vctx.step(u, vps, S=S)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            vctx.check()
+            v_ms = v0.elapsed_time(v1) / n_var
+            nodes = (16 * w.n_particles if kind == "pic"
+                     else 64 * w.n_particles + stencil_nodes(st.x, w))
+            variants[kind] = {"ms_per_step": v_ms, "node_updates_per_step": nodes,
+                              "node_updates_per_s": nodes / (v_ms * 1e-3),
+                              "gpu_launches_per_step": vctx.last_step_launches()}
+            vctx.close()
+            del vps
+
     # end to end through the public API: host (pinned) buffers in and out
     e2e = None
     if not args.no_e2e:
@@ -524,6 +556,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "coupled_loop": loop,
+            "weights_variants": variants,
             "tiling": tiling,
             "e2e": e2e,
             # counted by the library at each kernel launch of a step

@@ -63,9 +63,35 @@ enum {
   ERPP_FP64 = 1u << 1,         /* double grids; plain FP64 kernels           */
   ERPP_NORMALIZE = 1u << 2,    /* unit discrete mass per axis (recommended)  */
   ERPP_SELF_REMOVAL = 1u << 3, /* subtract the closed-form self disturbance  */
-  ERPP_KAHAN = 1u << 4         /* FP32 only: compensated (two-sum) scatter
+  ERPP_KAHAN = 1u << 4,        /* FP32 only: compensated (two-sum) scatter
                                   accumulation; costs a second shared array  */
+  ERPP_PIC = 1u << 5,          /* classical particle-in-cell coupling instead
+                                  of the regularised kernel (see below)      */
+  ERPP_POINT_GATHER = 1u << 6  /* point-value gather (see below); the source
+                                  stays the regularised kernel               */
 };
+
+/* Other weights on the same grid (the comparisons of Sec. 3.2.1-3.2.2 and the
+ * interpolation question of Sec. 2.5).  At most one of the two flags.
+ *
+ * ERPP_PIC (cloud in cell): a particle at grid coordinates s = x N / L (one
+ *   rounding per axis), cell j0 = floor(s), f = s - j0, gives its force to the
+ *   8 nodes j0 .. j0 + 1 (wrapped) with the trilinear weights
+ *   w = prod_a (1 - f_a or f_a), as the source density
+ *   S_j = -(1/rho_f) sum_p D_p w_p(j) / dV, and the fluid velocity is
+ *   interpolated at the particle with the same weights.  The self
+ *   disturbance of PIC has no closed form: ERPP_SELF_REMOVAL and ERPP_KAHAN
+ *   are rejected with it (ERPP_EINVAL).  The scatter adds with device atomics:
+ *   in FP32 the rounding of a node's sum depends on the order of arrival.
+ * ERPP_POINT_GATHER: the fluid velocity at the particle is the separable
+ *   4-point Lagrange (cubic) interpolant over the nodes j0 - 1 .. j0 + 2; the
+ *   self disturbance is removed at the variance the particle's point sees,
+ *   s2 = 2 nu (eps_R + dt), without the gather's own sigma_R^2.
+ * Both keep eps_R and cutoff subject to the stencil requirements below.  They
+ * apply to erpp_interpolate, erpp_particle_advance, erpp_scatter_source,
+ * erpp_step, erpp_step_host and erpp_momentum; the adjoints, the batched step
+ * and erpp_interpolate_noalloc return ERPP_EINVAL for such a context or
+ * parameter set. */
 
 /* Physical and numerical parameters (Sec. 2.3-2.5).  sigma_R =
  * sqrt(2 nu eps_R); the stencil keeps, per axis, the nodes within

@@ -49,6 +49,10 @@ void free_scratch(erpp_ctx* c) {
   cudaFree(c->entries);
   cudaFree(c->piece_slot);
   cudaFree(c->up64);
+  cudaFree(c->w_key);
+  cudaFree(c->w_slot);
+  cudaFree(c->w_perm);
+  c->w_key = c->w_slot = c->w_perm = nullptr;
   c->geo_t = nullptr;
   c->geo_c = nullptr;
   c->xw = nullptr;
@@ -72,9 +76,14 @@ erpp_status ensure_capacity(erpp_ctx* c, int64_t n) {
   int64_t cap = std::max<int64_t>(n, 1024);
   free_scratch(c);
   cudaError_t e = cudaSuccess;
-  if (c->fp64) {
+  if (c->fp64 || c->kp.weights != ERPP_W_GAUSS)
     e = cudaMalloc(&c->up64, sizeof(double) * 3 * (size_t)cap);
-  } else {
+  if (c->kp.weights != ERPP_W_GAUSS) {
+    if (e == cudaSuccess) e = cudaMalloc(&c->w_key, sizeof(int32_t) * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc(&c->w_slot, sizeof(int32_t) * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc(&c->w_perm, sizeof(int32_t) * (size_t)cap);
+  }
+  if (!c->fp64 && e == cudaSuccess) {
     int64_t ecap = cap * (int64_t)c->maxseg[0] * c->maxseg[1] * c->maxseg[2];
     e = cudaMalloc(&c->geo_t, sizeof(float4) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->xw, sizeof(float) * (size_t)c->xw_len * (size_t)cap);
@@ -109,6 +118,21 @@ erpp_status alloc_tile_tables(erpp_ctx* c) {
   if (e == cudaSuccess) e = cudaMalloc(&c->scan_tmp, sizeof(int32_t) * (nbins / 4096 + 1));
   const size_t hb = (size_t)kp.ntiles * (size_t)kp.halo_per_tile;
   if (e == cudaSuccess) e = cudaMalloc(&c->halo, sizeof(float) * hb);
+  return set_cuda_err(e);
+}
+
+// Cell-block tables of the other weights' particle sort (8 x 8 x 8-node blocks
+// plus one bin for invalid positions).
+erpp_status alloc_weight_tables(erpp_ctx* c) {
+  if (c->kp.weights == ERPP_W_GAUSS) return ERPP_OK;
+  const erpp_kparams& kp = c->kp;
+  int64_t nb = 1;
+  for (int a = 0; a < 3; ++a) nb *= (kp.n[a] + 7) / 8;
+  if (nb + 1 > (int64_t)1 << 30) return ERPP_EINVAL;
+  c->w_nbins = (int)nb + 1;
+  cudaError_t e = cudaMalloc(&c->w_cnt, sizeof(int32_t) * (size_t)c->w_nbins);
+  if (e == cudaSuccess) e = cudaMalloc(&c->w_start, sizeof(int32_t) * ((size_t)c->w_nbins + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&c->w_tmp, sizeof(int32_t) * (c->w_nbins / 4096 + 1));
   return set_cuda_err(e);
 }
 
@@ -157,7 +181,10 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
   if (prec != ERPP_FP32 && prec != ERPP_FP64) return ERPP_EINVAL;
   if ((p->flags & ERPP_KAHAN) && prec != ERPP_FP32) return ERPP_EINVAL;
   if (p->flags & ~(uint32_t)(ERPP_FP32 | ERPP_FP64 | ERPP_NORMALIZE | ERPP_SELF_REMOVAL |
-                             ERPP_KAHAN))
+                             ERPP_KAHAN | ERPP_PIC | ERPP_POINT_GATHER))
+    return ERPP_EINVAL;
+  if ((p->flags & ERPP_PIC) &&
+      (p->flags & (ERPP_POINT_GATHER | ERPP_SELF_REMOVAL | ERPP_KAHAN)))
     return ERPP_EINVAL;
   if ((double)n[0] * n[1] * n[2] * 3.0 >= 9.0e18) return ERPP_EINVAL;
 
@@ -196,7 +223,12 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
   kp.shear_rate = p->shear_rate;
   kp.sig2 = sig2;
   kp.raw_norm3 = pow(2.0 * kPi * sig2, -1.5);
-  kp.self_s2 = (2.0 * p->nu) * (p->eps_R + p->dt) + (2.0 * p->nu) * p->eps_R;
+  kp.weights = (p->flags & ERPP_PIC) ? ERPP_W_PIC
+               : (p->flags & ERPP_POINT_GATHER) ? ERPP_W_POINT : ERPP_W_GAUSS;
+  // The disturbance as the gather sees it: forcing diffused one step, plus the
+  // matching kernel's own sigma_R^2 (none for a point-value gather).
+  kp.self_s2 = (2.0 * p->nu) * (p->eps_R + p->dt) +
+               (kp.weights == ERPP_W_POINT ? 0.0 : (2.0 * p->nu) * p->eps_R);
   kp.self_pref = (float)(-(p->dt / p->rho_f) / pow(2.0 * kPi * kp.self_s2, 1.5));
   kp.self_inv_w = (float)(1.0 / sqrt(2.0 * kp.self_s2));
   kp.drag_f = (float)(6.0 * kPi * kp.mu);
@@ -347,6 +379,7 @@ erpp_status erpp_init(const erpp_params* p, erpp_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->red, sizeof(double) * (6 * 304 + 8));
   erpp_status st = set_cuda_err(e);
   if (st == ERPP_OK) st = alloc_tile_tables(c);
+  if (st == ERPP_OK) st = alloc_weight_tables(c);
   if (st != ERPP_OK) {
     erpp_destroy(c);
     cudaGetLastError();
@@ -369,6 +402,9 @@ erpp_status erpp_destroy(erpp_ctx* c) {
   cudaFree(c->tile_start);
   cudaFree(c->scan_tmp);
   cudaFree(c->halo);
+  cudaFree(c->w_cnt);
+  cudaFree(c->w_start);
+  cudaFree(c->w_tmp);
   cudaFree(c->err);
   cudaFree(c->red);
   free(c);
@@ -424,7 +460,10 @@ erpp_status erpp_interpolate(erpp_ctx* c, const void* u, int64_t n, const double
   erpp_status s = erpp::ensure_capacity(c, n);
   if (s) return s;
   cudaError_t e;
-  if (c->fp64) {
+  if (c->kp.weights != ERPP_W_GAUSS) {
+    e = erpp::sort_by_cell_block(c, n, x, st);
+    if (e == cudaSuccess) e = erpp::launch_gather_weights(c, u, n, x, up, st);
+  } else if (c->fp64) {
     e = erpp::launch_gather_f64(c, (const double*)u, n, x, up, st);
   } else {
     e = erpp::bin_particles(c, n, x, true, st);
@@ -452,21 +491,13 @@ erpp_status erpp_scatter_source(erpp_ctx* c, int64_t n, const double* const x[3]
   cudaStream_t st = (cudaStream_t)stream;
   erpp_status s = erpp::ensure_capacity(c, n);
   if (s) return s;
-  cudaError_t e;
-  if (c->fp64) {
-    e = erpp::launch_scatter_f64(c, n, x, D, -1.0 / c->params.rho_f, (double*)S, st);
-  } else {
-    e = erpp::bin_particles(c, n, x, false, st);
-    if (e == cudaSuccess) e = erpp::launch_prep_fscat(c, n, D, -c->kp.inv_rho_dV, st);
-    if (e == cudaSuccess) e = erpp::launch_scatter_f32(c, (float*)S, st);
-  }
-  return set_cuda_err(e);
+  return set_cuda_err(erpp::scatter_source(c, n, x, D, S, st));
 }
 
 erpp_status erpp_scatter_backward(erpp_ctx* c, int64_t n, const double* const x[3],
                                   const double* const D[3], const void* R, double* const dD[3],
                                   double* const dx[3], erpp_stream stream) {
-  if (!c || !R || check_n(n)) return ERPP_EINVAL;
+  if (!c || !R || check_n(n) || c->kp.weights != ERPP_W_GAUSS) return ERPP_EINVAL;
   if (n == 0) return ERPP_OK;
   if (!valid_vec(x) || !valid_vec(D) || !dx || !dx[0] || !dx[1] || !dx[2]) return ERPP_EINVAL;
   if (dD && (!dD[0] || !dD[1] || !dD[2])) return ERPP_EINVAL;
@@ -478,7 +509,7 @@ erpp_status erpp_scatter_backward(erpp_ctx* c, int64_t n, const double* const x[
 erpp_status erpp_gather_backward(erpp_ctx* c, int64_t n, const double* const x[3], const void* u,
                                  const double* const g[3], void* du, double* const dx[3],
                                  erpp_stream stream) {
-  if (!c || !u || check_n(n)) return ERPP_EINVAL;
+  if (!c || !u || check_n(n) || c->kp.weights != ERPP_W_GAUSS) return ERPP_EINVAL;
   if (n > 0 && (!valid_vec(x) || !valid_vec(g))) return ERPP_EINVAL;
   if (dx && (!dx[0] || !dx[1] || !dx[2])) return ERPP_EINVAL;
   if (!du && !dx) return ERPP_EINVAL;
@@ -515,6 +546,21 @@ erpp_status erpp_step(erpp_ctx* c, const void* u, const erpp_particles* P, void*
 
 namespace erpp {
 
+cudaError_t scatter_source(erpp_ctx* c, int64_t n, const double* const x[3],
+                           const double* const D[3], void* S, cudaStream_t st) {
+  if (c->kp.weights == ERPP_W_PIC) {
+    cudaError_t e = erpp::sort_by_cell_block(c, n, x, st);
+    if (e != cudaSuccess) return e;
+    return erpp::launch_scatter_pic(c, n, x, D, -1.0 / c->params.rho_f, S, st);
+  }
+  if (c->fp64)
+    return erpp::launch_scatter_f64(c, n, x, D, -1.0 / c->params.rho_f, (double*)S, st);
+  cudaError_t e = erpp::bin_particles(c, n, x, false, st);
+  if (e == cudaSuccess) e = erpp::launch_prep_fscat(c, n, D, -c->kp.inv_rho_dV, st);
+  if (e == cudaSuccess) e = erpp::launch_scatter_f32(c, (float*)S, st);
+  return e;
+}
+
 erpp_status step_device(erpp_ctx* c, const void* u, const erpp_particles* P, void* S,
                         int first_step, cudaStream_t st, cudaEvent_t after_advance) {
   const int64_t n = P->n;
@@ -525,7 +571,23 @@ erpp_status step_device(erpp_ctx* c, const void* u, const erpp_particles* P, voi
   const double* const Dv[3] = {P->D[0], P->D[1], P->D[2]};
   cudaError_t e;
   c->launches = 0;
-  if (c->fp64) {
+  if (c->kp.weights != ERPP_W_GAUSS) {
+    // other weights: gather into up64, advance from it, scatter D^n at x^n
+    // (the PIC source reuses the order of the gather: x_prev holds x^n after
+    // the advance)
+    double* up[3] = {c->up64, c->up64 + c->cap, c->up64 + 2 * c->cap};
+    e = erpp::sort_by_cell_block(c, n, xin, st);
+    if (e == cudaSuccess) e = erpp::launch_gather_weights(c, u, n, xin, up, st);
+    const double* const upc[3] = {up[0], up[1], up[2]};
+    if (e == cudaSuccess) e = erpp::launch_advance(c, P, upc, false, false, first_step, st);
+    if (e == cudaSuccess && after_advance) e = cudaEventRecord(after_advance, st);
+    if (e == cudaSuccess) {
+      if (c->kp.weights == ERPP_W_PIC)
+        e = erpp::launch_scatter_pic(c, n, xprev, Dv, -1.0 / c->params.rho_f, S, st);
+      else
+        e = erpp::scatter_source(c, n, xprev, Dv, S, st);
+    }
+  } else if (c->fp64) {
     double* up[3] = {c->up64, c->up64 + c->cap, c->up64 + 2 * c->cap};
     e = erpp::launch_gather_f64(c, (const double*)u, n, xin, up, st);
     const double* const upc[3] = {up[0], up[1], up[2]};

@@ -316,6 +316,16 @@ __global__ void k_scan_add(int32_t* __restrict__ start, const int32_t* __restric
 
 namespace erpp {
 
+cudaError_t launch_scan(erpp_ctx* ctx, const int32_t* cnt, int32_t* start, int32_t* tmp,
+                        int nbins, cudaStream_t st) {
+  const int nchunks = (nbins + kScanChunk - 1) / kScanChunk;
+  ctx->launches += 3;
+  k_scan_local<<<nchunks, 1024, 0, st>>>(cnt, start, tmp, nbins);
+  k_scan_top<<<1, 1024, 0, st>>>(tmp, nchunks, start, nbins);
+  k_scan_add<<<(nbins + 255) / 256, 256, 0, st>>>(start, tmp, nbins);
+  return cudaGetLastError();
+}
+
 cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bool zero_acc,
                           cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;

@@ -31,6 +31,11 @@
 
 #include "../../include/erpp.h"
 
+// Weights of the coupling (erpp_kparams.weights).
+#define ERPP_W_GAUSS 0  // the regularised Gaussian kernel, matching gather
+#define ERPP_W_PIC 1    // trilinear projection and interpolation (cloud in cell)
+#define ERPP_W_POINT 2  // Gaussian source, 4-point Lagrange point-value gather
+
 // Sticky device error bits.
 #define ERPP_ERRBIT_RANGE 1u
 #define ERPP_ERRBIT_BOUNDS 2u
@@ -66,6 +71,7 @@ struct erpp_kparams {
   int64_t halo_per_tile; // design 4: floats of one tile's scatter halo strips
   int64_t ystrip_off;    // design 4: offset (floats) of the y-strips in them
   int32_t normalize, self_removal, kahan;
+  int32_t weights;   // ERPP_W_GAUSS, ERPP_W_PIC or ERPP_W_POINT
   double inv_dx[3];  // N / L
   double L[3];
   double cp[3];      // r_c / dx
@@ -108,7 +114,14 @@ struct erpp_ctx {
   int xw_len;
   float* up_acc;          // [3][cap]
   float4* fscat;
-  double* up64;           // FP64 mode: gathered velocity [3][cap]
+  double* up64;           // FP64 mode or other weights: gathered velocity [3][cap]
+  int32_t* w_key;         // other weights: sort key, place and order of each particle [cap]
+  int32_t* w_slot;
+  int32_t* w_perm;
+  int32_t* w_cnt;         // [w_nbins]: particles per cell block (last: invalid positions)
+  int32_t* w_start;       // [w_nbins + 1]
+  int32_t* w_tmp;         // scan chunk totals
+  int w_nbins;
   int4* entries;
   int64_t entries_cap;
   float* halo;            // scatter x-halo columns, [ntiles][3][T_z][T_y][xhlo + xhhi]
@@ -138,6 +151,10 @@ inline int nbins(const erpp_kparams& kp) { return kp.design == 4 ? kp.ntiles : k
 // after_advance (when not null) on st once the particles are advanced.
 erpp_status step_device(erpp_ctx* c, const void* u, const erpp_particles* P, void* S,
                         int first_step, cudaStream_t st, cudaEvent_t after_advance);
+// The source of forces D at positions x into S (zeroed first), -(1/rho_f) times
+// the context's projection weights.
+cudaError_t scatter_source(erpp_ctx* c, int64_t n, const double* const x[3],
+                           const double* const D[3], void* S, cudaStream_t st);
 // Frees the host-data pipeline of erpp_step_host (synchronises the device).
 void free_host_pipe(erpp_ctx* c);
 cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bool zero_acc,
@@ -168,6 +185,23 @@ cudaError_t launch_momentum(erpp_ctx* ctx, const void* S, int64_t n, const doubl
                             const double* const D[3], cudaStream_t st);
 cudaError_t launch_windows(erpp_ctx* ctx, int64_t n, const double* const x[3], int32_t* jlo,
                            int32_t* jhi, cudaStream_t st);
+// Other weights (ERPP_W_PIC, ERPP_W_POINT): the gather of u (the context's grid
+// type) into up, and the PIC source S = fscale sum_p D_p w_p(j) / dV (zeroes S
+// first).
+// Exclusive scan of cnt[0..nbins) into start[0..nbins] (start[nbins] = total);
+// tmp holds nbins / 4096 + 1 ints.
+cudaError_t launch_scan(erpp_ctx* ctx, const int32_t* cnt, int32_t* start, int32_t* tmp,
+                        int nbins, cudaStream_t st);
+// Other weights: orders the particles by 8 x 8 x 8-node block of their cell
+// (counting sort into ctx->w_perm), so that the gathers and the PIC source
+// walk the grid block by block.
+cudaError_t sort_by_cell_block(erpp_ctx* ctx, int64_t n, const double* const x[3],
+                               cudaStream_t st);
+cudaError_t launch_gather_weights(erpp_ctx* ctx, const void* u, int64_t n,
+                                  const double* const x[3], double* const up[3], cudaStream_t st);
+cudaError_t launch_scatter_pic(erpp_ctx* ctx, int64_t n, const double* const x[3],
+                               const double* const D[3], double fscale, void* S,
+                               cudaStream_t st);
 
 }  // namespace erpp
 

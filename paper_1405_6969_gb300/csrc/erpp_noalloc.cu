@@ -70,6 +70,7 @@ extern "C" erpp_status erpp_interpolate_noalloc(const erpp_params* params, const
                                                 double* const u_p[3], erpp_stream stream) {
   if (!params || !u) return ERPP_EINVAL;
   if ((params->flags & (ERPP_FP32 | ERPP_FP64)) != ERPP_FP32) return ERPP_EINVAL;
+  if (params->flags & (ERPP_PIC | ERPP_POINT_GATHER)) return ERPP_EINVAL;
   if (n < 0 || n > kNoallocParticles) return ERPP_EINVAL;
   if (n > 0 && (!x || !x[0] || !x[1] || !x[2] || !u_p || !u_p[0] || !u_p[1] || !u_p[2]))
     return ERPP_EINVAL;

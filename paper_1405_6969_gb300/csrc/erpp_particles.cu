@@ -295,8 +295,9 @@ __global__ void k_part_sum(erpp_kparams kp, int64_t n, const double* __restrict_
   double acc[3] = {0.0, 0.0, 0.0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double M = 1.0;
-    if (!kp.normalize) M = axis_mass(kp, 0, x0[i]) * axis_mass(kp, 1, x1[i]) * axis_mass(kp, 2, x2[i]);
+    double M = 1.0;  // trilinear (PIC) weights always carry unit mass
+    if (!kp.normalize && kp.weights != ERPP_W_PIC)
+      M = axis_mass(kp, 0, x0[i]) * axis_mass(kp, 1, x1[i]) * axis_mass(kp, 2, x2[i]);
     acc[0] += M * D0[i];
     acc[1] += M * D1[i];
     acc[2] += M * D2[i];

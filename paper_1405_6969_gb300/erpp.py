@@ -92,9 +92,18 @@ class ParticleState:
                                (self.x, self.v, self.x_prev, self.D, self.radius, self.rho_p)))
 
 
-def make_params(params, precision="fp32", normalize=True, self_removal=True, kahan=False):
+WEIGHTS = ("gaussian", "pic", "point")
+
+
+def make_params(params, precision="fp32", normalize=True, self_removal=True, kahan=False,
+                weights="gaussian"):
     """erpp_params from a parameter dict (n, L, nu, rho_f, eps_R, cutoff, dt,
-    gravity, shear_rate) and the option flags."""
+    gravity, shear_rate) and the option flags.  ``weights``: "gaussian" (the
+    regularised kernel and its matching gather), "pic" (trilinear projection
+    and interpolation, no self removal) or "point" (Gaussian source, 4-point
+    Lagrange point-value gather)."""
+    if weights not in WEIGHTS:
+        raise ValueError(f"weights must be one of {WEIGHTS}")
     p = _lib.Params()
     p.nx, p.ny, p.nz = (int(v) for v in params["n"])
     p.Lx, p.Ly, p.Lz = (float(v) for v in params["L"])
@@ -110,6 +119,10 @@ def make_params(params, precision="fp32", normalize=True, self_removal=True, kah
         flags |= _lib.SELF_REMOVAL
     if kahan:
         flags |= _lib.KAHAN
+    if weights == "pic":
+        flags |= _lib.PIC
+    elif weights == "point":
+        flags |= _lib.POINT_GATHER
     p.flags = flags
     return p
 
@@ -118,13 +131,19 @@ class Context:
     """One ERPP context (grid, parameters, scratch) on the current device.
 
     params: dict with n=(nx, ny, nz), L=(Lx, Ly, Lz), nu, rho_f, eps_R,
-    cutoff, dt, gravity=(gx, gy, gz), shear_rate.
+    cutoff, dt, gravity=(gx, gy, gz), shear_rate.  weights: "gaussian" (the
+    ERPP kernel), "pic" (trilinear particle-in-cell coupling, no self
+    removal) or "point" (Gaussian source, 4-point Lagrange point-value
+    gather); see make_params.
     """
 
     def __init__(self, params, precision="fp32", normalize=True, self_removal=True,
-                 kahan=False):
+                 kahan=False, weights="gaussian"):
         self.lib = _lib.load()
-        p = make_params(params, precision, normalize, self_removal, kahan)
+        if weights == "pic":
+            self_removal = False  # PIC has no closed-form self disturbance
+        p = make_params(params, precision, normalize, self_removal, kahan, weights)
+        self.weights = weights
         self.params = dict(params)
         self.precision = precision
         self.kahan = bool(kahan)

@@ -267,14 +267,15 @@ def test_imposed_motion_disturbance(erpp):
                                                   shift=eps + dt / 2)[0] / v_t)
             rs.append(abs(k * dx - xend))
             sing.append(V.imposed_motion_velocity(x, t_end, xp_of, D_of, NU, RHO)[0] / v_t
-                        if rs[-1] >= 6 * sig else np.nan)
+                        if rs[-1] >= 10 * sig else np.nan)
         num, regs, sing, rs = map(np.array, (num, regs, sing, rs))
         # the whole profile on the regularised solution
         assert np.abs(num - regs).max() < 0.02 * np.abs(regs).max(), (eps, num, regs)
-        # the far field on Eq. ref_velo_disturbance, whatever eps_R
-        far = rs >= 6 * sig
+        # the far field on Eq. ref_velo_disturbance, whatever eps_R (the
+        # regularised and singular solutions differ by 1.5% at 10 sigma_R)
+        far = rs >= 10 * sig
         assert far.sum() >= 4
-        assert np.all(np.abs(num[far] / sing[far] - 1.0) < 0.04), (eps, num[far], sing[far])
+        assert np.all(np.abs(num[far] / sing[far] - 1.0) < 0.025), (eps, num[far], sing[far])
         peak[eps] = np.abs(line).max() / v_t
     # eps_R sets the near field: the smaller width carries the larger peak
     assert peak[0.001] > 1.5 * peak[0.006], peak
