@@ -60,6 +60,10 @@ def parse():
                     help="skip the closed-loop (coupling + fluid stand-in) timing")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the timing of the PIC and point-value-gather steps")
+    ap.add_argument("--weights", default="gaussian", choices=["gaussian", "pic", "point"],
+                    help="time the step with other weights (pic: trilinear particle-in-cell; "
+                         "point: 4-point Lagrange point-value gather) instead of the ERPP "
+                         "kernel; the extra timings are then skipped")
     ap.add_argument("--workload", default="shear", choices=["shear", "cube256", "batched64"],
                     help="shear: 512x256x256 box (the benchmark); cube256: 256^3, 1M "
                          "particles (profiling case); batched64: 64 independent boxes "
@@ -369,9 +373,14 @@ def main():
     st = I.make_particles(w, None, seed=w.particle_seed + seed)
     u = torch.as_tensor(grid64, dtype=torch.float32).cuda().contiguous()
     ps = ParticleState.from_numpy(st)
-    ctx = Context(w.params(), precision="fp32", kahan=args.kahan)
+    ctx = Context(w.params(), precision="fp32", kahan=args.kahan, weights=args.weights)
     S = ctx.new_grid()
-    nodes_per_step = 2 * stencil_nodes(st.x, w)
+    if args.weights == "gaussian":
+        nodes_per_step = 2 * stencil_nodes(st.x, w)
+    else:
+        args.no_loop = args.no_e2e = args.no_cpu_baseline = args.no_variants = True
+        nodes_per_step = (16 * w.n_particles if args.weights == "pic"
+                          else 64 * w.n_particles + stencil_nodes(st.x, w))
     stream = torch.cuda.current_stream()
 
     # tile shape: time the candidates on this workload (a few steps each, on
@@ -381,7 +390,7 @@ def main():
         t = [int(v) for v in args.tiling.lower().split("x")] + [0]
         ctx.set_tiling(t[0], t[1], t[2])
         tiling = {"tile": tuple(t[:3]), "tiling": ctx.tiling(), "ms": None, "cached": False}
-    elif not args.no_autotune:
+    elif not args.no_autotune and args.weights != "pic":
         from paper_1405_6969_gb300 import autotune
         tiling = autotune.tune(ctx, u, ps, S=S, use_cache=False)
 
@@ -421,17 +430,20 @@ def main():
     ms_per_step = t_max / args.steps
     value = ws * nodes_per_step * args.steps / (t_max * 1e-3)
 
-    # roofline of the dominant kernel, timed live with CUDA events
+    # roofline of the dominant kernel, timed live with CUDA events (the
+    # per-phase events are recorded by the ERPP-kernel step only)
     names = ["bin", "gather", "advance", "scatter"]
     per = {nm: phase_ms[k] / max(nsteps, 1) for k, nm in enumerate(names)}
     alg = algorithmic_bytes(w, w.n_particles)
-    dom = max(("gather", "scatter"), key=lambda nm: per[nm])
     peak, peak_kind = measured_peaks()
-    achieved = alg[dom] / (per[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak,
-                "traffic": captured_traffic(w, dom, ctx.tiling()),
-                "peak_kind": peak_kind}
+    roofline = None
+    if nsteps > 0:
+        dom = max(("gather", "scatter"), key=lambda nm: per[nm])
+        achieved = alg[dom] / (per[dom] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": captured_traffic(w, dom, ctx.tiling()),
+                    "peak_kind": peak_kind}
     step_gbs = alg["step"] / (ms_per_step * 1e-3) / 1e9
 
     # the closed loop of the shear workload: coupling step, then the fluid
@@ -545,12 +557,12 @@ def main():
             "config": {"workload": w.name, "grid": list(w.n), "box": [round(v, 6) for v in w.L],
                        "particles_per_gpu": w.n_particles, "sigma_over_dx": w.sigma_over_dx,
                        "cutoff_sigmas": w.cutoff, "precision": "fp32",
-                       "kahan": bool(args.kahan),
+                       "kahan": bool(args.kahan), "weights": args.weights,
                        "l2": "inputs larger than L2: u and S 403 MB each, particles 112 MB",
                        "fluid": "held fixed during the timed steps"},
             "steps_per_s": 1e3 / ms_per_step,
             "node_updates_per_step": nodes_per_step,
-            "phase_ms": per,
+            "phase_ms": per if nsteps > 0 else None,
             "step_hbm": {"alg_bytes": alg["step"], "achieved_gbs": step_gbs,
                          "frac": step_gbs / peak},
             "roofline": roofline,

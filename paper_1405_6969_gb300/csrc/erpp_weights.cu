@@ -11,16 +11,17 @@
 // Cell of a particle, per axis: s = x * (N / L) rounded once, j0 = floor(s),
 // f = s - j0 (exact), node indices wrapped modulo N.
 //
-// An 8-node PIC stencil has nothing to stage: the PIC kernels run one thread
-// per particle straight on global memory, the scatter adding into the zeroed
-// grid with device atomics (red.global.add; FP32 sums depend on the order of
-// arrival).  The particles are first put in the order of the 8 x 8 x 8-node
-// block of their cell (a counting sort: count with returning atomics, scan,
-// fill), so that neighbouring threads touch neighbouring nodes and the grid
-// lines they share meet in L2 instead of being fetched from HBM per particle.  The weights are evaluated in the grid's type (the cell decision
-// in FP64).  The Lagrange gather gives each particle 16 lanes, one per
-// (y, z) row of 4 x-nodes, and sums the rows by shuffles: its 64 nodes are
-// read as 16 short row segments instead of 64 scattered words.
+// The particles are first put in the order of the 8 x 8 x 8-node block of
+// their cell (a counting sort: count with returning atomics, scan, fill), so
+// that neighbouring lanes touch neighbouring nodes and the grid lines they
+// share meet in L2 instead of being fetched from HBM per particle.  An 8-node
+// PIC stencil has nothing worth staging: the PIC kernels run straight on
+// global memory with two lanes per particle (one per x-neighbour), the source
+// adding into the zeroed grid with device atomics (red.global.add; FP32 sums
+// depend on the order of arrival).  The Lagrange gather gives each particle 4
+// lanes, one per x-column of its 4 x 4 x 4 stencil, summed by shuffles, so
+// that each row's 4 nodes are read by one warp instruction.  Weights are
+// evaluated in the grid's type (the cell decision in FP64).
 #include <cuda_runtime.h>
 
 #include "erpp_internal.cuh"
@@ -61,6 +62,9 @@ __device__ __forceinline__ T pick4(const T w[4], int k) {
   return k == 0 ? w[0] : k == 1 ? w[1] : k == 2 ? w[2] : w[3];
 }
 
+// PIC kernels: 2 lanes per particle, lane dx taking the nodes j0_x + dx, so
+// that the two x-neighbours of a row go out in one warp instruction (one
+// sector for both, where the row does not wrap).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_scatter_pic(
     erpp_kparams kp, int64_t n, const double* __restrict__ x0, const double* __restrict__ x1,
@@ -68,19 +72,23 @@ __global__ void __launch_bounds__(kThreads) k_scatter_pic(
     const double* __restrict__ D2, double coef, const int32_t* __restrict__ perm,
     T* __restrict__ S, uint32_t* err) {
   const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int dx = threadIdx.x & 1;
+  const int64_t stride = (int64_t)gridDim.x * (kThreads / 2);
+  for (int64_t i = (int64_t)blockIdx.x * (kThreads / 2) + (threadIdx.x >> 1); i < n;
+       i += stride) {
     const int64_t p = perm[i];
     int64_t j0[3];
     double f[3];
     if (!cell_axis(kp, 0, x0[p], &j0[0], &f[0]) || !cell_axis(kp, 1, x1[p], &j0[1], &f[1]) ||
         !cell_axis(kp, 2, x2[p], &j0[2], &f[2])) {
-      erpp_set_err(err, ERPP_ERRBIT_RANGE);
+      if (dx == 0) erpp_set_err(err, ERPP_ERRBIT_RANGE);
       continue;
     }
     // weights and products in the grid's type
     const T F[3] = {(T)(coef * D0[p]), (T)(coef * D1[p]), (T)(coef * D2[p])};
     const T fx = (T)f[0], fy = (T)f[1], fz = (T)f[2];
+    const T wx = dx ? fx : T(1) - fx;
+    const size_t jx = (size_t)(dx ? wrap_up(j0[0] + 1, kp.n[0]) : j0[0]);
 #pragma unroll
     for (int dz = 0; dz < 2; ++dz) {
       const T wz = dz ? fz : T(1) - fz;
@@ -89,16 +97,11 @@ __global__ void __launch_bounds__(kThreads) k_scatter_pic(
       for (int dy = 0; dy < 2; ++dy) {
         const T wy = dy ? fy : T(1) - fy;
         const size_t jy = (size_t)(dy ? wrap_up(j0[1] + 1, kp.n[1]) : j0[1]);
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-          const T wx = dx ? fx : T(1) - fx;
-          const size_t jx = (size_t)(dx ? wrap_up(j0[0] + 1, kp.n[0]) : j0[0]);
-          const T W = (wx * wy) * wz;
-          const size_t node = (jz * kp.n[1] + jy) * kp.n[0] + jx;
-          atomicAdd(S + node, F[0] * W);
-          atomicAdd(S + nn + node, F[1] * W);
-          atomicAdd(S + 2 * nn + node, F[2] * W);
-        }
+        const T W = (wx * wy) * wz;
+        const size_t node = (jz * kp.n[1] + jy) * kp.n[0] + jx;
+        atomicAdd(S + node, F[0] * W);
+        atomicAdd(S + nn + node, F[1] * W);
+        atomicAdd(S + 2 * nn + node, F[2] * W);
       }
     }
   }
@@ -111,61 +114,13 @@ __global__ void __launch_bounds__(kThreads) k_gather_pic(
     double* __restrict__ up0, double* __restrict__ up1, double* __restrict__ up2,
     uint32_t* err) {
   const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = perm[i];
-    const double xv[3] = {x0[p], x1[p], x2[p]};
-    int64_t j0[3];
-    double f[3];
-    T acc[3] = {T(0), T(0), T(0)};
-    if (cell_axis(kp, 0, xv[0], &j0[0], &f[0]) && cell_axis(kp, 1, xv[1], &j0[1], &f[1]) &&
-        cell_axis(kp, 2, xv[2], &j0[2], &f[2])) {
-      const T fx = (T)f[0], fy = (T)f[1], fz = (T)f[2];
-#pragma unroll
-      for (int dz = 0; dz < 2; ++dz) {
-        const T wz = dz ? fz : T(1) - fz;
-        const size_t jz = (size_t)(dz ? wrap_up(j0[2] + 1, kp.n[2]) : j0[2]);
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy) {
-          const T wy = dy ? fy : T(1) - fy;
-          const size_t jy = (size_t)(dy ? wrap_up(j0[1] + 1, kp.n[1]) : j0[1]);
-#pragma unroll
-          for (int dx = 0; dx < 2; ++dx) {
-            const T wx = dx ? fx : T(1) - fx;
-            const size_t jx = (size_t)(dx ? wrap_up(j0[0] + 1, kp.n[0]) : j0[0]);
-            const T W = (wx * wy) * wz;
-            const size_t node = (jz * kp.n[1] + jy) * kp.n[0] + jx;
-            acc[0] += W * u[node];
-            acc[1] += W * u[nn + node];
-            acc[2] += W * u[2 * nn + node];
-          }
-        }
-      }
-    } else {
-      erpp_set_err(err, ERPP_ERRBIT_RANGE);
-    }
-    up0[p] = (double)acc[0] + kp.shear_rate * xv[1];
-    up1[p] = (double)acc[1];
-    up2[p] = (double)acc[2];
-  }
-}
-
-// 16 lanes per particle: lane r of the group takes the row (ky, kz) = (r % 4,
-// r / 4) of the 4 x 4 x 4 Lagrange stencil.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_gather_point(
-    erpp_kparams kp, int64_t n, const double* __restrict__ x0, const double* __restrict__ x1,
-    const double* __restrict__ x2, const T* __restrict__ u, const int32_t* __restrict__ perm,
-    double* __restrict__ up0, double* __restrict__ up1, double* __restrict__ up2,
-    uint32_t* err) {
-  const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
-  const int r = threadIdx.x & 15;
-  const int64_t groups = (int64_t)gridDim.x * (kThreads / 16);
-  // every lane of a warp runs the same number of iterations (the shuffles
-  // below take the whole warp): the loop bound rounds n up to pairs
-  const int64_t n2 = (n + 1) & ~(int64_t)1;
-  for (int64_t i = (int64_t)blockIdx.x * (kThreads / 16) + (threadIdx.x >> 4); i < n2;
-       i += groups) {
+  const int dx = threadIdx.x & 1;
+  const int64_t stride = (int64_t)gridDim.x * (kThreads / 2);
+  // both lanes of a pair take every iteration (the shuffle below): the bound
+  // rounds n up to whole warps of pairs
+  const int64_t nr = (n + 15) & ~(int64_t)15;
+  for (int64_t i = (int64_t)blockIdx.x * (kThreads / 2) + (threadIdx.x >> 1); i < nr;
+       i += stride) {
     const bool live = i < n;
     const int64_t p = live ? perm[i] : 0;
     double xv[3] = {0.0, 0.0, 0.0};
@@ -178,7 +133,69 @@ __global__ void __launch_bounds__(kThreads) k_gather_point(
       xv[2] = x2[p];
       ok = cell_axis(kp, 0, xv[0], &j0[0], &f[0]) && cell_axis(kp, 1, xv[1], &j0[1], &f[1]) &&
            cell_axis(kp, 2, xv[2], &j0[2], &f[2]);
-      if (!ok && r == 0) erpp_set_err(err, ERPP_ERRBIT_RANGE);
+      if (!ok && dx == 0) erpp_set_err(err, ERPP_ERRBIT_RANGE);
+    }
+    T acc[3] = {T(0), T(0), T(0)};
+    if (ok) {
+      const T fx = (T)f[0], fy = (T)f[1], fz = (T)f[2];
+      const T wx = dx ? fx : T(1) - fx;
+      const size_t jx = (size_t)(dx ? wrap_up(j0[0] + 1, kp.n[0]) : j0[0]);
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz) {
+        const T wz = dz ? fz : T(1) - fz;
+        const size_t jz = (size_t)(dz ? wrap_up(j0[2] + 1, kp.n[2]) : j0[2]);
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const T wy = dy ? fy : T(1) - fy;
+          const size_t jy = (size_t)(dy ? wrap_up(j0[1] + 1, kp.n[1]) : j0[1]);
+          const T W = (wx * wy) * wz;
+          const size_t node = (jz * kp.n[1] + jy) * kp.n[0] + jx;
+          acc[0] += W * u[node];
+          acc[1] += W * u[nn + node];
+          acc[2] += W * u[2 * nn + node];
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
+    if (live && dx == 0) {
+      up0[p] = (double)acc[0] + kp.shear_rate * xv[1];
+      up1[p] = (double)acc[1];
+      up2[p] = (double)acc[2];
+    }
+  }
+}
+
+// Point-value gather: 4 lanes per particle, lane kx taking the node column
+// j0_x - 1 + kx of all 16 (y, z) rows of the 4 x 4 x 4 Lagrange stencil, so
+// that each row's 4 nodes go out in one warp instruction.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_gather_point(
+    erpp_kparams kp, int64_t n, const double* __restrict__ x0, const double* __restrict__ x1,
+    const double* __restrict__ x2, const T* __restrict__ u, const int32_t* __restrict__ perm,
+    double* __restrict__ up0, double* __restrict__ up1, double* __restrict__ up2,
+    uint32_t* err) {
+  const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
+  const int kx = threadIdx.x & 3;
+  const int64_t stride = (int64_t)gridDim.x * (kThreads / 4);
+  // every lane of a warp runs the same number of iterations (the shuffles
+  // below take the whole warp): the bound rounds n up to whole warps
+  const int64_t nr = (n + 7) & ~(int64_t)7;
+  for (int64_t i = (int64_t)blockIdx.x * (kThreads / 4) + (threadIdx.x >> 2); i < nr;
+       i += stride) {
+    const bool live = i < n;
+    const int64_t p = live ? perm[i] : 0;
+    double xv[3] = {0.0, 0.0, 0.0};
+    int64_t j0[3] = {0, 0, 0};
+    double f[3] = {0.0, 0.0, 0.0};
+    bool ok = false;
+    if (live) {
+      xv[0] = x0[p];
+      xv[1] = x1[p];
+      xv[2] = x2[p];
+      ok = cell_axis(kp, 0, xv[0], &j0[0], &f[0]) && cell_axis(kp, 1, xv[1], &j0[1], &f[1]) &&
+           cell_axis(kp, 2, xv[2], &j0[2], &f[2]);
+      if (!ok && kx == 0) erpp_set_err(err, ERPP_ERRBIT_RANGE);
     }
     T acc[3] = {T(0), T(0), T(0)};
     if (ok) {
@@ -186,24 +203,26 @@ __global__ void __launch_bounds__(kThreads) k_gather_point(
       lagrange4<T>((T)f[0], wx);
       lagrange4<T>((T)f[1], wy);
       lagrange4<T>((T)f[2], wz);
-      const int ky = r & 3, kz = r >> 2;
-      const size_t jz = (size_t)wrap_up(wrap_down(j0[2] - 1 + kz, kp.n[2]), kp.n[2]);
-      const size_t jy = (size_t)wrap_up(wrap_down(j0[1] - 1 + ky, kp.n[1]), kp.n[1]);
-      const size_t row = (jz * kp.n[1] + jy) * kp.n[0];
-      const T wyz = pick4<T>(wy, ky) * pick4<T>(wz, kz);
+      const T wxk = pick4<T>(wx, kx);
+      const size_t jx = (size_t)wrap_up(wrap_down(j0[0] - 1 + kx, kp.n[0]), kp.n[0]);
 #pragma unroll
-      for (int kx = 0; kx < 4; ++kx) {
-        const size_t node = row + (size_t)wrap_up(wrap_down(j0[0] - 1 + kx, kp.n[0]), kp.n[0]);
-        const T W = wx[kx] * wyz;
-        acc[0] += W * u[node];
-        acc[1] += W * u[nn + node];
-        acc[2] += W * u[2 * nn + node];
+      for (int kz = 0; kz < 4; ++kz) {
+        const size_t jz = (size_t)wrap_up(wrap_down(j0[2] - 1 + kz, kp.n[2]), kp.n[2]);
+#pragma unroll
+        for (int ky = 0; ky < 4; ++ky) {
+          const size_t jy = (size_t)wrap_up(wrap_down(j0[1] - 1 + ky, kp.n[1]), kp.n[1]);
+          const size_t node = (jz * kp.n[1] + jy) * kp.n[0] + jx;
+          const T W = wxk * (wy[ky] * wz[kz]);
+          acc[0] += W * u[node];
+          acc[1] += W * u[nn + node];
+          acc[2] += W * u[2 * nn + node];
+        }
       }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      for (int o = 8; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-    if (live && r == 0) {
+      for (int o = 2; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (live && kx == 0) {
       up0[p] = (double)acc[0] + kp.shear_rate * xv[1];
       up1[p] = (double)acc[1];
       up2[p] = (double)acc[2];
@@ -275,7 +294,7 @@ cudaError_t launch_gather_weights(erpp_ctx* ctx, const void* u, int64_t n,
   const erpp_kparams& kp = ctx->kp;
   ++ctx->launches;
   if (kp.weights == ERPP_W_PIC) {
-    const int b = blocks_for(n, kThreads);
+    const int b = blocks_for(n, kThreads / 2);
     if (ctx->fp64)
       k_gather_pic<double><<<b, kThreads, 0, st>>>(kp, n, x[0], x[1], x[2], (const double*)u,
                                                    ctx->w_perm, up[0], up[1], up[2], ctx->err);
@@ -283,7 +302,7 @@ cudaError_t launch_gather_weights(erpp_ctx* ctx, const void* u, int64_t n,
       k_gather_pic<float><<<b, kThreads, 0, st>>>(kp, n, x[0], x[1], x[2], (const float*)u,
                                                   ctx->w_perm, up[0], up[1], up[2], ctx->err);
   } else {
-    const int b = blocks_for(n, kThreads / 16);
+    const int b = blocks_for(n, kThreads / 4);
     if (ctx->fp64)
       k_gather_point<double><<<b, kThreads, 0, st>>>(kp, n, x[0], x[1], x[2],
                                                      (const double*)u, ctx->w_perm, up[0],
@@ -304,7 +323,7 @@ cudaError_t launch_scatter_pic(erpp_ctx* ctx, int64_t n, const double* const x[3
   cudaError_t e = cudaMemsetAsync(S, 0, elem * 3 * nn, st);
   if (e != cudaSuccess || n <= 0) return e;
   const double coef = fscale / kp.dV;
-  const int b = blocks_for(n, kThreads);
+  const int b = blocks_for(n, kThreads / 2);
   ++ctx->launches;
   if (ctx->fp64)
     k_scatter_pic<double><<<b, kThreads, 0, st>>>(kp, n, x[0], x[1], x[2], D[0], D[1], D[2], coef,
