@@ -64,6 +64,10 @@ def parse():
                     help="time the step with other weights (pic: trilinear particle-in-cell; "
                          "point: 4-point Lagrange point-value gather) instead of the ERPP "
                          "kernel; the extra timings are then skipped")
+    ap.add_argument("--lag", action="store_true",
+                    help="time the step with the source delayed by eps_R (ERPP_LAG: "
+                         "round(eps_R/dt) steps of positions and forces kept on the device); "
+                         "the extra timings are then skipped")
     ap.add_argument("--workload", default="shear", choices=["shear", "cube256", "batched64"],
                     help="shear: 512x256x256 box (the benchmark); cube256: 256^3, 1M "
                          "particles (profiling case); batched64: 64 independent boxes "
@@ -373,8 +377,11 @@ def main():
     st = I.make_particles(w, None, seed=w.particle_seed + seed)
     u = torch.as_tensor(grid64, dtype=torch.float32).cuda().contiguous()
     ps = ParticleState.from_numpy(st)
-    ctx = Context(w.params(), precision="fp32", kahan=args.kahan, weights=args.weights)
+    ctx = Context(w.params(), precision="fp32", kahan=args.kahan, weights=args.weights,
+                  lag=args.lag)
     S = ctx.new_grid()
+    if args.lag:
+        args.no_loop = args.no_e2e = args.no_cpu_baseline = args.no_variants = True
     if args.weights == "gaussian":
         nodes_per_step = 2 * stencil_nodes(st.x, w)
     else:
@@ -390,12 +397,19 @@ def main():
         t = [int(v) for v in args.tiling.lower().split("x")] + [0]
         ctx.set_tiling(t[0], t[1], t[2])
         tiling = {"tile": tuple(t[:3]), "tiling": ctx.tiling(), "ms": None, "cached": False}
+    elif args.lag:
+        # the first round(eps_R/dt) delayed steps have no source to time: keep
+        # the tile shape the autotuner picks for this workload without delay
+        ctx.set_tiling(16, 2, 256)
+        tiling = {"tile": (16, 2, 256), "tiling": ctx.tiling(), "ms": None, "cached": False}
     elif not args.no_autotune and args.weights != "pic":
         from paper_1405_6969_gb300 import autotune
         tiling = autotune.tune(ctx, u, ps, S=S, use_cache=False)
 
-    # warm-up (the first step has no previous force to remove)
-    for k in range(args.warmup):
+    # warm-up (the first step has no previous force to remove; with the delayed
+    # source, past the round(eps_R/dt) + 1 steps without source or removal)
+    warm = args.warmup + (max(1, round(w.eps_R / w.dt)) + 1 if args.lag else 0)
+    for k in range(warm):
         ctx.step(u, ps, S=S, first_step=(k == 0))
     ctx.check()
     torch.cuda.synchronize()
@@ -558,6 +572,7 @@ def main():
                        "particles_per_gpu": w.n_particles, "sigma_over_dx": w.sigma_over_dx,
                        "cutoff_sigmas": w.cutoff, "precision": "fp32",
                        "kahan": bool(args.kahan), "weights": args.weights,
+                       "lag_steps": (max(1, round(w.eps_R / w.dt)) if args.lag else 0),
                        "l2": "inputs larger than L2: u and S 403 MB each, particles 112 MB",
                        "fluid": "held fixed during the timed steps"},
             "steps_per_s": 1e3 / ms_per_step,

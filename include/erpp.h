@@ -67,9 +67,24 @@ enum {
                                   accumulation; costs a second shared array  */
   ERPP_PIC = 1u << 5,          /* classical particle-in-cell coupling instead
                                   of the regularised kernel (see below)      */
-  ERPP_POINT_GATHER = 1u << 6  /* point-value gather (see below); the source
+  ERPP_POINT_GATHER = 1u << 6, /* point-value gather (see below); the source
                                   stays the regularised kernel               */
+  ERPP_LAG = 1u << 7           /* delay the source by eps_R (see below)      */
 };
+
+/* ERPP_LAG: the literal time delay of Eq. ns_regularized_filtered.  The
+ * source of step n is D^(n-L) spread at x^(n-L), L = round(eps_R / dt) >= 1
+ * steps earlier, instead of the step's own D^n at x^n; the first L steps
+ * after a first_step have no source (S = 0).  The self disturbance removed
+ * at step n is that of the previous step's source, D^(n-1-L) at x^(n-1-L)
+ * (none while n < L + 1).  The context keeps the positions and forces of
+ * the last L + 1 steps (48 bytes per particle and step, (L + 1) * 48 bytes
+ * per particle in all).  Applies to erpp_step and erpp_step_host (the other
+ * calls work on what they are given); with the Gaussian weights only
+ * (ERPP_PIC / ERPP_POINT_GATHER: ERPP_EINVAL), not in the batched step
+ * (ERPP_EINVAL); dt must be positive; the particle count must not change
+ * between first steps, and after erpp_set_tiling the next step must be a
+ * first step (else ERPP_ESTATE). */
 
 /* Other weights on the same grid (the comparisons of Sec. 3.2.1-3.2.2 and the
  * interpolation question of Sec. 2.5).  At most one of the two flags.

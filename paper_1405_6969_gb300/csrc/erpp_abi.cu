@@ -53,6 +53,8 @@ void free_scratch(erpp_ctx* c) {
   cudaFree(c->w_slot);
   cudaFree(c->w_perm);
   c->w_key = c->w_slot = c->w_perm = nullptr;
+  cudaFree(c->lag_ring);
+  c->lag_ring = nullptr;
   c->geo_t = nullptr;
   c->geo_c = nullptr;
   c->xw = nullptr;
@@ -78,6 +80,8 @@ erpp_status ensure_capacity(erpp_ctx* c, int64_t n) {
   cudaError_t e = cudaSuccess;
   if (c->fp64 || c->kp.weights != ERPP_W_GAUSS)
     e = cudaMalloc(&c->up64, sizeof(double) * 3 * (size_t)cap);
+  if (c->kp.lag > 0 && e == cudaSuccess)
+    e = cudaMalloc(&c->lag_ring, sizeof(double) * 6 * (size_t)cap * (size_t)(c->kp.lag + 1));
   if (c->kp.weights != ERPP_W_GAUSS) {
     if (e == cudaSuccess) e = cudaMalloc(&c->w_key, sizeof(int32_t) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->w_slot, sizeof(int32_t) * (size_t)cap);
@@ -181,7 +185,10 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
   if (prec != ERPP_FP32 && prec != ERPP_FP64) return ERPP_EINVAL;
   if ((p->flags & ERPP_KAHAN) && prec != ERPP_FP32) return ERPP_EINVAL;
   if (p->flags & ~(uint32_t)(ERPP_FP32 | ERPP_FP64 | ERPP_NORMALIZE | ERPP_SELF_REMOVAL |
-                             ERPP_KAHAN | ERPP_PIC | ERPP_POINT_GATHER))
+                             ERPP_KAHAN | ERPP_PIC | ERPP_POINT_GATHER | ERPP_LAG))
+    return ERPP_EINVAL;
+  if ((p->flags & ERPP_LAG) && ((p->flags & (ERPP_PIC | ERPP_POINT_GATHER)) || !(p->dt > 0.0) ||
+                                !(p->eps_R / p->dt < 1.0e6)))
     return ERPP_EINVAL;
   if ((p->flags & ERPP_PIC) &&
       (p->flags & (ERPP_POINT_GATHER | ERPP_SELF_REMOVAL | ERPP_KAHAN)))
@@ -223,6 +230,7 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
   kp.shear_rate = p->shear_rate;
   kp.sig2 = sig2;
   kp.raw_norm3 = pow(2.0 * kPi * sig2, -1.5);
+  kp.lag = (p->flags & ERPP_LAG) ? std::max(1, (int)lround(p->eps_R / p->dt)) : 0;
   kp.weights = (p->flags & ERPP_PIC) ? ERPP_W_PIC
                : (p->flags & ERPP_POINT_GATHER) ? ERPP_W_POINT : ERPP_W_GAUSS;
   // The disturbance as the gather sees it: forcing diffused one step, plus the
@@ -435,6 +443,7 @@ erpp_status erpp_set_tiling(erpp_ctx* c, int32_t tile_y, int32_t tile_z, int32_t
   c->tile_req[0] = tile_y;
   c->tile_req[1] = tile_z;
   c->tile_req[2] = threads;
+  c->lag_n = -1;  // the delayed source's history went with the scratch: first_step next
   c->kp = probe.kp;
   for (int a = 0; a < 3; ++a) c->maxseg[a] = probe.maxseg[a];
   c->xw_len = probe.xw_len;
@@ -561,11 +570,82 @@ cudaError_t scatter_source(erpp_ctx* c, int64_t n, const double* const x[3],
   return e;
 }
 
+// The step with the source delayed by L = kp.lag steps (ERPP_LAG): ring slot
+// k mod (L + 1) holds (x^k, D^k).  At step n the advance removes the
+// disturbance of the source of step n - 1 (slot n - 1 - L), the source is
+// slot n - L (none while n < L), and (x^n, D^n) then go to slot n, the one the
+// removal has just read.
+erpp_status step_lagged(erpp_ctx* c, const void* u, const erpp_particles* P, void* S,
+                        int first_step, cudaStream_t st, cudaEvent_t after_advance) {
+  const int64_t n = P->n;
+  const int64_t L = c->kp.lag;
+  if (first_step) {
+    c->lag_step = 0;
+    c->lag_n = n;
+  } else if (n != c->lag_n) {
+    return ERPP_ESTATE;
+  }
+  const int64_t k = c->lag_step;
+  const size_t slot_len = (size_t)6 * (size_t)c->cap;
+  auto slot = [&](int64_t j) { return c->lag_ring + (size_t)(j % (L + 1)) * slot_len; };
+  auto xs_of = [&](double* b, const double* out[3]) {
+    for (int a = 0; a < 3; ++a) out[a] = b + (size_t)a * c->cap;
+  };
+  auto Ds_of = [&](double* b, const double* out[3]) {
+    for (int a = 0; a < 3; ++a) out[a] = b + (size_t)(3 + a) * c->cap;
+  };
+  const double* const xin[3] = {P->x[0], P->x[1], P->x[2]};
+  const double* const xprev[3] = {P->x_prev[0], P->x_prev[1], P->x_prev[2]};
+  const double* const Dv[3] = {P->D[0], P->D[1], P->D[2]};
+  const bool remove = k >= L + 1;
+  const double* xs[3] = {nullptr, nullptr, nullptr};
+  const double* Ds[3] = {nullptr, nullptr, nullptr};
+  if (remove) {
+    xs_of(slot(k - 1 - L), xs);
+    Ds_of(slot(k - 1 - L), Ds);
+  }
+  const int no_removal = remove ? 0 : 1;
+  cudaError_t e;
+  c->launches = 0;
+  if (c->fp64) {
+    double* up[3] = {c->up64, c->up64 + c->cap, c->up64 + 2 * c->cap};
+    e = erpp::launch_gather_f64(c, (const double*)u, n, xin, up, st);
+    const double* const upc[3] = {up[0], up[1], up[2]};
+    if (e == cudaSuccess)
+      e = erpp::launch_advance(c, P, upc, false, false, no_removal, st, remove ? xs : nullptr,
+                               remove ? Ds : nullptr);
+  } else {
+    e = erpp::bin_particles(c, n, xin, true, st);
+    if (e == cudaSuccess) e = erpp::launch_gather_f32(c, (const float*)u, n, st);
+    if (e == cudaSuccess)
+      e = erpp::launch_advance(c, P, nullptr, true, false, no_removal, st, remove ? xs : nullptr,
+                               remove ? Ds : nullptr);
+  }
+  if (e == cudaSuccess && after_advance) e = cudaEventRecord(after_advance, st);
+  if (e == cudaSuccess) {
+    if (k >= L) {
+      const double* xl[3];
+      const double* Dl[3];
+      xs_of(slot(k - L), xl);
+      Ds_of(slot(k - L), Dl);
+      e = erpp::scatter_source(c, n, xl, Dl, S, st);
+    } else {
+      const size_t nn = (size_t)c->kp.n[0] * c->kp.n[1] * c->kp.n[2];
+      e = cudaMemsetAsync(S, 0, 3 * nn * (c->fp64 ? sizeof(double) : sizeof(float)), st);
+    }
+  }
+  if (e == cudaSuccess) e = erpp::launch_lag_store(c, n, xprev, Dv, slot(k), st);
+  if (e == cudaSuccess) c->lag_step = k + 1;
+  c->last_step_launches = c->launches;
+  return set_cuda_err(e);
+}
+
 erpp_status step_device(erpp_ctx* c, const void* u, const erpp_particles* P, void* S,
                         int first_step, cudaStream_t st, cudaEvent_t after_advance) {
   const int64_t n = P->n;
   erpp_status s = erpp::ensure_capacity(c, n);
   if (s) return s;
+  if (c->kp.lag > 0) return step_lagged(c, u, P, S, first_step, st, after_advance);
   const double* const xin[3] = {P->x[0], P->x[1], P->x[2]};
   const double* const xprev[3] = {P->x_prev[0], P->x_prev[1], P->x_prev[2]};
   const double* const Dv[3] = {P->D[0], P->D[1], P->D[2]};

@@ -72,6 +72,7 @@ struct erpp_kparams {
   int64_t ystrip_off;    // design 4: offset (floats) of the y-strips in them
   int32_t normalize, self_removal, kahan;
   int32_t weights;   // ERPP_W_GAUSS, ERPP_W_PIC or ERPP_W_POINT
+  int32_t lag;       // ERPP_LAG: source delay in steps, round(eps_R / dt) >= 1; else 0
   double inv_dx[3];  // N / L
   double L[3];
   double cp[3];      // r_c / dx
@@ -122,6 +123,9 @@ struct erpp_ctx {
   int32_t* w_start;       // [w_nbins + 1]
   int32_t* w_tmp;         // scan chunk totals
   int w_nbins;
+  double* lag_ring;       // ERPP_LAG: [lag + 1][6][cap] positions and forces of past steps
+  int64_t lag_step;       // steps since the last first_step
+  int64_t lag_n;          // particle count of those steps
   int4* entries;
   int64_t entries_cap;
   float* halo;            // scatter x-halo columns, [ntiles][3][T_z][T_y][xhlo + xhhi]
@@ -169,8 +173,15 @@ cudaError_t launch_finalize_up(erpp_ctx* ctx, int64_t n, const double* const x[3
 // fscat_i = scale * norm_i * D_i (scale = -1/(rho_f dV) for the source).
 cudaError_t launch_prep_fscat(erpp_ctx* ctx, int64_t n, const double* const D[3], float scale,
                               cudaStream_t st);
+// xs, Ds (optional): position and force of the source whose disturbance is
+// removed, instead of P's x_prev and D.
 cudaError_t launch_advance(erpp_ctx* ctx, const erpp_particles* P, const double* const up[3],
-                           bool from_acc, bool write_fscat, int first_step, cudaStream_t st);
+                           bool from_acc, bool write_fscat, int first_step, cudaStream_t st,
+                           const double* const xs[3] = nullptr,
+                           const double* const Ds[3] = nullptr);
+// ring[slot] <- (x, D) for the delayed source (slot: six arrays of ctx->cap doubles).
+cudaError_t launch_lag_store(erpp_ctx* ctx, int64_t n, const double* const x[3],
+                             const double* const D[3], double* slot, cudaStream_t st);
 cudaError_t launch_gather_f64(erpp_ctx* ctx, const double* u, int64_t n,
                               const double* const x[3], double* const up[3], cudaStream_t st);
 cudaError_t launch_scatter_f64(erpp_ctx* ctx, int64_t n, const double* const x[3],

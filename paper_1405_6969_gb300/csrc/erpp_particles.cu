@@ -14,6 +14,10 @@ struct PartPtrs {
   double* D[3];
   const double* radius;
   const double* rho_p;
+  // position and force of the source whose disturbance is removed: x_prev and
+  // D (the previous step's) unless the source is delayed by eps_R
+  const double* xs[3];
+  const double* Ds[3];
 };
 
 struct UpPtrs {
@@ -140,11 +144,11 @@ __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, Par
     double r[3], D[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const double d = x[a] - P.xp[a][i];
+      const double d = x[a] - P.xs[a][i];
       // the exact minimum-image test only where the float difference is
       // near half the box
       r[a] = fabsf((float)d) > 0.99f * kp.halfL_f[a] ? min_image(d, kp.L[a]) : d;
-      D[a] = P.D[a][i];
+      D[a] = P.Ds[a][i];
     }
     if (F32) {
       float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
@@ -339,6 +343,8 @@ static PartPtrs part_ptrs(const erpp_particles* P) {
     q.v[a] = P->v[a];
     q.xp[a] = P->x_prev[a];
     q.D[a] = P->D[a];
+    q.xs[a] = P->x_prev[a];
+    q.Ds[a] = P->D[a];
   }
   q.radius = P->radius;
   q.rho_p = P->rho_p;
@@ -346,10 +352,16 @@ static PartPtrs part_ptrs(const erpp_particles* P) {
 }
 
 cudaError_t launch_advance(erpp_ctx* ctx, const erpp_particles* P, const double* const up[3],
-                           bool from_acc, bool write_fscat, int first_step, cudaStream_t st) {
+                           bool from_acc, bool write_fscat, int first_step, cudaStream_t st,
+                           const double* const xs[3], const double* const Ds[3]) {
   const int64_t n = P->n;
   if (n <= 0) return cudaSuccess;
   PartPtrs q = part_ptrs(P);
+  if (xs && Ds)
+    for (int a = 0; a < 3; ++a) {
+      q.xs[a] = xs[a];
+      q.Ds[a] = Ds[a];
+    }
   UpPtrs U;
   for (int a = 0; a < 3; ++a) U.up[a] = up ? up[a] : nullptr;
   int blocks = (int)((n + 255) / 256);
@@ -366,6 +378,32 @@ cudaError_t launch_advance(erpp_ctx* ctx, const erpp_particles* P, const double*
     k_advance<false, false><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, nullptr, 0, nullptr,
                                                     nullptr, nullptr, first_step);
   }
+  return cudaGetLastError();
+}
+
+// ring[slot] <- (x^n, D^n): six arrays of n doubles, [x0 x1 x2 D0 D1 D2].
+__global__ void k_lag_store(int64_t n, const double* __restrict__ x0, const double* __restrict__ x1,
+                            const double* __restrict__ x2, const double* __restrict__ D0,
+                            const double* __restrict__ D1, const double* __restrict__ D2,
+                            double* __restrict__ slot, int64_t stride) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    slot[i] = x0[i];
+    slot[stride + i] = x1[i];
+    slot[2 * stride + i] = x2[i];
+    slot[3 * stride + i] = D0[i];
+    slot[4 * stride + i] = D1[i];
+    slot[5 * stride + i] = D2[i];
+  }
+}
+
+cudaError_t launch_lag_store(erpp_ctx* ctx, int64_t n, const double* const x[3],
+                             const double* const D[3], double* slot, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  ++ctx->launches;
+  k_lag_store<<<(int)b, 256, 0, st>>>(n, x[0], x[1], x[2], D[0], D[1], D[2], slot, ctx->cap);
   return cudaGetLastError();
 }
 

@@ -96,12 +96,13 @@ WEIGHTS = ("gaussian", "pic", "point")
 
 
 def make_params(params, precision="fp32", normalize=True, self_removal=True, kahan=False,
-                weights="gaussian"):
+                weights="gaussian", lag=False):
     """erpp_params from a parameter dict (n, L, nu, rho_f, eps_R, cutoff, dt,
     gravity, shear_rate) and the option flags.  ``weights``: "gaussian" (the
     regularised kernel and its matching gather), "pic" (trilinear projection
     and interpolation, no self removal) or "point" (Gaussian source, 4-point
-    Lagrange point-value gather)."""
+    Lagrange point-value gather).  ``lag``: delay the source of erpp_step by
+    eps_R (round(eps_R / dt) steps, the literal Eq. ns_regularized_filtered)."""
     if weights not in WEIGHTS:
         raise ValueError(f"weights must be one of {WEIGHTS}")
     p = _lib.Params()
@@ -123,6 +124,8 @@ def make_params(params, precision="fp32", normalize=True, self_removal=True, kah
         flags |= _lib.PIC
     elif weights == "point":
         flags |= _lib.POINT_GATHER
+    if lag:
+        flags |= _lib.LAG
     p.flags = flags
     return p
 
@@ -134,15 +137,17 @@ class Context:
     cutoff, dt, gravity=(gx, gy, gz), shear_rate.  weights: "gaussian" (the
     ERPP kernel), "pic" (trilinear particle-in-cell coupling, no self
     removal) or "point" (Gaussian source, 4-point Lagrange point-value
-    gather); see make_params.
+    gather); see make_params.  lag: the source of step() is delayed by eps_R
+    (round(eps_R / dt) steps; the context keeps the positions and forces of
+    the steps in between).
     """
 
     def __init__(self, params, precision="fp32", normalize=True, self_removal=True,
-                 kahan=False, weights="gaussian"):
+                 kahan=False, weights="gaussian", lag=False):
         self.lib = _lib.load()
         if weights == "pic":
             self_removal = False  # PIC has no closed-form self disturbance
-        p = make_params(params, precision, normalize, self_removal, kahan, weights)
+        p = make_params(params, precision, normalize, self_removal, kahan, weights, lag)
         self.weights = weights
         self.params = dict(params)
         self.precision = precision
