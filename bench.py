@@ -435,6 +435,16 @@ def main():
     phase_ms, nsteps = ctx.profile_read()
     ctx.profile_enable(False)
     ctx.check()
+    # per-step times of 50 more steps, each between its own events: the median
+    # (the timed region above gives the mean)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(51)]
+    evs[0].record(stream)
+    for k in range(50):
+        ctx.step(u, ps, S=S)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms_median = statistics.median(evs[k].elapsed_time(evs[k + 1]) for k in range(50))
     elapsed_ms = e0.elapsed_time(e1)
     t_max = elapsed_ms
     if ws > 1:
@@ -576,6 +586,7 @@ def main():
                        "l2": "inputs larger than L2: u and S 403 MB each, particles 112 MB",
                        "fluid": "held fixed during the timed steps"},
             "steps_per_s": 1e3 / ms_per_step,
+            "ms_per_step_median_of_50": ms_median,
             "node_updates_per_step": nodes_per_step,
             "phase_ms": per if nsteps > 0 else None,
             "step_hbm": {"alg_bytes": alg["step"], "achieved_gbs": step_gbs,
