@@ -64,6 +64,10 @@ def parse():
                     help="time the step with other weights (pic: trilinear particle-in-cell; "
                          "point: 4-point Lagrange point-value gather) instead of the ERPP "
                          "kernel; the extra timings are then skipped")
+    ap.add_argument("--full-force", action="store_true",
+                    help="time the step with the general force of Eq. force_particle "
+                         "(ERPP_FULL_FORCE: Faxen, added mass, one-step Basset memory); the "
+                         "extra timings are then skipped")
     ap.add_argument("--lag", action="store_true",
                     help="time the step with the source delayed by eps_R (ERPP_LAG: "
                          "round(eps_R/dt) steps of positions and forces kept on the device); "
@@ -378,9 +382,9 @@ def main():
     u = torch.as_tensor(grid64, dtype=torch.float32).cuda().contiguous()
     ps = ParticleState.from_numpy(st)
     ctx = Context(w.params(), precision="fp32", kahan=args.kahan, weights=args.weights,
-                  lag=args.lag)
+                  lag=args.lag, full_force=args.full_force)
     S = ctx.new_grid()
-    if args.lag:
+    if args.lag or args.full_force:
         args.no_loop = args.no_e2e = args.no_cpu_baseline = args.no_variants = True
     if args.weights == "gaussian":
         nodes_per_step = 2 * stencil_nodes(st.x, w)
@@ -583,6 +587,7 @@ def main():
                        "cutoff_sigmas": w.cutoff, "precision": "fp32",
                        "kahan": bool(args.kahan), "weights": args.weights,
                        "lag_steps": (max(1, round(w.eps_R / w.dt)) if args.lag else 0),
+                       "force": "general (Eq. force_particle)" if args.full_force else "Stokes drag",
                        "l2": "inputs larger than L2: u and S 403 MB each, particles 112 MB",
                        "fluid": "held fixed during the timed steps"},
             "steps_per_s": 1e3 / ms_per_step,

@@ -69,8 +69,27 @@ enum {
                                   of the regularised kernel (see below)      */
   ERPP_POINT_GATHER = 1u << 6, /* point-value gather (see below); the source
                                   stays the regularised kernel               */
-  ERPP_LAG = 1u << 7           /* delay the source by eps_R (see below)      */
+  ERPP_LAG = 1u << 7,          /* delay the source by eps_R (see below)      */
+  ERPP_FULL_FORCE = 1u << 8    /* the general force of Eq. force_particle   */
 };
+
+/* ERPP_FULL_FORCE: erpp_step computes the general hydrodynamic force of
+ * Eq. force_particle instead of the Stokes drag: the Faxen terms (the
+ * Laplacian of the gathered velocity, with the Laplacian of the removed self
+ * disturbance, 2 d/ds2 of App. A.5's closed form), the fluid-acceleration and
+ * added-mass terms and the Basset memory over the last step (Sec. 2.5).
+ * With q = u~ + (a^2/6) lap u~, m_f = rho_f (4/3) pi a^3 and
+ * c_B = 12 mu a^2 sqrt(pi / (nu dt)):
+ *   F = 6 pi mu a (q - v) + m_f du~/dt + (m_f/2) d(u~ + (a^2/10) lap u~)/dt
+ *       + c_B dq,    (du~/dt etc. the change over the last step / dt)
+ *   [(m_p + m_f/2)/dt + c_B] (v' - v) = F + (m_p - m_f) g,
+ *   D = F - [(m_f/2)/dt + c_B] (v' - v)  (what the fluid receives, negated).
+ * The context keeps u~ and lap u~ of the previous step (48 bytes per
+ * particle); a first step takes no time derivatives.  Gaussian weights only,
+ * not with ERPP_LAG, not in the batched step (ERPP_EINVAL); dt must be
+ * positive; the particle count must not change between first steps, and
+ * after erpp_set_tiling the next step must be a first step (ERPP_ESTATE).
+ * Other calls (erpp_interpolate, erpp_particle_advance, ...) are unchanged. */
 
 /* ERPP_LAG: the literal time delay of Eq. ns_regularized_filtered.  The
  * source of step n is D^(n-L) spread at x^(n-L), L = round(eps_R / dt) >= 1

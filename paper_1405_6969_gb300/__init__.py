@@ -5,10 +5,10 @@ The computation lives in the CUDA library ``liberpp.so`` behind the C ABI of
 ``include/erpp.h``; this package is its PyTorch binding.
 """
 
-from ._lib import (FP32, FP64, KAHAN, LAG, NORMALIZE, PIC, POINT_GATHER,  # noqa: F401
-                   SELF_REMOVAL, ErppError, load)
+from ._lib import (FP32, FP64, FULL_FORCE, KAHAN, LAG, NORMALIZE, PIC,  # noqa: F401
+                   POINT_GATHER, SELF_REMOVAL, ErppError, load)
 from .erpp import (Batch, Context, Interpolate, ParticleState, ScatterSource,  # noqa: F401
                    StokesFluid)
 
 __all__ = ["Batch", "Context", "StokesFluid", "ParticleState", "ScatterSource", "Interpolate", "ErppError", "load",
-           "FP32", "FP64", "NORMALIZE", "SELF_REMOVAL", "KAHAN", "PIC", "POINT_GATHER", "LAG"]
+           "FP32", "FP64", "NORMALIZE", "SELF_REMOVAL", "KAHAN", "PIC", "POINT_GATHER", "LAG", "FULL_FORCE"]

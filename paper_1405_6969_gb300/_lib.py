@@ -24,6 +24,7 @@ KAHAN = 1 << 4
 PIC = 1 << 5
 POINT_GATHER = 1 << 6
 LAG = 1 << 7
+FULL_FORCE = 1 << 8
 
 STATUS = {0: "ERPP_OK", 1: "ERPP_EINVAL", 2: "ERPP_ENOMEM", 3: "ERPP_ECUDA",
           4: "ERPP_ERANGE", 5: "ERPP_EBOUNDS", 6: "ERPP_ETIMEOUT", 7: "ERPP_ESTATE"}

@@ -55,6 +55,9 @@ void free_scratch(erpp_ctx* c) {
   c->w_key = c->w_slot = c->w_perm = nullptr;
   cudaFree(c->lag_ring);
   c->lag_ring = nullptr;
+  cudaFree(c->ff_lap);
+  cudaFree(c->ff_prev);
+  c->ff_lap = c->ff_prev = nullptr;
   c->geo_t = nullptr;
   c->geo_c = nullptr;
   c->xw = nullptr;
@@ -80,9 +83,14 @@ erpp_status ensure_capacity(erpp_ctx* c, int64_t n) {
   cudaError_t e = cudaSuccess;
   if (c->fp64 || c->kp.weights != ERPP_W_GAUSS)
     e = cudaMalloc(&c->up64, sizeof(double) * 3 * (size_t)cap);
+  if (c->kp.full_force && e == cudaSuccess) {
+    e = cudaMalloc(&c->ff_lap, sizeof(double) * 3 * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc(&c->ff_prev, sizeof(double) * 6 * (size_t)cap);
+    if (e == cudaSuccess && !c->up64) e = cudaMalloc(&c->up64, sizeof(double) * 3 * (size_t)cap);
+  }
   if (c->kp.lag > 0 && e == cudaSuccess)
     e = cudaMalloc(&c->lag_ring, sizeof(double) * 6 * (size_t)cap * (size_t)(c->kp.lag + 1));
-  if (c->kp.weights != ERPP_W_GAUSS) {
+  if (c->kp.weights != ERPP_W_GAUSS || (c->kp.full_force && !c->fp64)) {
     if (e == cudaSuccess) e = cudaMalloc(&c->w_key, sizeof(int32_t) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->w_slot, sizeof(int32_t) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->w_perm, sizeof(int32_t) * (size_t)cap);
@@ -128,7 +136,7 @@ erpp_status alloc_tile_tables(erpp_ctx* c) {
 // Cell-block tables of the other weights' particle sort (8 x 8 x 8-node blocks
 // plus one bin for invalid positions).
 erpp_status alloc_weight_tables(erpp_ctx* c) {
-  if (c->kp.weights == ERPP_W_GAUSS) return ERPP_OK;
+  if (c->kp.weights == ERPP_W_GAUSS && !(c->kp.full_force && !c->fp64)) return ERPP_OK;
   const erpp_kparams& kp = c->kp;
   int64_t nb = 1;
   for (int a = 0; a < 3; ++a) nb *= (kp.n[a] + 7) / 8;
@@ -185,10 +193,14 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
   if (prec != ERPP_FP32 && prec != ERPP_FP64) return ERPP_EINVAL;
   if ((p->flags & ERPP_KAHAN) && prec != ERPP_FP32) return ERPP_EINVAL;
   if (p->flags & ~(uint32_t)(ERPP_FP32 | ERPP_FP64 | ERPP_NORMALIZE | ERPP_SELF_REMOVAL |
-                             ERPP_KAHAN | ERPP_PIC | ERPP_POINT_GATHER | ERPP_LAG))
+                             ERPP_KAHAN | ERPP_PIC | ERPP_POINT_GATHER | ERPP_LAG |
+                             ERPP_FULL_FORCE))
     return ERPP_EINVAL;
   if ((p->flags & ERPP_LAG) && ((p->flags & (ERPP_PIC | ERPP_POINT_GATHER)) || !(p->dt > 0.0) ||
                                 !(p->eps_R / p->dt < 1.0e6)))
+    return ERPP_EINVAL;
+  if ((p->flags & ERPP_FULL_FORCE) &&
+      ((p->flags & (ERPP_PIC | ERPP_POINT_GATHER | ERPP_LAG)) || !(p->dt > 0.0)))
     return ERPP_EINVAL;
   if ((p->flags & ERPP_PIC) &&
       (p->flags & (ERPP_POINT_GATHER | ERPP_SELF_REMOVAL | ERPP_KAHAN)))
@@ -231,13 +243,17 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
   kp.sig2 = sig2;
   kp.raw_norm3 = pow(2.0 * kPi * sig2, -1.5);
   kp.lag = (p->flags & ERPP_LAG) ? std::max(1, (int)lround(p->eps_R / p->dt)) : 0;
+  kp.full_force = (p->flags & ERPP_FULL_FORCE) ? 1 : 0;
   kp.weights = (p->flags & ERPP_PIC) ? ERPP_W_PIC
                : (p->flags & ERPP_POINT_GATHER) ? ERPP_W_POINT : ERPP_W_GAUSS;
   // The disturbance as the gather sees it: forcing diffused one step, plus the
   // matching kernel's own sigma_R^2 (none for a point-value gather).
   kp.self_s2 = (2.0 * p->nu) * (p->eps_R + p->dt) +
                (kp.weights == ERPP_W_POINT ? 0.0 : (2.0 * p->nu) * p->eps_R);
-  kp.self_pref = (float)(-(p->dt / p->rho_f) / pow(2.0 * kPi * kp.self_s2, 1.5));
+  kp.self_pref64 = -(p->dt / p->rho_f) / pow(2.0 * kPi * kp.self_s2, 1.5);
+  kp.self_pref = (float)kp.self_pref64;
+  kp.raw_norm1 = 1.0 / sqrt(2.0 * kPi * sig2);
+  kp.basset_c = p->dt > 0.0 ? 12.0 * (p->rho_f * p->nu) * sqrt(kPi / (p->nu * p->dt)) : 0.0;
   kp.self_inv_w = (float)(1.0 / sqrt(2.0 * kp.self_s2));
   kp.drag_f = (float)(6.0 * kPi * kp.mu);
   kp.rho_f_f = (float)p->rho_f;
@@ -385,6 +401,8 @@ erpp_status erpp_init(const erpp_params* p, erpp_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&c->red, sizeof(double) * (6 * 304 + 8));
+  c->lag_n = -1;  // the delayed source and the general force start with a first step
+  c->ff_n = -1;
   erpp_status st = set_cuda_err(e);
   if (st == ERPP_OK) st = alloc_tile_tables(c);
   if (st == ERPP_OK) st = alloc_weight_tables(c);
@@ -444,6 +462,7 @@ erpp_status erpp_set_tiling(erpp_ctx* c, int32_t tile_y, int32_t tile_z, int32_t
   c->tile_req[1] = tile_z;
   c->tile_req[2] = threads;
   c->lag_n = -1;  // the delayed source's history went with the scratch: first_step next
+  c->ff_n = -1;
   c->kp = probe.kp;
   for (int a = 0; a < 3; ++a) c->maxseg[a] = probe.maxseg[a];
   c->xw_len = probe.xw_len;
@@ -640,12 +659,36 @@ erpp_status step_lagged(erpp_ctx* c, const void* u, const erpp_particles* P, voi
   return set_cuda_err(e);
 }
 
+// The step with the general force (ERPP_FULL_FORCE): gather of the velocity and
+// its Laplacian, the general-force advance, the source of D^n at x^n.
+erpp_status step_full_force(erpp_ctx* c, const void* u, const erpp_particles* P, void* S,
+                            int first_step, cudaStream_t st, cudaEvent_t after_advance) {
+  const int64_t n = P->n;
+  if (first_step)
+    c->ff_n = n;
+  else if (n != c->ff_n)
+    return ERPP_ESTATE;
+  const double* const xin[3] = {P->x[0], P->x[1], P->x[2]};
+  const double* const xprev[3] = {P->x_prev[0], P->x_prev[1], P->x_prev[2]};
+  const double* const Dv[3] = {P->D[0], P->D[1], P->D[2]};
+  double* up[3] = {c->up64, c->up64 + c->cap, c->up64 + 2 * c->cap};
+  const double* const upc[3] = {up[0], up[1], up[2]};
+  c->launches = 0;
+  cudaError_t e = erpp::launch_gather_faxen(c, u, n, xin, up, st);
+  if (e == cudaSuccess) e = erpp::launch_advance_full(c, P, upc, first_step, st);
+  if (e == cudaSuccess && after_advance) e = cudaEventRecord(after_advance, st);
+  if (e == cudaSuccess) e = erpp::scatter_source(c, n, xprev, Dv, S, st);
+  c->last_step_launches = c->launches;
+  return set_cuda_err(e);
+}
+
 erpp_status step_device(erpp_ctx* c, const void* u, const erpp_particles* P, void* S,
                         int first_step, cudaStream_t st, cudaEvent_t after_advance) {
   const int64_t n = P->n;
   erpp_status s = erpp::ensure_capacity(c, n);
   if (s) return s;
   if (c->kp.lag > 0) return step_lagged(c, u, P, S, first_step, st, after_advance);
+  if (c->kp.full_force) return step_full_force(c, u, P, S, first_step, st, after_advance);
   const double* const xin[3] = {P->x[0], P->x[1], P->x[2]};
   const double* const xprev[3] = {P->x_prev[0], P->x_prev[1], P->x_prev[2]};
   const double* const Dv[3] = {P->D[0], P->D[1], P->D[2]};

@@ -108,7 +108,8 @@ erpp_status erpp_batch_init(int32_t nbox, const erpp_box_desc* boxes, erpp_batch
     const erpp_box_desc& d = boxes[i];
     const erpp_particles& P = d.particles;
     if (!d.u || !d.S || P.n < 0 || P.n > ERPP_MAX_PARTICLES) return ERPP_EINVAL;
-    if (d.params.flags & (ERPP_PIC | ERPP_POINT_GATHER | ERPP_LAG)) return ERPP_EINVAL;
+    if (d.params.flags & (ERPP_PIC | ERPP_POINT_GATHER | ERPP_LAG | ERPP_FULL_FORCE))
+      return ERPP_EINVAL;
     if (P.n > 0) {
       if (!P.radius || !P.rho_p) return ERPP_EINVAL;
       for (int a = 0; a < 3; ++a)

@@ -73,6 +73,7 @@ struct erpp_kparams {
   int32_t normalize, self_removal, kahan;
   int32_t weights;   // ERPP_W_GAUSS, ERPP_W_PIC or ERPP_W_POINT
   int32_t lag;       // ERPP_LAG: source delay in steps, round(eps_R / dt) >= 1; else 0
+  int32_t full_force;// ERPP_FULL_FORCE
   double inv_dx[3];  // N / L
   double L[3];
   double cp[3];      // r_c / dx
@@ -82,6 +83,9 @@ struct erpp_kparams {
   double gravity[3];
   double shear_rate;
   double raw_norm3;  // (2 pi sigma_R^2)^(-3/2)
+  double raw_norm1;  // (2 pi sigma_R^2)^(-1/2)
+  double self_pref64;// -(dt/rho_f) (2 pi self_s2)^(-3/2)
+  double basset_c;   // 12 mu sqrt(pi / (nu dt)) (ERPP_FULL_FORCE; 0 when dt = 0)
   double sig2;       // sigma_R^2
   double self_s2;    // variance of the self disturbance as gathered
   float beta[3];     // log2(e) dx_a^2 / (2 sigma_R^2)
@@ -126,6 +130,9 @@ struct erpp_ctx {
   double* lag_ring;       // ERPP_LAG: [lag + 1][6][cap] positions and forces of past steps
   int64_t lag_step;       // steps since the last first_step
   int64_t lag_n;          // particle count of those steps
+  double* ff_lap;         // ERPP_FULL_FORCE: gathered Laplacian [3][cap]
+  double* ff_prev;        // ERPP_FULL_FORCE: u~ and lap u~ of the previous step [6][cap]
+  int64_t ff_n;           // particle count since the last first step (-1: none)
   int4* entries;
   int64_t entries_cap;
   float* halo;            // scatter x-halo columns, [ntiles][3][T_z][T_y][xhlo + xhhi]
@@ -179,6 +186,13 @@ cudaError_t launch_advance(erpp_ctx* ctx, const erpp_particles* P, const double*
                            bool from_acc, bool write_fscat, int first_step, cudaStream_t st,
                            const double* const xs[3] = nullptr,
                            const double* const Ds[3] = nullptr);
+// ERPP_FULL_FORCE: gathered velocity (plus the mean shear) and its Laplacian in
+// the particle position, into up and ctx->ff_lap; then the general-force
+// advance from them (ctx->ff_prev holds u~ and lap u~ of the previous step).
+cudaError_t launch_gather_faxen(erpp_ctx* ctx, const void* u, int64_t n,
+                                const double* const x[3], double* const up[3], cudaStream_t st);
+cudaError_t launch_advance_full(erpp_ctx* ctx, const erpp_particles* P,
+                                const double* const up[3], int first_step, cudaStream_t st);
 // ring[slot] <- (x, D) for the delayed source (slot: six arrays of ctx->cap doubles).
 cudaError_t launch_lag_store(erpp_ctx* ctx, int64_t n, const double* const x[3],
                              const double* const D[3], double* slot, cudaStream_t st);

@@ -79,7 +79,7 @@ __device__ void self_velocity_f64(const erpp_kparams& kp, const double r[3], con
                                   double out[3]) {
   const double pi = 3.141592653589793238462643;
   double s2 = kp.self_s2;
-  double pref = -(kp.dt / kp.rho_f) / pow(2.0 * pi * s2, 1.5);
+  double pref = kp.self_pref64;
   double rr = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
   double eta = rr / sqrt(2.0 * s2);
   double F;
@@ -102,6 +102,176 @@ __device__ void self_velocity_f64(const erpp_kparams& kp, const double r[3], con
     Ddr = D[0] * rh[0] + D[1] * rh[1] + D[2] * rh[2];
   }
   for (int a = 0; a < 3; ++a) out[a] = pref * ((e - F) * D[a] - Ddr * (e - 3.0 * F) * rh[a]);
+}
+
+// Laplacian in r of the disturbance above: the disturbance is the Leray
+// projection of a Gaussian of variance s2, and d g/d s2 = (1/2) lap g, so
+// lap v = 2 dv/ds2 at fixed dt/rho_f.  With v = pref(s2) B(eta),
+// pref ~ s2^(-3/2), eta = r / sqrt(2 s2):  lap v = -(pref / s2)(3 B + eta dB/deta),
+// dB/deta = [e' - F'] D - (D.rh)[e' - 3 F'] rh, e' = -2 eta e^-eta^2,
+// F' = e^-eta^2 / eta - 3 F / eta (series below eta = 1/2).
+__device__ void self_laplacian_f64(const erpp_kparams& kp, const double r[3], const double D[3],
+                                   double out[3]) {
+  const double pi = 3.141592653589793238462643;
+  const double s2 = kp.self_s2;
+  const double pref = kp.self_pref64;
+  const double rr = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  const double eta = rr / sqrt(2.0 * s2);
+  const double e = exp(-eta * eta);
+  double F, dF;
+  if (eta < 0.5) {
+    double e2 = eta * eta, term = 1.0, sum = 0.0, dsum = 0.0;
+    for (int k = 0; k < 20; ++k) {
+      sum += term / (double)(2 * k + 3);
+      dsum += (double)(2 * k) * term / (double)(2 * k + 3);
+      term = -term * e2 / (double)(k + 1);
+    }
+    F = sum;
+    dF = eta > 0.0 ? dsum / eta : 0.0;
+  } else {
+    const double f = 0.5 * sqrt(pi) * erf(eta) - eta * e;
+    F = f / (2.0 * eta * eta * eta);
+    dF = e / eta - 3.0 * F / eta;
+  }
+  const double de = -2.0 * eta * e;
+  double rh[3] = {0.0, 0.0, 0.0};
+  double Ddr = 0.0;
+  if (rr > 0.0) {
+    for (int a = 0; a < 3; ++a) rh[a] = r[a] / rr;
+    Ddr = D[0] * rh[0] + D[1] * rh[1] + D[2] * rh[2];
+  }
+  for (int a = 0; a < 3; ++a) {
+    const double B = (e - F) * D[a] - Ddr * (e - 3.0 * F) * rh[a];
+    const double dB = (de - dF) * D[a] - Ddr * (de - 3.0 * dF) * rh[a];
+    out[a] = -(pref / s2) * (3.0 * B + eta * dB);
+  }
+}
+
+// The same in FP32 (the closed forms of the FP32 step): series below eta = 1/2.
+__device__ void self_laplacian_f32(const erpp_kparams& kp, const float r[3], const float D[3],
+                                   float out[3]) {
+  const float rr = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  const float eta = rr * kp.self_inv_w;
+  const float e = expf(-eta * eta);
+  float F, dF;
+  if (eta < 0.5f) {
+    float e2 = eta * eta, term = 1.f, sum = 0.f, dsum = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      sum += term / (float)(2 * k + 3);
+      dsum += (float)(2 * k) * term / (float)(2 * k + 3);
+      term = -term * e2 / (float)(k + 1);
+    }
+    F = sum;
+    dF = eta > 0.f ? dsum / eta : 0.f;
+  } else {
+    const float f = 0.886226925452758f * erff(eta) - eta * e;
+    F = f / (2.f * eta * eta * eta);
+    dF = e / eta - 3.f * F / eta;
+  }
+  const float de = -2.f * eta * e;
+  float rh[3] = {0.f, 0.f, 0.f};
+  float Ddr = 0.f;
+  if (rr > 0.f) {
+    const float inv = 1.f / rr;
+    for (int a = 0; a < 3; ++a) rh[a] = r[a] * inv;
+    Ddr = D[0] * rh[0] + D[1] * rh[1] + D[2] * rh[2];
+  }
+  const float c = -kp.self_pref / (float)kp.self_s2;
+  for (int a = 0; a < 3; ++a) {
+    const float B = (e - F) * D[a] - Ddr * (e - 3.f * F) * rh[a];
+    const float dB = (de - dF) * D[a] - Ddr * (de - 3.f * dF) * rh[a];
+    out[a] = c * (3.f * B + eta * dB);
+  }
+}
+
+// The general force of Eq. force_particle (ERPP_FULL_FORCE), one thread per
+// particle in FP64: self removal of the velocity and of its Laplacian, Faxen
+// slip q - v (q = u~ + (a^2/6) lap u~), fluid-acceleration and added-mass
+// terms from the change of u~ over the last step (prev: u~ and lap u~ of the
+// previous step, [6][stride]; none on a first step), one-step Basset memory
+// c_B (q - q_prev), the particle's own added mass and memory at the step's
+// velocity change, Euler update.
+// F32: the closed forms of the removed disturbance in FP32 (as in the FP32
+// Stokes-drag step); the force terms and the update in FP64.
+template <bool F32>
+__global__ void __launch_bounds__(256) k_advance_full(erpp_kparams kp, int64_t n, PartPtrs P,
+                                                      UpPtrs U, const double* __restrict__ lap,
+                                                      double* __restrict__ prev, int64_t stride,
+                                                      int first_step) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double pi = 3.141592653589793238462643;
+  double x[3], v[3], ut[3], Lt[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    x[a] = P.x[a][i];
+    v[a] = P.v[a][i];
+    ut[a] = U.up[a][i];
+    Lt[a] = lap[a * stride + i];
+  }
+  if (kp.self_removal && !first_step) {
+    double r[3], D[3], vs[3], ls[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      r[a] = min_image(x[a] - P.xp[a][i], kp.L[a]);
+      D[a] = P.D[a][i];
+    }
+    if (F32) {
+      const float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
+      const float Df[3] = {(float)D[0], (float)D[1], (float)D[2]};
+      float vf[3], lf[3];
+      self_velocity_f32(kp, rf, Df, vf);
+      self_laplacian_f32(kp, rf, Df, lf);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        vs[a] = (double)vf[a];
+        ls[a] = (double)lf[a];
+      }
+    } else {
+      self_velocity_f64(kp, r, D, vs);
+      self_laplacian_f64(kp, r, D, ls);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      ut[a] -= vs[a];
+      Lt[a] -= ls[a];
+    }
+  }
+  double up_prev[3], Lp_prev[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    up_prev[a] = first_step ? ut[a] : prev[a * stride + i];
+    Lp_prev[a] = first_step ? Lt[a] : prev[(3 + a) * stride + i];
+  }
+  const double a_p = P.radius[i];
+  const double a2 = a_p * a_p;
+  const double vol = (4.0 / 3.0) * pi * a_p * a2;
+  const double m_p = vol * P.rho_p[i];
+  const double m_f = vol * kp.rho_f;
+  const double dt = kp.dt;
+  const double c_B = kp.basset_c * a2;
+  const double k_drag = 6.0 * pi * kp.mu * a_p;
+  // one division per particle: the FP64 divide is slow on this part
+  const double mf_dt = m_f / dt;
+  const double inv_M = 1.0 / (m_p / dt + 0.5 * mf_dt + c_B);
+  const double c_D = 0.5 * mf_dt + c_B;
+  const double a2_6 = a2 * (1.0 / 6.0), a2_10 = a2 * 0.1;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double q = ut[a] + a2_6 * Lt[a];
+    const double q_prev = up_prev[a] + a2_6 * Lp_prev[a];
+    const double F = k_drag * (q - v[a]) + mf_dt * (ut[a] - up_prev[a]) +
+                     0.5 * mf_dt * ((ut[a] + a2_10 * Lt[a]) - (up_prev[a] + a2_10 * Lp_prev[a])) +
+                     c_B * (q - q_prev);
+    const double dv = (F + (m_p - m_f) * kp.gravity[a]) * inv_M;
+    P.D[a][i] = F - c_D * dv;
+    P.v[a][i] = v[a] + dv;
+    P.x[a][i] = wrap_coord(x[a] + dt * v[a], kp.L[a]);
+    P.xp[a][i] = x[a];
+    prev[a * stride + i] = ut[a];
+    prev[(3 + a) * stride + i] = Lt[a];
+  }
 }
 
 // Removal + drag + Euler (Sec. 2.5, Eqs. particle_motion, force_stokes_drag).
@@ -378,6 +548,24 @@ cudaError_t launch_advance(erpp_ctx* ctx, const erpp_particles* P, const double*
     k_advance<false, false><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, nullptr, 0, nullptr,
                                                     nullptr, nullptr, first_step);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_full(erpp_ctx* ctx, const erpp_particles* P,
+                                const double* const up[3], int first_step, cudaStream_t st) {
+  const int64_t n = P->n;
+  if (n <= 0) return cudaSuccess;
+  PartPtrs q = part_ptrs(P);
+  UpPtrs U;
+  for (int a = 0; a < 3; ++a) U.up[a] = up[a];
+  ++ctx->launches;
+  const int blocks = (int)((n + 255) / 256);
+  if (ctx->fp64)
+    k_advance_full<false><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, ctx->ff_lap, ctx->ff_prev,
+                                                  ctx->cap, first_step);
+  else
+    k_advance_full<true><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, ctx->ff_lap, ctx->ff_prev,
+                                                 ctx->cap, first_step);
   return cudaGetLastError();
 }
 

@@ -96,13 +96,15 @@ WEIGHTS = ("gaussian", "pic", "point")
 
 
 def make_params(params, precision="fp32", normalize=True, self_removal=True, kahan=False,
-                weights="gaussian", lag=False):
+                weights="gaussian", lag=False, full_force=False):
     """erpp_params from a parameter dict (n, L, nu, rho_f, eps_R, cutoff, dt,
     gravity, shear_rate) and the option flags.  ``weights``: "gaussian" (the
     regularised kernel and its matching gather), "pic" (trilinear projection
     and interpolation, no self removal) or "point" (Gaussian source, 4-point
     Lagrange point-value gather).  ``lag``: delay the source of erpp_step by
-    eps_R (round(eps_R / dt) steps, the literal Eq. ns_regularized_filtered)."""
+    eps_R (round(eps_R / dt) steps, the literal Eq. ns_regularized_filtered).
+    ``full_force``: the general force of Eq. force_particle (Faxen, added mass,
+    one-step Basset memory) instead of the Stokes drag."""
     if weights not in WEIGHTS:
         raise ValueError(f"weights must be one of {WEIGHTS}")
     p = _lib.Params()
@@ -126,6 +128,8 @@ def make_params(params, precision="fp32", normalize=True, self_removal=True, kah
         flags |= _lib.POINT_GATHER
     if lag:
         flags |= _lib.LAG
+    if full_force:
+        flags |= _lib.FULL_FORCE
     p.flags = flags
     return p
 
@@ -139,15 +143,17 @@ class Context:
     removal) or "point" (Gaussian source, 4-point Lagrange point-value
     gather); see make_params.  lag: the source of step() is delayed by eps_R
     (round(eps_R / dt) steps; the context keeps the positions and forces of
-    the steps in between).
+    the steps in between).  full_force: step() with the general force of
+    Eq. force_particle (Faxen, added mass, one-step Basset memory).
     """
 
     def __init__(self, params, precision="fp32", normalize=True, self_removal=True,
-                 kahan=False, weights="gaussian", lag=False):
+                 kahan=False, weights="gaussian", lag=False, full_force=False):
         self.lib = _lib.load()
         if weights == "pic":
             self_removal = False  # PIC has no closed-form self disturbance
-        p = make_params(params, precision, normalize, self_removal, kahan, weights, lag)
+        p = make_params(params, precision, normalize, self_removal, kahan, weights, lag,
+                        full_force)
         self.weights = weights
         self.params = dict(params)
         self.precision = precision

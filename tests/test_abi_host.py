@@ -42,9 +42,10 @@ def _params(lib, **kw):
 
 @pytest.mark.parametrize("bad", [
     dict(nx=0), dict(Lx=-1.0), dict(nu=0.0), dict(eps_R=float("nan")), dict(cutoff=0.0),
-    dict(cutoff=40.0), dict(flags=0), dict(flags=3), dict(flags=2 | 16), dict(flags=1 | 256),
+    dict(cutoff=40.0), dict(flags=0), dict(flags=3), dict(flags=2 | 16), dict(flags=1 | 512),
     dict(flags=1 | 8 | 32), dict(flags=1 | 32 | 64), dict(flags=1 | 16 | 32),
     dict(flags=1 | 32 | 128), dict(flags=1 | 64 | 128), dict(flags=1 | 128, dt=0.0),
+    dict(flags=1 | 128 | 256), dict(flags=1 | 32 | 256), dict(flags=1 | 256, dt=0.0),
     dict(dt=-1.0), dict(rho_f=0.0)])
 def test_init_rejects_invalid(lib, bad):
     so = lib.load()
