@@ -23,7 +23,10 @@ sigma_R = sqrt(2 nu eps_R), F_0 = (1, 0, 0), dt = eps_R / 10).  The fields are
     sigma_R/Dx = 0.36;
   - the disturbance of a particle settling on the imposed path of
     Eq. uncoupled_solution at t = 20 tau_p (Sec. 3.2.1) against the
-    quadrature of Eq. ref_velo_disturbance, for eps_R = 0.006 and 0.001.
+    quadrature of Eq. ref_velo_disturbance, for eps_R = 0.006 and 0.001;
+  - the same disturbance on two grids with the ERPP and with the PIC weights
+    (Fig. cfr_PIC_uncoupled): grid independent at fixed eps_R, grid dependent
+    with PIC.
 
 Reading (lag 0, as in the coupling step): a source deposited in step m is
 spread to sigma_R and then diffused by the remaining steps, so the exact
@@ -209,13 +212,13 @@ def test_fixed_force_velocity_profiles(erpp, steps):
     assert np.abs(num - ref).max() < 0.01 * np.abs(ref).max()
 
 
-def _imposed(erpp, N, eps, steps, t_end, tau_p, d_p, v_t, x0):
+def _imposed(erpp, N, eps, steps, t_end, tau_p, d_p, v_t, x0, weights="gaussian"):
     """GPU: the particle follows x_p(t) of Eq. uncoupled_solution; each step
     scatters its Stokes force (at the step's midpoint) and advances the fluid."""
     import torch
     dt = t_end / steps
     p = params(N, eps=eps, dt=dt)
-    ctx = erpp.Context(p, precision="fp32")
+    ctx = erpp.Context(p, precision="fp32", weights=weights)
     fl = erpp.StokesFluid(p, precision="fp32")
     tm = (np.arange(steps) + 0.5) * dt
     vp = v_t * (1.0 - np.exp(-tm / tau_p))
@@ -279,3 +282,30 @@ def test_imposed_motion_disturbance(erpp):
         peak[eps] = np.abs(line).max() / v_t
     # eps_R sets the near field: the smaller width carries the larger peak
     assert peak[0.001] > 1.5 * peak[0.006], peak
+
+
+def test_pic_is_grid_dependent_erpp_is_not(erpp):
+    """Sec. 3.2.1, Fig. cfr_PIC_uncoupled on synthetic input: the imposed
+    motion above (eps_R = 0.006) on 128^3 and 256^3 (sigma_R/Dx = 1.1 and 2.2).
+    With eps_R fixed the ERPP disturbance does not depend on the grid; the PIC
+    one (the force spread over one cell) sharpens as the grid is refined."""
+    tau_p, d_p = 0.01, 0.05
+    v_t = 1e-3 * NU / d_p
+    x0 = np.array([16.0 * X32, 16.0 * X32, 16.0 * X32])
+    lines = {}
+    for weights in ("gaussian", "pic"):
+        for N in (128, 256):
+            line, _ = _imposed(erpp, N, 0.006, 400, 20 * tau_p, tau_p, d_p, v_t, x0,
+                               weights=weights)
+            lines[weights, N] = line / v_t
+    # the nodes of the coarse grid are every second node of the fine one
+    g128, g256 = lines["gaussian", 128], lines["gaussian", 256][::2]
+    p128, p256 = lines["pic", 128], lines["pic", 256][::2]
+    scale = np.abs(g128).max()
+    assert np.abs(g256 - g128).max() < 0.02 * scale
+    # the PIC peak grows with refinement (1.46x here from 128^3 to 256^3; the
+    # step's own diffusion, sqrt(2 nu dt) = 0.03, keeps it below the 2x of the
+    # cell volume), the ERPP profile does not move
+    assert np.abs(lines["pic", 256]).max() > 1.3 * np.abs(p128).max()
+    assert abs(np.abs(lines["gaussian", 256]).max() / scale - 1.0) < 0.02
+    assert np.abs(p256 - p128).max() > 0.1 * np.abs(p128).max()
