@@ -1,5 +1,7 @@
 // erpp_abi.cu -- the C ABI: parameter validation, context and scratch
-// management, and the stream-ordered launch sequences of each entry point.
+// management, and the stream-ordered launch sequences of each entry point
+// (the step with the regularised kernel, with other weights, with the
+// delayed source and with the general force).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdlib.h>

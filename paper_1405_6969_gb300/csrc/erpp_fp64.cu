@@ -1,11 +1,18 @@
-// erpp_fp64.cu -- the plain FP64 form of the gather and the scatter.
+// erpp_fp64.cu -- the plain FP64 form of the gather and the scatter, and the
+// gather of the velocity with its Laplacian for the general force.
 //
 // One warp per particle, particles in index order, no binning: the lanes
 // evaluate the per-axis weights of Sec. 2.4's truncated Gaussian in double
 // precision, then walk the flattened window.  The gather reads the grid from
 // global memory; the scatter adds fscale * D_p W_p(j) (fscale = -1/rho_f for
-// the source) into the zeroed grid with FP64 global atomics.  This is the straightforward double-precision implementation the
-// FP32 tile kernels are measured against.
+// the source) into the zeroed grid with FP64 global atomics.  This is the
+// straightforward double-precision implementation the FP32 tile kernels are
+// measured against.
+//
+// The Laplacian gather (ERPP_FULL_FORCE, Eq. force_particle) walks the same
+// window with the weights' second derivatives as well; on FP32 grids its
+// windows are computed once per particle and its particles visited in
+// cell-block order.
 #include <cuda_runtime.h>
 
 #include "erpp_internal.cuh"

@@ -1,6 +1,8 @@
 // erpp_particles.cu -- per-particle kernels: self-disturbance removal, Stokes
-// drag and explicit Euler advance (Sec. 2.5), normalisation of the gathered
-// velocity, the scatter's force words, momentum sums and debug windows.
+// drag and explicit Euler advance (Sec. 2.5), the general-force advance of
+// Eq. force_particle, normalisation of the gathered velocity, the scatter's
+// force words, the delayed source's ring store, momentum sums and debug
+// windows.
 #include <cuda_runtime.h>
 
 #include "erpp_internal.cuh"
