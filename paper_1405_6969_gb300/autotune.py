@@ -85,8 +85,12 @@ def tune(ctx, u, state, S=None, candidates=CANDIDATES, steps=5, warmup=2, cache_
     """Choose and apply the fastest tile shape for this context and workload.
 
     Returns {"tile": (T_y, T_z, threads), "tiling": ctx.tiling(), "ms": {...} or None,
-    "cached": bool}.  Contexts without x/y-halo tiles are left unchanged."""
-    if ctx.tiling()[0] != 4:
+    "cached": bool}.  Contexts without x/y-halo tiles, PIC contexts (no tiles) and
+    contexts with the delayed source (whose first round(eps_R/dt) steps have no
+    source to time) are left unchanged.  Re-tiling drops the step history of a
+    context with the general force: its next step must be a first step."""
+    if (ctx.tiling()[0] != 4 or getattr(ctx, "weights", "gaussian") == "pic"
+            or getattr(ctx, "lag", False)):
         return {"tile": None, "tiling": ctx.tiling(), "ms": None, "cached": False}
     path = cache_path or default_cache_path()
     key = workload_key(ctx.params, state.n, ctx.precision, getattr(ctx, "kahan", False))

@@ -155,6 +155,8 @@ class Context:
         p = make_params(params, precision, normalize, self_removal, kahan, weights, lag,
                         full_force)
         self.weights = weights
+        self.lag = bool(lag)
+        self.full_force = bool(full_force)
         self.params = dict(params)
         self.precision = precision
         self.kahan = bool(kahan)
