@@ -367,24 +367,32 @@ __global__ void __launch_bounds__(kWarps * 32) k_gather_faxen_f32(
   __syncwarp();
   float acc[3] = {0.f, 0.f, 0.f}, lac[3] = {0.f, 0.f, 0.f};
   const size_t nn = (size_t)kp.n[0] * kp.n[1] * kp.n[2];
-  if (ok) {
-    const int total = nw[0] * nw[1] * nw[2];
-    for (int f = lane; f < total; f += 32) {
-      const int kx = f % nw[0];
-      const int t = f / nw[0];
-      const int ky = t % nw[1];
-      const int kz = t / nw[1];
-      const size_t node = ((size_t)jw[warp][2][kz] * kp.n[1] + (size_t)jw[warp][1][ky]) *
-                              kp.n[0] + (size_t)jw[warp][0][kx];
-      const float wx = w[warp][0][kx], wy = w[warp][1][ky], wz = w[warp][2][kz];
-      const float W = wx * wy * wz;
-      const float K = w2[warp][0][kx] * wy * wz + wx * w2[warp][1][ky] * wz +
-                      wx * wy * w2[warp][2][kz];
+  // lanes as (kx, row): lane kx = lane % nw_x of rows lane / nw_x, + R, ...
+  // (R = 32 / nw_x rows per pass); the row's (ky, kz) advance without divisions
+  const int R = 32 / nw[0];
+  const int kx = lane % nw[0];
+  int r0 = lane / nw[0];
+  if (ok && r0 < R) {
+    const float wx = w[warp][0][kx], w2x = w2[warp][0][kx];
+    const size_t jx = (size_t)jw[warp][0][kx];
+    int ky = r0 % nw[1], kz = r0 / nw[1];
+    for (; kz < nw[2];) {
+      const float wy = w[warp][1][ky], wz = w[warp][2][kz];
+      const float w2y = w2[warp][1][ky], w2z = w2[warp][2][kz];
+      const float W = wx * (wy * wz);
+      const float K = w2x * (wy * wz) + wx * (w2y * wz + wy * w2z);
+      const size_t node =
+          ((size_t)jw[warp][2][kz] * kp.n[1] + (size_t)jw[warp][1][ky]) * kp.n[0] + jx;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const float uv = u[c * nn + node];
         acc[c] += W * uv;
         lac[c] += K * uv;
+      }
+      ky += R;
+      while (ky >= nw[1]) {
+        ky -= nw[1];
+        ++kz;
       }
     }
   }
