@@ -166,7 +166,7 @@ def stencil_nodes(x, w):
 
 
 def algorithmic_bytes(w, n_p):
-    """Bytes the step must move (see DESIGN.md): read u and write S once
+    """Bytes the step must move: read u and write S once
     (12 B per node each, FP32), and per particle read x, v, x_prev, D,
     radius, rho_p (112 B) and write x, v, x_prev, D (96 B)."""
     return {"gather": 12 * w.n_nodes, "scatter": 12 * w.n_nodes, "advance": 208 * n_p,
