@@ -88,7 +88,8 @@ enum {
  * particle); a first step takes no time derivatives.  Gaussian weights only,
  * not with ERPP_LAG, not in the batched step (ERPP_EINVAL); dt must be
  * positive; the particle count must not change between first steps, and
- * after erpp_set_tiling the next step must be a first step (ERPP_ESTATE).
+ * after erpp_set_tiling or any call with more particles than the context has
+ * held so far the next step must be a first step (ERPP_ESTATE).
  * Other calls (erpp_interpolate, erpp_particle_advance, ...) are unchanged. */
 
 /* ERPP_LAG: the literal time delay of Eq. ns_regularized_filtered.  The
@@ -102,8 +103,9 @@ enum {
  * calls work on what they are given); with the Gaussian weights only
  * (ERPP_PIC / ERPP_POINT_GATHER: ERPP_EINVAL), not in the batched step
  * (ERPP_EINVAL); dt must be positive; the particle count must not change
- * between first steps, and after erpp_set_tiling the next step must be a
- * first step (else ERPP_ESTATE). */
+ * between first steps, and after erpp_set_tiling or any call with more
+ * particles than the context has held so far the next step must be a first
+ * step (else ERPP_ESTATE). */
 
 /* Other weights on the same grid (the comparisons of Sec. 3.2.1-3.2.2 and the
  * interpolation question of Sec. 2.5).  At most one of the two flags.

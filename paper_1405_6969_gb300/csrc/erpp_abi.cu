@@ -82,6 +82,10 @@ erpp_status ensure_capacity(erpp_ctx* c, int64_t n) {
   if (n <= c->cap) return ERPP_OK;
   int64_t cap = std::max<int64_t>(n, 1024);
   free_scratch(c);
+  // the step histories (delayed source, general force) lived in the scratch:
+  // the next step of such a context must be a first step
+  c->lag_n = -1;
+  c->ff_n = -1;
   cudaError_t e = cudaSuccess;
   if (c->fp64 || c->kp.weights != ERPP_W_GAUSS)
     e = cudaMalloc(&c->up64, sizeof(double) * 3 * (size_t)cap);

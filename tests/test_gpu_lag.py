@@ -176,3 +176,24 @@ def test_lagged_refuses_a_changed_particle_count(erpp):
     # a first step with the new count starts a new history
     ctx.step(u, erpp.ParticleState.from_numpy(small), S=S, first_step=True)
     ctx.check()
+
+
+def test_lagged_history_dropped_when_the_scratch_grows(erpp):
+    """A call with more particles than the context has held reallocates its
+    scratch, history included: the next step must be a first step."""
+    from paper_1405_6969_gb300 import ErppError
+    w, p, grid, st = _case()
+    ctx = erpp.Context(p, precision="fp64", lag=True)
+    u = cuda(grid)
+    S = ctx.new_grid()
+    ps = erpp.ParticleState.from_numpy(st)
+    ctx.step(u, ps, S=S, first_step=True)
+    ctx.step(u, ps, S=S)
+    big = 2 * st.n + 2048
+    rng = np.random.default_rng(5)
+    xb = np.stack([rng.uniform(0, w.L[a], big) for a in range(3)])
+    ctx.scatter_source(cuda(xb), cuda(np.zeros((3, big))), S=S)
+    with pytest.raises(ErppError):
+        ctx.step(u, ps, S=S)
+    ctx.step(u, ps, S=S, first_step=True)
+    ctx.check()
