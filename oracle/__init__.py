@@ -8,6 +8,12 @@ module only marshals NumPy arrays through ctypes.
 
 Array conventions: particle vectors ``[3, n]`` float64, grid fields
 ``[3, nz, ny, nx]`` float64, nodes at ``x_j = j L / N``.
+
+Sibling modules (plain NumPy on top of these functions): ``stokes`` (the
+exact Stokes step of the fluid stand-in), ``validation`` (the references of
+the paper's validation cases), ``weights`` (PIC and point-value weights),
+``lagged`` (the source delayed by eps_R) and ``full_force`` (the general
+particle force).
 """
 
 from __future__ import annotations
