@@ -28,7 +28,9 @@ sigma_R = sqrt(2 nu eps_R), F_0 = (1, 0, 0), dt = eps_R / 10).  The fields are
     (Fig. cfr_PIC_uncoupled): grid independent at fixed eps_R, grid dependent
     with PIC;
   - the fixed-force profiles for eps_R from 0.0025 to 0.02: the far field
-    does not depend on eps_R, the near-field peak does.
+    does not depend on eps_R, the near-field peak does;
+  - the imposed motion at v_t* = 1e-3 and 1e-5 in a box of 8 pi: fore-aft
+    asymmetry of the faster particle's disturbance.
 
 Reading (lag 0, as in the coupling step): a source deposited in step m is
 spread to sigma_R and then diffused by the remaining steps, so the exact
@@ -214,12 +216,12 @@ def test_fixed_force_velocity_profiles(erpp, steps):
     assert np.abs(num - ref).max() < 0.01 * np.abs(ref).max()
 
 
-def _imposed(erpp, N, eps, steps, t_end, tau_p, d_p, v_t, x0, weights="gaussian"):
+def _imposed(erpp, N, eps, steps, t_end, tau_p, d_p, v_t, x0, weights="gaussian", box=LB):
     """GPU: the particle follows x_p(t) of Eq. uncoupled_solution; each step
     scatters its Stokes force (at the step's midpoint) and advances the fluid."""
     import torch
     dt = t_end / steps
-    p = params(N, eps=eps, dt=dt)
+    p = dict(params(N, eps=eps, dt=dt), L=(box,) * 3)
     ctx = erpp.Context(p, precision="fp32", weights=weights)
     fl = erpp.StokesFluid(p, precision="fp32")
     tm = (np.arange(steps) + 0.5) * dt
@@ -351,3 +353,39 @@ def test_eps_sweep_controls_the_near_field_only(erpp):
         assert np.all(spread < 0.03), (t, v)
     assert all(a > b for a, b in zip(peaks, peaks[1:])), peaks
     assert peaks[0] > 1.5 * peaks[-1], peaks
+
+
+def test_imposed_motion_fore_aft_asymmetry(erpp):
+    """Sec. 3.2.1, right panel of Fig. sigmaR_Re: box L_B = 8 pi (240^3,
+    sigma_R/Dx = 1.05, eps_R = 0.006), v_t* = v_t d_p / nu = 1e-3 (v_t = 1)
+    and 1e-5 (v_t = 0.01), d_p = 1e-3.  Both disturbances follow the
+    regularised Eq. ref_velo_disturbance; the faster particle's is no longer
+    symmetric fore and aft (its wake is stronger), the slow one's is."""
+    from oracle import validation as V
+    box, eps, N, steps = 8 * math.pi, 0.006, 240, 400
+    tau_p, d_p, t_end = 0.01, 1e-3, 0.2
+    x0 = np.array([box / 2] * 3)
+    dx = box / N
+    ratio = {}
+    for v_t in (1.0, 0.01):
+        def xp_of(tau, v_t=v_t):
+            return np.array([x0[0] + v_t * (tau + tau_p * math.expm1(-tau / tau_p)),
+                             x0[1], x0[2]])
+
+        def D_of(tau, v_t=v_t):
+            return np.array([-3 * math.pi * NU * RHO * d_p * v_t * math.expm1(-tau / tau_p),
+                             0.0, 0.0])
+
+        line, dt = _imposed(erpp, N, eps, steps, t_end, tau_p, d_p, v_t, x0, box=box)
+        line = line / v_t
+        xend = xp_of(t_end)[0]
+        xs = np.arange(N) * dx
+        ks = [k for k in range(N) if abs(xs[k] - xend) <= 1.0][::3]
+        regs = np.array([V.imposed_motion_velocity(np.array([xs[k], x0[1], x0[2]]), t_end, xp_of,
+                                                   D_of, NU, RHO, shift=eps + dt / 2)[0] / v_t
+                         for k in ks])
+        assert np.abs(line[ks] - regs).max() < 0.02 * np.abs(regs).max(), (v_t, line[ks], regs)
+        aft, fore = np.interp(xend - 0.8, xs, line), np.interp(xend + 0.8, xs, line)
+        ratio[v_t] = aft / fore
+    assert ratio[1.0] > 1.2, ratio
+    assert abs(ratio[0.01] - 1.0) < 0.02, ratio
