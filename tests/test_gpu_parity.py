@@ -81,6 +81,11 @@ CASES = [
                                          2 * math.pi * 20 / 68)), 2000),
     ("odd_x_45x30x20", rep(I.CFG_SMALL, n=(45, 30, 20), kmax=3.0,
                            L=(2 * math.pi, 2 * math.pi * 30 / 45, 2 * math.pi * 20 / 45)), 1500),
+    # sigma_R = 2.5 dx: windows of 15-16 nodes, the widest the FP32 x/y-halo
+    # tiles take (16 x-weights per particle)
+    ("wide_80x48x40_sigma2.5", rep(I.CFG_SMALL, n=(80, 48, 40), kmax=3.0, sigma_over_dx=2.5,
+                                   L=(2 * math.pi, 2 * math.pi * 48 / 80,
+                                      2 * math.pi * 40 / 80)), 600),
 ]
 
 
@@ -356,3 +361,26 @@ def test_invalid_arguments(erpp):
         erpp.Context(dict(p, nu=-1.0))
     with pytest.raises(erpp.ErppError):
         erpp.Context(p, precision="fp64", kahan=True)
+
+
+def test_widest_window_fp64(erpp, oracle_lib):
+    """sigma_R = 5 dx at cutoff 3: windows of 30-31 nodes, the widest the
+    library takes.  The FP64 plain form matches the oracle; an FP32 context refuses the
+    parameters (its tiles take x-windows of at most 16 nodes)."""
+    from paper_1405_6969_gb300 import ErppError
+    w = rep(I.CFG_SMALL, n=(72, 64, 64), kmax=3.0, sigma_over_dx=5.0,
+            L=(2 * math.pi * 72 / 64, 2 * math.pi, 2 * math.pi))
+    p = w.params()
+    grid, st = _setup(w, 200)
+    # windows of 30 nodes, 31 for a particle whose s = x N / L is an integer
+    lo, hi = oracle_lib.windows(p, st.x)
+    assert (hi - lo + 1).max() >= 30
+    ctx = erpp.Context(p, precision="fp64")
+    S = ctx.scatter_source(cuda(st.x), cuda(st.D))
+    assert rel(S.cpu().numpy(), oracle_lib.scatter(p, st.x, st.D)) < 1e-12
+    up = ctx.interpolate(grid_t(grid, "fp64"), cuda(st.x)).cpu().numpy()
+    ref = oracle_lib.gather(p, st.x, grid)
+    assert np.abs(up - ref).max() < 1e-12 * np.abs(ref).max()
+    ctx.check()
+    with pytest.raises(ErppError):
+        erpp.Context(p, precision="fp32")
