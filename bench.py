@@ -492,15 +492,21 @@ def main():
             fl.step(u_loop, S)
         l1.record(stream)
         n_loop = 100
-        for _ in range(n_loop):
+        lev = [torch.cuda.Event(enable_timing=True) for _ in range(n_loop)]
+        for k in range(n_loop):
             ctx.step(u_loop, ps, S=S)
             fl.step(u_loop, S)
+            lev[k].record(stream)
         l2.record(stream)
         torch.cuda.synchronize()
         ctx.check()
         fluid_ms = l0.elapsed_time(l1) / 20
         loop_ms = l1.elapsed_time(l2) / n_loop
-        loop = {"steps": n_loop, "loop_ms_per_step": loop_ms, "fluid_ms_per_step": fluid_ms,
+        per_step = [l1.elapsed_time(lev[0])] + [lev[k - 1].elapsed_time(lev[k])
+                                                for k in range(1, n_loop)]
+        loop = {"steps": n_loop, "loop_ms_per_step": loop_ms,
+                "loop_ms_per_step_median": statistics.median(per_step),
+                "fluid_ms_per_step": fluid_ms,
                 "coupling_ms_per_step": loop_ms - fluid_ms,
                 "fluid": "exact periodic Stokes step (cuFFT R2C/C2R + spectral kernel)"}
         del u_loop
