@@ -5,7 +5,9 @@ unequal spacings, sigma_R / dx between 1 and 2.4 (windows of 7-15 nodes), a
 cutoff between 2.5 and 3.5, a particle cloud (uniform or clustered, 50-2500
 particles), a mean shear and gravity.  For each: integer stencil windows bit
 for bit, and three coupled steps (the first without removal) with the source,
-force and velocity within 1e-5 (FP32, relative L2) and 1e-12 (FP64).
+force and velocity within 1e-5 (FP32, relative L2) and 1e-12 (FP64); then the
+options (PIC, point-value gather, delayed source, general force) on six of
+them, five steps each against their oracle steps.
 """
 
 import dataclasses
@@ -95,6 +97,65 @@ def test_fuzz_windows_and_steps(erpp, oracle_lib, seed):
             ctx.step(u, ps, S=S, first_step=(k == 0))
             S_ref = oracle_lib.step(p, grid, ref, first_step=(k == 0))
             assert rel(S.cpu().numpy(), S_ref) < tol, (precision, k)
+            assert rel(ps.D.cpu().numpy(), ref.D) < tol, (precision, k)
+            assert rel(ps.v.cpu().numpy(), ref.v) < tol, (precision, k)
+        ctx.check()
+
+
+KINDS = ("pic", "point", "lag", "full")
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("kind", KINDS)
+def test_fuzz_options(erpp, oracle_lib, kind, seed):
+    """The options on the same random configurations, five steps each against
+    their oracle steps: PIC and point-value weights, the source delayed by
+    L = 2 steps (dt = eps_R / 2 with nu = 1 and particles of radius 0.05, so
+    that the step stays short and stable), the general force (rho_p / rho_f =
+    2, radius 0.05)."""
+    import torch
+    from oracle import full_force as FF
+    from oracle import lagged as LG
+    from oracle import weights as W
+    w, g = _config(seed)
+    if not _valid(w):
+        pytest.skip("drawn parameters outside the library's stencil limits")
+    if kind == "lag":
+        # dt = eps_R / 2: nu = 1 keeps eps_R (and the step) short, radius 0.05
+        # keeps tau_p above dt
+        w = dataclasses.replace(w, radius=0.05, nu=1.0)
+        p = w.params(gravity=g, dt=w.eps_R / 2.0)
+    elif kind == "full":
+        w = dataclasses.replace(w, radius=0.05, rho_ratio=2.0)
+        p = w.params(gravity=g)
+    else:
+        p = w.params(gravity=g)
+    grid, field = I.make_grid(w)
+    st = I.make_particles(w, field)
+    opts = {"pic": dict(weights="pic"), "point": dict(weights="point"),
+            "lag": dict(lag=True), "full": dict(full_force=True)}[kind]
+    for precision in ("fp32", "fp64"):
+        tol = (5e-5 if kind == "full" else 1e-5) if precision == "fp32" else 1e-11
+        dtype = torch.float32 if precision == "fp32" else torch.float64
+        ctx = erpp.Context(p, precision=precision, **opts)
+        ps = erpp.ParticleState.from_numpy(st)
+        u = cuda(grid, dtype)
+        S = ctx.new_grid()
+        ref, hist = st.copy(), (LG.History() if kind == "lag" else FF.History())
+        for k in range(5):
+            first = k == 0
+            ctx.step(u, ps, S=S, first_step=first)
+            if kind in ("pic", "point"):
+                S_ref = W.step(p, grid, ref, kind, first_step=first)
+            elif kind == "lag":
+                S_ref = LG.step(p, grid, ref, hist, first_step=first)
+            else:
+                S_ref = FF.step(p, grid, ref, hist, first_step=first)
+            got = S.cpu().numpy()
+            if np.abs(S_ref).max() == 0.0:
+                assert float(np.abs(got).max()) == 0.0, (precision, k)
+            else:
+                assert rel(got, S_ref) < tol, (precision, k)
             assert rel(ps.D.cpu().numpy(), ref.D) < tol, (precision, k)
             assert rel(ps.v.cpu().numpy(), ref.v) < tol, (precision, k)
         ctx.check()
