@@ -72,6 +72,9 @@ def parse():
                     help="time the step with the source delayed by eps_R (ERPP_LAG: "
                          "round(eps_R/dt) steps of positions and forces kept on the device); "
                          "the extra timings are then skipped")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the extra records (compensated scatter, 256^3 box, 64 batched "
+                         "boxes)")
     ap.add_argument("--workload", default="shear", choices=["shear", "cube256", "batched64"],
                     help="shear: 512x256x256 box (the benchmark); cube256: 256^3, 1M "
                          "particles (profiling case); batched64: 64 independent boxes "
@@ -231,16 +234,34 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(w, grid, st):
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def cpu_baseline(w, grid, st, gpu_step=None):
+    """The FP64 oracle timed on the host cores on a bounded sample (500k of
+    the particles, full grid).  gpu_step(sample) -> {mode: (S, D, v)} runs the
+    GPU step on the same sample; its error against this oracle step is
+    returned too (the oracle runs here and nowhere else in the bench)."""
     import oracle
     oracle.build()
     n_s = 500_000
     sub = I.ParticleState(*(np.ascontiguousarray(a[..., :n_s])
                             for a in (st.x, st.v, st.x_prev, st.D, st.radius, st.rho_p)))
+    inp = sub.copy()
     nn = 2 * stencil_nodes(sub.x, w)
     t0 = time.perf_counter()
-    oracle.step(w.params(), grid, sub, first_step=False)
+    S_ref = oracle.step(w.params(), grid, sub, first_step=False)
     dt = time.perf_counter() - t0
+    errors = None
+    if gpu_step is not None:
+        errors = {"sample": f"one step of {n_s} of the particles on the full grid, against "
+                            f"this oracle step", "tolerance": 1e-5}
+        for mode, (S, D, v) in gpu_step(inp).items():
+            errors[mode] = {"S": rel_l2(S, S_ref), "D": rel_l2(D, sub.D), "v": rel_l2(v, sub.v)}
+    del S_ref
     out = {"value": nn / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
            "sample": f"one FP64 oracle step of {n_s} of the 1M particles on the full "
                      f"512x256x256 grid ({dt:.1f} s, single thread)"}
@@ -256,18 +277,18 @@ def cpu_baseline(w, grid, st):
         out["all_cores"] = {"value": nn / dt_all, "cores": cores,
                             "sample": f"the same step on {cores} threads ({dt_all:.2f} s, "
                                       f"{dt / dt_all:.1f}x the single thread)"}
-    return out
+    return out, errors
 
 
-def run_batched(args, ws, rank, local):
+def batched_record(args, ws, rank, steps, peak):
     """64 independent boxes: one replayed CUDA graph per step, against the
-    same boxes as 64 plain launch sequences and against the plain FP64 form."""
+    same boxes as 64 plain launch sequences and against the plain FP64 form.
+    Returns the record (rank 0) with the timings, the step's HBM roofline
+    and the FP32 batched result's difference from the FP64 plain form on one
+    step of every box (the FP64 form matches the FP64 oracle to 1e-12)."""
     import torch
-    import torch.distributed as dist
     from paper_1405_6969_gb300 import Batch, ParticleState
     from paper_1405_6969_gb300 import dist as D
-    if ws > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     boxes = I.batched_boxes(64, seed0=D.batched_seed0(rank))
     nodes_per_step = 0
     made = []
@@ -283,12 +304,13 @@ def run_batched(args, ws, rank, local):
         for w, grid, st in made:
             u = torch.as_tensor(grid, dtype=dt).cuda().contiguous()
             entries.append((w.params(), u, ParticleState.from_numpy(st), torch.empty_like(u)))
-        return Batch(entries, precision=precision)
+        return Batch(entries, precision=precision), entries
 
     stream = torch.cuda.current_stream()
+    warm = max(3, args.warmup)
 
-    def timed(b, use_graph, steps):
-        for k in range(args.warmup):
+    def timed(b, use_graph, nsteps):
+        for k in range(warm):
             b.step(first_step=(k == 0), use_graph=use_graph)
         b.check()
         D.barrier()
@@ -296,60 +318,169 @@ def run_batched(args, ws, rank, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(steps):
+        for _ in range(nsteps):
             b.step(use_graph=use_graph)
         e1.record(stream)
         torch.cuda.synchronize()
         D.barrier()
         b.check()
-        return D.max_over_ranks(e0.elapsed_time(e1) / steps, device="cuda")
+        return D.max_over_ranks(e0.elapsed_time(e1) / nsteps, device="cuda")
 
-    b32 = batch("fp32")
+    # accuracy at the timed configuration: one step (not a first step) of
+    # every box from the same state, FP32 batched graph against FP64 plain
+    b32, e32 = batch("fp32")
     tiles = None
     if not args.no_autotune:
         import collections
-        import tempfile
         cache = os.path.join(tempfile.mkdtemp(), "tune.json")
         tiles = collections.Counter("x".join(map(str, t)) if t else "x-halo"
                                     for t in b32.autotune(cache_path=cache))
+    b64, e64 = batch("fp64")
+    b32.step(first_step=False, use_graph=True)
+    b64.step(first_step=False, use_graph=False)
+    b32.check()
+    b64.check()
+    num = {"S": 0.0, "D": 0.0, "v": 0.0}
+    den = {"S": 0.0, "D": 0.0, "v": 0.0}
+    for (_, _, p32, S32), (_, _, p64, S64) in zip(e32, e64):
+        for k, (a32, a64) in {"S": (S32, S64), "D": (p32.D, p64.D),
+                              "v": (p32.v, p64.v)}.items():
+            num[k] += float(((a32.double() - a64) ** 2).sum())
+            den[k] += float((a64 ** 2).sum())
+    accuracy = {k: math.sqrt(num[k] / max(den[k], 1e-300)) for k in num}
+    b32.close()
+    b64.close()
+    del e32, e64
+
+    b32, _ = batch("fp32")
+    if tiles:
+        b32.autotune(cache_path=cache)  # the cached choices: no timing
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
-    ms_graph = timed(b32, True, args.steps)
+    ms_graph = timed(b32, True, steps)
     clocks = sampler.stop()
-    ms_eager = timed(b32, False, max(3, args.steps // 4))
+    ms_eager = timed(b32, False, max(3, steps // 4))
     launches_per_step = b32.last_step_launches()
     b32.close()
-    b64 = batch("fp64")
-    ms_f64 = timed(b64, False, max(3, min(args.steps // 10, 10)))
+    b64, _ = batch("fp64")
+    ms_f64 = timed(b64, False, max(3, min(steps // 10, 10)))
     b64.close()
+    torch.cuda.empty_cache()
     value = D.aggregate_rate(nodes_per_step, ws, ms_graph * 1e-3)
+    if rank != 0:
+        return None
+    n_p = sum(w.n_particles for w, _, _ in made)
+    n_nodes = sum(w.n_nodes for w, _, _ in made)
+    alg = 24 * n_nodes + 208 * n_p
+    achieved = alg / (ms_graph * 1e-3) / 1e9
+    return {
+        "metric": "particle-stencil node updates/s (gather + scatter), 64 batched boxes",
+        "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
+        "warmup": warm, "ms_per_step": ms_graph, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 kernels, f64 particle integration", "data": "synthetic",
+        "config": {"workload": "batched64_boxes_64-128cube_1e3-2e5_particles",
+                   "boxes": len(made), "particles_total": n_p, "nodes_total": n_nodes,
+                   "l2": "inputs larger than L2 (about 0.9 GB of grids)"},
+        "steps_per_s": 1e3 / ms_graph,
+        "plain_launches_ms_per_step": ms_eager,
+        "graph_speedup_vs_plain_launches": ms_eager / ms_graph,
+        "fp64_plain_form_ms_per_step": ms_f64,
+        "speedup_vs_fp64_plain_form": ms_f64 / ms_graph,
+        "accuracy_fp32_vs_fp64_plain": dict(accuracy, tolerance=1e-5,
+                                            note="relative L2 over all boxes of one step; "
+                                                 "both forms meet the 1e-5 stated accuracy "
+                                                 "when these are below it"),
+        "tiles_per_box": dict(tiles) if tiles else None,
+        "roofline": {"bound": "hbm", "kernel": "whole batched step (graph)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "alg_bytes": alg},
+        "gpu_launches": launches_per_step * steps,
+        "clocks": clocks,
+    }
+
+
+def run_batched(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    peak, peak_kind = measured_peaks()
+    line = batched_record(args, ws, rank, args.steps, peak)
     if rank == 0:
-        n_p = sum(w.n_particles for w, _, _ in made)
-        line = {
-            "metric": "particle-stencil node updates/s (gather + scatter), 64 batched boxes",
-            "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 kernels, f64 particle integration", "data": "synthetic",
-            "config": {"workload": "batched64_boxes_64-128cube_1e3-2e5_particles",
-                       "boxes": len(made), "particles_total": n_p,
-                       "nodes_total": sum(w.n_nodes for w, _, _ in made),
-                       "l2": "inputs larger than L2 (about 0.9 GB of grids)"},
-            "steps_per_s": 1e3 / ms_graph,
-            "plain_launches_ms_per_step": ms_eager,
-            "graph_speedup_vs_plain_launches": ms_eager / ms_graph,
-            "fp64_plain_form_ms_per_step": ms_f64,
-            "speedup_vs_fp64_plain_form": ms_f64 / ms_graph,
-            "tiles_per_box": dict(tiles) if tiles else None,
-            "roofline": None, "cpu_baseline": None,
-            "e2e": None,
-            "gpu_launches": launches_per_step * args.steps,
-            "clocks": clocks,
-        }
+        line["roofline"]["peak_kind"] = peak_kind
+        line["cpu_baseline"] = None
+        line["e2e"] = None
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+PHASES = ["bin", "gather", "advance", "scatter"]
+
+
+def workload_record(w, args, peak, kahan=False, steps=100, made=None):
+    """One more single-box workload (the same step, its own autotuned tiles):
+    ms per step, node updates/s, per-phase times and the HBM roofline of the
+    slower tile phase and of the whole step.  made: (u, particle state) of
+    the workload when already on hand."""
+    import torch
+    from paper_1405_6969_gb300 import Context, ParticleState
+    if made is None:
+        grid64, _ = I.make_grid(w)
+        st = I.make_particles(w, None)
+        u = torch.as_tensor(grid64, dtype=torch.float32).cuda().contiguous()
+        del grid64
+    else:
+        u, st = made
+    ps = ParticleState.from_numpy(st)
+    ctx = Context(w.params(), precision="fp32", kahan=kahan)
+    S = ctx.new_grid()
+    if args.tiling:
+        t = [int(v) for v in args.tiling.lower().split("x")] + [0]
+        ctx.set_tiling(t[0], t[1], t[2])
+    elif not args.no_autotune:
+        from paper_1405_6969_gb300 import autotune
+        autotune.tune(ctx, u, ps, S=S, use_cache=False)
+    stream = torch.cuda.current_stream()
+    for k in range(max(3, args.warmup)):
+        ctx.step(u, ps, S=S, first_step=(k == 0))
+    ctx.check()
+    ctx.profile_enable(True)
+    ctx.profile_read()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.step(u, ps, S=S)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    phase_ms, nsteps = ctx.profile_read()
+    ctx.profile_enable(False)
+    ctx.check()
+    ms = e0.elapsed_time(e1) / steps
+    nodes = 2 * stencil_nodes(st.x, w)
+    per = {nm: phase_ms[k] / max(nsteps, 1) for k, nm in enumerate(PHASES)}
+    alg = algorithmic_bytes(w, w.n_particles)
+    dom = max(("gather", "scatter"), key=lambda nm: per[nm])
+    ach = alg[dom] / (per[dom] * 1e-3) / 1e9
+    step_gbs = alg["step"] / (ms * 1e-3) / 1e9
+    rec = {"workload": w.name, "grid": list(w.n), "particles": w.n_particles,
+           "kahan": bool(kahan), "ms_per_step": ms, "steps": steps,
+           "node_updates_per_s": nodes / (ms * 1e-3), "steps_per_s": 1e3 / ms,
+           "phase_ms": per, "tiling": ctx.tiling(),
+           "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak,
+                        "unit": "GB/s", "frac": ach / peak, "traffic": None},
+           "step_hbm": {"alg_bytes": alg["step"], "achieved_gbs": step_gbs,
+                        "frac": step_gbs / peak},
+           "gpu_launches_per_step": ctx.last_step_launches()}
+    ctx.close()
+    del u, S, ps
+    torch.cuda.empty_cache()
+    return rec
 
 
 def main():
@@ -384,11 +515,14 @@ def main():
     ctx = Context(w.params(), precision="fp32", kahan=args.kahan, weights=args.weights,
                   lag=args.lag, full_force=args.full_force)
     S = ctx.new_grid()
+    if args.lag or args.full_force or args.kahan or args.workload != "shear":
+        args.no_extra = True
     if args.lag or args.full_force:
         args.no_loop = args.no_e2e = args.no_cpu_baseline = args.no_variants = True
     if args.weights == "gaussian":
         nodes_per_step = 2 * stencil_nodes(st.x, w)
     else:
+        args.no_extra = True
         args.no_loop = args.no_e2e = args.no_cpu_baseline = args.no_variants = True
         nodes_per_step = (16 * w.n_particles if args.weights == "pic"
                           else 64 * w.n_particles + stencil_nodes(st.x, w))
@@ -460,8 +594,7 @@ def main():
 
     # roofline of the dominant kernel, timed live with CUDA events (the
     # per-phase events are recorded by the ERPP-kernel step only)
-    names = ["bin", "gather", "advance", "scatter"]
-    per = {nm: phase_ms[k] / max(nsteps, 1) for k, nm in enumerate(names)}
+    per = {nm: phase_ms[k] / max(nsteps, 1) for k, nm in enumerate(PHASES)}
     alg = algorithmic_bytes(w, w.n_particles)
     peak, peak_kind = measured_peaks()
     roofline = None
@@ -578,9 +711,35 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k_e2e,
                "ms_per_step": e_ms / k_e2e}
 
+    # extra records: the compensated (Kahan) scatter on this workload, the
+    # 256^3 / 1M box and the 64 batched boxes, each timed on its own
+    extra = {}
+    if not args.no_extra:
+        extra["kahan"] = workload_record(w, args, peak, kahan=True, steps=50, made=(u, st))
+        extra["cube256"] = workload_record(I.CFG_CUBE256, args, peak, steps=100)
+        extra["batched64"] = batched_record(args, ws, rank, 20, peak)
+
     cpu = None
+    errors = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, grid64, st)
+        def gpu_step(sample):
+            # the timed workload's step (its tiles) on the oracle's sample, in
+            # both scatter modes
+            out = {}
+            for mode in ("fixed_point", "kahan"):
+                ectx = Context(w.params(), precision="fp32", kahan=(mode == "kahan"))
+                t = ctx.tiling()
+                if t[0] == 4:
+                    ectx.set_tiling(t[2], t[3], t[4])
+                ectx.set_scatter_mode(ctx.scatter_mode())
+                eps = ParticleState.from_numpy(sample)
+                eS = ectx.step(u, eps, first_step=False)
+                ectx.check()
+                out[mode] = (eS.cpu().numpy(), eps.D.cpu().numpy(), eps.v.cpu().numpy())
+                ectx.close()
+                del eS, eps
+            return out
+        cpu, errors = cpu_baseline(w, grid64, st, gpu_step)
 
     if rank == 0:
         line = {
@@ -604,6 +763,10 @@ def main():
                          "frac": step_gbs / peak},
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "error_vs_oracle": errors,
+            "kahan": extra.get("kahan"),
+            "cube256": extra.get("cube256"),
+            "batched64": extra.get("batched64"),
             "coupled_loop": loop,
             "weights_variants": variants,
             "tiling": tiling,

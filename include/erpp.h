@@ -260,7 +260,8 @@ erpp_status erpp_momentum(erpp_ctx* ctx, const void* S, int64_t n, const double*
 
 /* Synchronises the stream and returns (and clears) the sticky device error:
  * ERPP_ERANGE for NaN/Inf/out-of-box positions seen since the last check,
- * ERPP_EBOUNDS for a failed internal index check, else ERPP_OK. */
+ * ERPP_EBOUNDS for a failed internal index check, ERPP_ETIMEOUT for a
+ * bounded device wait that gave up (see erpp_debug_set_wait), else ERPP_OK. */
 erpp_status erpp_check(erpp_ctx* ctx, erpp_stream stream);
 
 /* Stencil windows as the kernels compute them: for each particle and axis,
@@ -269,6 +270,19 @@ erpp_status erpp_check(erpp_ctx* ctx, erpp_stream stream);
  * arrays of 3*n (component-major). */
 erpp_status erpp_debug_windows(erpp_ctx* ctx, int64_t n, const double* const x[3],
                                int32_t* jlo, int32_t* jhi, erpp_stream stream);
+
+/* Bounded device-side waits (a tracing and testing aid, not part of the
+ * method).  The FP32 tile gather stages each tile by asynchronous copies
+ * completed on a shared-memory barrier; one thread of the block waits for it
+ * for at most limit_ns nanoseconds of the GPU's global timer, after which the
+ * block records ERPP_ETIMEOUT in the context's error word (reported by
+ * erpp_check) and returns, leaving no copy in flight.
+ * limit_ns: 0 = the default (250 ms), else 1e3 .. 1e10.  stall: 1 makes
+ * every such block, once its copies have landed, also wait on a barrier that
+ * nothing ever completes, so that the wait runs out (for tests of the
+ * timeout path); 0 = normal operation.  Takes effect for the context's next
+ * launches; ERPP_EINVAL for values out of range. */
+erpp_status erpp_debug_set_wait(erpp_ctx* ctx, int64_t limit_ns, int32_t stall);
 
 /* Kernel gather without any allocation, for callers that must not allocate
  * device memory: code running while a memory pool is frozen or exhausted,
@@ -391,6 +405,23 @@ erpp_status erpp_fluid_destroy(erpp_fluid* fluid);
  * EINVAL for other values.  Contexts outside that scope accept the call and
  * keep their own tiling. */
 erpp_status erpp_set_tiling(erpp_ctx* ctx, int32_t tile_y, int32_t tile_z, int32_t threads);
+
+/* How the FP32 scatter (x/y-halo tiles) adds each tile's halo to its
+ * neighbours (a tuning option: both modes compute the same sums up to the
+ * order of FP32 additions, and each is reproducible bit for bit):
+ *   ERPP_SCATTER_MERGE (default): one block per tile writes its interior to S
+ *     and its halo to strips in a context buffer; two merge kernels then add
+ *     the strips onto the neighbouring tiles' rims.
+ *   ERPP_SCATTER_CLUSTER: the x-tiles of each (y, z) tile row run as one
+ *     thread-block cluster, and every tile adds its x-neighbours' halo columns
+ *     to its own rim straight from their shared memory (fixed order: own,
+ *     left, right); the y-halo still goes through strips and one merge kernel.
+ *     Needs rows of at most 8 x-tiles starting on multiples of 4 nodes (nx a
+ *     multiple of 4) and a 16-byte aligned S, and enough resources for a
+ *     cluster to be resident; otherwise the MERGE form runs.
+ * ERPP_EINVAL for other values. */
+enum { ERPP_SCATTER_MERGE = 0, ERPP_SCATTER_CLUSTER = 1 };
+erpp_status erpp_set_scatter_mode(erpp_ctx* ctx, int32_t mode);
 
 /* out[0] = tile design in use (4: x/y-halo tiles, 3: x-halo tiles cut in y
  * and z), out[1..3] = tile size W, T_y, T_z, out[4] = threads per block.

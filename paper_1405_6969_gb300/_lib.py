@@ -26,6 +26,8 @@ POINT_GATHER = 1 << 6
 LAG = 1 << 7
 FULL_FORCE = 1 << 8
 
+SCATTER_MODES = {"merge": 0, "cluster": 1}
+
 STATUS = {0: "ERPP_OK", 1: "ERPP_EINVAL", 2: "ERPP_ENOMEM", 3: "ERPP_ECUDA",
           4: "ERPP_ERANGE", 5: "ERPP_EBOUNDS", 6: "ERPP_ETIMEOUT", 7: "ERPP_ESTATE"}
 
@@ -86,6 +88,7 @@ _SIGS = {
     "erpp_momentum": (_st, [_vp, _vp, _i64, _dp3, _dp3, _dp, _vp]),
     "erpp_check": (_st, [_vp, _vp]),
     "erpp_debug_windows": (_st, [_vp, _i64, _dp3, _vp, _vp, _vp]),
+    "erpp_debug_set_wait": (_st, [_vp, _i64, ctypes.c_int32]),
     "erpp_interpolate_noalloc": (_st, [ctypes.POINTER(Params), _vp, _i64, _dp3, _dp3, _vp]),
     "erpp_profile_enable": (_st, [_vp, ctypes.c_int]),
     "erpp_profile_read": (_st, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)]),
@@ -97,6 +100,7 @@ _SIGS = {
     "erpp_batch_destroy": (_st, [_vp]),
     "erpp_set_tiling": (_st, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "erpp_get_tiling": (_st, [_vp, ctypes.POINTER(ctypes.c_int32)]),
+    "erpp_set_scatter_mode": (_st, [_vp, ctypes.c_int32]),
     "erpp_last_step_launches": (_st, [_vp, ctypes.POINTER(ctypes.c_int32)]),
     "erpp_batch_last_step_launches": (_st, [_vp, ctypes.POINTER(ctypes.c_int32)]),
     "erpp_batch_get_tiling": (_st, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),

@@ -8,9 +8,11 @@ threads per block hide more latency but split a tile's units over more
 warps.  The best shape depends on the grid, the kernel width sigma_R / dx and
 the particle density, so it is
 measured: every candidate runs a few coupling steps (CUDA events, on copies of
-the particle state) and the fastest is applied and remembered in a JSON cache
-keyed by (grid, r_c / dx, particles per node class, options).  Host logic
-only; every step it times runs in the CUDA library.
+the particle state), then the three fastest shapes are timed again with the
+scatter's x-halo exchanged through thread-block clusters (scatter mode
+"cluster"), and the fastest (shape, mode) is applied and remembered in a JSON
+cache keyed by (grid, r_c / dx, particles per node class, options).  Host
+logic only; every step it times runs in the CUDA library.
 """
 
 from __future__ import annotations
@@ -84,31 +86,43 @@ def tune(ctx, u, state, S=None, candidates=CANDIDATES, steps=5, warmup=2, cache_
          use_cache=True):
     """Choose and apply the fastest tile shape for this context and workload.
 
-    Returns {"tile": (T_y, T_z, threads), "tiling": ctx.tiling(), "ms": {...} or None,
-    "cached": bool}.  Contexts without x/y-halo tiles, PIC contexts (no tiles) and
+    Returns {"tile": (T_y, T_z, threads), "mode": scatter mode, "tiling": ctx.tiling(),
+    "ms": {...} or None, "cached": bool}.  Contexts without x/y-halo tiles, PIC contexts (no tiles) and
     contexts with the delayed source (whose first round(eps_R/dt) steps have no
     source to time) are left unchanged.  Re-tiling drops the step history of a
     context with the general force: its next step must be a first step."""
     if (ctx.tiling()[0] != 4 or getattr(ctx, "weights", "gaussian") == "pic"
             or getattr(ctx, "lag", False)):
-        return {"tile": None, "tiling": ctx.tiling(), "ms": None, "cached": False}
+        return {"tile": None, "mode": None, "tiling": ctx.tiling(), "ms": None, "cached": False}
     path = cache_path or default_cache_path()
     key = workload_key(ctx.params, state.n, ctx.precision, getattr(ctx, "kahan", False))
     cache = load_cache(path) if use_cache else {}
     if use_cache and key in cache and len(cache[key].get("tile", ())) == 3:
         ty, tz, nt = cache[key]["tile"]
+        mode = cache[key].get("mode", "merge")
         ctx.set_tiling(ty, tz, nt)
-        return {"tile": (ty, tz, nt), "tiling": ctx.tiling(), "ms": cache[key].get("ms"),
-                "cached": True}
+        ctx.set_scatter_mode(mode)
+        return {"tile": (ty, tz, nt), "mode": mode, "tiling": ctx.tiling(),
+                "ms": cache[key].get("ms"), "cached": True}
     S = ctx.new_grid() if S is None else S
     times = {}
+    ctx.set_scatter_mode("merge")
     for ty, tz, nt in candidates:
         ctx.set_tiling(ty, tz, nt)
         times[f"{ty}x{tz}x{nt}"] = _time_steps(ctx, u, state, S, steps, warmup)
+    ctx.set_scatter_mode("cluster")
+    for name in sorted(times, key=times.get)[:3]:
+        ty, tz, nt = (int(v) for v in name.split("x"))
+        ctx.set_tiling(ty, tz, nt)
+        times[f"{name}xcluster"] = _time_steps(ctx, u, state, S, steps, warmup)
     best = min(times, key=times.get)
-    ty, tz, nt = (int(v) for v in best.split("x"))
+    parts = best.split("x")
+    ty, tz, nt = (int(v) for v in parts[:3])
+    mode = "cluster" if len(parts) == 4 else "merge"
     ctx.set_tiling(ty, tz, nt)
+    ctx.set_scatter_mode(mode)
     if use_cache:
-        cache[key] = {"tile": [ty, tz, nt], "ms": times}
+        cache[key] = {"tile": [ty, tz, nt], "mode": mode, "ms": times}
         save_cache(path, cache)
-    return {"tile": (ty, tz, nt), "tiling": ctx.tiling(), "ms": times, "cached": False}
+    return {"tile": (ty, tz, nt), "mode": mode, "tiling": ctx.tiling(), "ms": times,
+            "cached": False}

@@ -139,6 +139,15 @@ erpp_status alloc_tile_tables(erpp_ctx* c) {
   return set_cuda_err(e);
 }
 
+void free_tile_tables(erpp_ctx* c) {
+  cudaFree(c->tile_cnt);
+  cudaFree(c->tile_start);
+  cudaFree(c->scan_tmp);
+  cudaFree(c->halo);
+  c->tile_cnt = c->tile_start = c->scan_tmp = nullptr;
+  c->halo = nullptr;
+}
+
 // Cell-block tables of the other weights' particle sort (8 x 8 x 8-node blocks
 // plus one bin for invalid positions).
 erpp_status alloc_weight_tables(erpp_ctx* c) {
@@ -250,6 +259,8 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
   kp.raw_norm3 = pow(2.0 * kPi * sig2, -1.5);
   kp.lag = (p->flags & ERPP_LAG) ? std::max(1, (int)lround(p->eps_R / p->dt)) : 0;
   kp.full_force = (p->flags & ERPP_FULL_FORCE) ? 1 : 0;
+  kp.wait_ns = c->wait_req_ns > 0 ? c->wait_req_ns : kDefaultWaitNs;
+  kp.debug_stall = c->stall_req ? 1 : 0;
   kp.weights = (p->flags & ERPP_PIC) ? ERPP_W_PIC
                : (p->flags & ERPP_POINT_GATHER) ? ERPP_W_POINT : ERPP_W_GAUSS;
   // The disturbance as the gather sees it: forcing diffused one step, plus the
@@ -430,10 +441,7 @@ erpp_status erpp_destroy(erpp_ctx* c) {
     free(c->prof_ev);
   }
   free_scratch(c);
-  cudaFree(c->tile_cnt);
-  cudaFree(c->tile_start);
-  cudaFree(c->scan_tmp);
-  cudaFree(c->halo);
+  free_tile_tables(c);
   cudaFree(c->w_cnt);
   cudaFree(c->w_start);
   cudaFree(c->w_tmp);
@@ -458,21 +466,23 @@ erpp_status erpp_set_tiling(erpp_ctx* c, int32_t tile_y, int32_t tile_z, int32_t
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return set_cuda_err(e);
   free_scratch(c);
-  cudaFree(c->tile_cnt);
-  cudaFree(c->tile_start);
-  cudaFree(c->scan_tmp);
-  cudaFree(c->halo);
-  c->tile_cnt = c->tile_start = c->scan_tmp = nullptr;
-  c->halo = nullptr;
+  free_tile_tables(c);
   c->tile_req[0] = tile_y;
   c->tile_req[1] = tile_z;
   c->tile_req[2] = threads;
   c->lag_n = -1;  // the delayed source's history went with the scratch: first_step next
   c->ff_n = -1;
   c->kp = probe.kp;
+  c->cluster_probe = 0;
   for (int a = 0; a < 3; ++a) c->maxseg[a] = probe.maxseg[a];
   c->xw_len = probe.xw_len;
   return alloc_tile_tables(c);
+}
+
+erpp_status erpp_set_scatter_mode(erpp_ctx* c, int32_t mode) {
+  if (!c || (mode != ERPP_SCATTER_MERGE && mode != ERPP_SCATTER_CLUSTER)) return ERPP_EINVAL;
+  c->scatter_mode = mode;
+  return ERPP_OK;
 }
 
 erpp_status erpp_get_tiling(erpp_ctx* c, int32_t out[5]) {
@@ -815,6 +825,17 @@ erpp_status erpp_momentum(erpp_ctx* c, const void* S, int64_t n, const double* c
   e = cudaMemcpyAsync(out, c->red + 6 * 304, sizeof(double) * 6, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return set_cuda_err(e);
   return erpp_check(c, stream);
+}
+
+erpp_status erpp_debug_set_wait(erpp_ctx* c, int64_t limit_ns, int32_t stall) {
+  if (!c || limit_ns < 0 || limit_ns > 10000000000LL || (stall != 0 && stall != 1))
+    return ERPP_EINVAL;
+  if (limit_ns > 0 && limit_ns < 1000) return ERPP_EINVAL;
+  c->wait_req_ns = limit_ns;
+  c->stall_req = stall;
+  c->kp.wait_ns = limit_ns > 0 ? limit_ns : kDefaultWaitNs;
+  c->kp.debug_stall = stall;
+  return ERPP_OK;
 }
 
 erpp_status erpp_debug_windows(erpp_ctx* c, int64_t n, const double* const x[3], int32_t* jlo,

@@ -74,6 +74,9 @@ struct erpp_kparams {
   int32_t weights;   // ERPP_W_GAUSS, ERPP_W_PIC or ERPP_W_POINT
   int32_t lag;       // ERPP_LAG: source delay in steps, round(eps_R / dt) >= 1; else 0
   int32_t full_force;// ERPP_FULL_FORCE
+  int32_t debug_stall;// test hook: after its copies land, the gather also waits
+                      // on a barrier that nothing completes (the wait runs out)
+  int64_t wait_ns;   // limit of every bounded device-side wait, nanoseconds
   double inv_dx[3];  // N / L
   double L[3];
   double cp[3];      // r_c / dx
@@ -108,6 +111,11 @@ struct erpp_ctx {
   int fp64;
   int maxseg[3];          // most tiles one window can reach per axis
   int tile_req[3];        // requested T_y, T_z, threads of the x/y-halo tiles (0: default)
+  int64_t wait_req_ns;    // erpp_debug_set_wait: bounded-wait limit (0: default)
+  int stall_req;          // erpp_debug_set_wait: stall hook of the gather
+  int scatter_mode;       // erpp_set_scatter_mode (ERPP_SCATTER_*)
+  int cluster_probe;      // clustered scatter for the current tiling: 0 = not yet
+                          // asked, 1 = resident clusters possible, 2 = not
   struct erpp_host_pipe* hp;  // erpp_step_host staging and streams (lazily created)
   int launches;           // kernels launched since erpp_step began (counted at each launch)
   int last_step_launches; // kernels the most recent erpp_step launched
@@ -150,6 +158,9 @@ struct erpp_ctx {
 };
 
 constexpr int kProfSets = 1024;
+// Default limit of a bounded device-side wait (a staged tile's copies land
+// within microseconds; the limit only guards against a copy that never does).
+constexpr int64_t kDefaultWaitNs = 250000000;
 
 // ---- host-side launchers (stream-ordered, no synchronisation) ----
 namespace erpp {

@@ -172,13 +172,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return done != 0;
 }
-// Waits for phase `parity` of the barrier, at most `limit` polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int limit) {
-  for (int i = 0; i < limit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
 }
-constexpr int kTmaWaitPolls = 1 << 22;
+// Waits for phase `parity` of the barrier for at most `limit_ns` nanoseconds
+// (the global timer); false when the phase has not completed by then.
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t* bar, unsigned parity, int64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((int64_t)(globaltimer_ns() - t0) > limit_ns) return false;
+  }
+}
 // Bulk copy global -> shared completed on an mbarrier (both 16-byte aligned,
 // bytes a multiple of 16).
 __device__ __forceinline__ void bulk_load_g2s(unsigned dst, const void* src, unsigned bytes,
@@ -187,6 +195,32 @@ __device__ __forceinline__ void bulk_load_g2s(unsigned dst, const void* src, uns
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
       ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
       : "memory");
+}
+
+// ---- thread-block clusters: rank, barrier, distributed shared memory ----
+__device__ __forceinline__ unsigned cluster_ctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
+}
+// Every thread of every block of the cluster arrives (release: this block's
+// earlier memory accesses are ordered before the others' waits return).
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+// The address of the same shared-memory location in block `rank` of the cluster.
+__device__ __forceinline__ unsigned mapa_shared(unsigned addr, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float ld_cluster_f32(unsigned addr) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];\n" : "=f"(v) : "r"(addr) : "memory");
+  return v;
 }
 
 // ---- shared-memory accesses by 32-bit shared address, immediate offsets ----
@@ -579,6 +613,7 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SchedState ss;
   __shared__ __align__(8) uint64_t tma_bar;
+  __shared__ __align__(8) uint64_t stall_bar;  // debug_stall only: never completed
   constexpr int PB = Batch<XW>::kPB;
   static_assert(PB <= NT, "a batch holds at most one piece per thread");
   const int tile = blockIdx.x;
@@ -601,6 +636,7 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
                     (kp.px & 3) == 0 && (((uintptr_t)u) & 15) == 0;
   if (threadIdx.x == 0 && (tma || rows)) {
     mbar_init(&tma_bar, 1);
+    if (kp.debug_stall) mbar_init(&stall_bar, 1);
     if (tma) {
       mbar_expect_tx(&tma_bar, (unsigned)(3 * kp.plane * 4));
       tma_load_4d(cv.field, &tmap, &tma_bar, x0, y0, b[2], 0);
@@ -625,16 +661,27 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
     for (int k = threadIdx.x; k < 3 * PB; k += NT) cv.pacc[k] = 0.f;
     const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
     cp_async_wait_all();                            // field (first batch), x-weights
-    if ((tma || rows) && !staged) {
-      staged = true;
-      if (!mbar_wait_bounded(&tma_bar, 0, kTmaWaitPolls)) {
-        // the copy did not complete: report, wait once more for it, give up
-        if (threadIdx.x == 0) erpp_set_err(err, ERPP_ERRBIT_TIMEOUT);
-        mbar_wait_bounded(&tma_bar, 0, kTmaWaitPolls);
-        return;
+    // One thread waits (bounded) for the staged field; the block learns the
+    // outcome at the barrier and either goes on or returns as a whole.
+    int timed_out = 0;
+    const bool first_wait = (tma || rows) && !staged;
+    if (first_wait && threadIdx.x == 0) {
+      bool ok = mbar_wait_ns(&tma_bar, 0, kp.wait_ns);
+      if (!ok) {
+        mbar_wait_ns(&tma_bar, 0, kp.wait_ns);  // once more for the copy in flight
+      } else if (kp.debug_stall) {
+        ok = mbar_wait_ns(&stall_bar, 0, kp.wait_ns);  // nothing arrives: runs out
+      }
+      if (!ok) {
+        erpp_set_err(err, ERPP_ERRBIT_TIMEOUT);
+        timed_out = 1;
       }
     }
-    __syncthreads();
+    staged = staged || first_wait;
+    if (__syncthreads_or(timed_out)) return;
+    // the phase has completed: every thread observes it (acquire of the
+    // copied field), which returns at once
+    if (first_wait && threadIdx.x != 0) mbar_try_wait(&tma_bar, 0);
     for (int r = 0; r < R; ++r) {
       const uint16_t ui = cv.sched[r * NT + warp * 32 + lane];
       const bool active = ui != kEmpty;
@@ -709,24 +756,37 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
 }
 
 // MODE 0: fixed point (FP32 atomics on dense tiles); MODE 1: compensated FP32.
+// CL: the launch groups the nt[0] x-tiles of one (y, z) tile row into a
+// thread-block cluster (rank = x-tile): once every block of the row has
+// formed its final values in shared memory, each block adds its x-neighbours'
+// halo columns to its own rim columns straight from their shared memory, in a
+// fixed order (own, left, right), so that no x-strip is written and
+// k_merge_cols is not needed; the y-halo rows, which then hold the diagonal
+// neighbours' corner columns too, still leave as y-strips for k_merge_rows.
+// Requires rows of a multiple of 4 nodes and 16-byte aligned S and strips
+// (the host launches CL only then).
+// Result of accumulating one tile's pieces in shared memory.
+struct TileAcc {
+  bool any;         // the tile has pieces
+  bool fixedp;      // 32-bit fixed point (else FP32 values)
+  float inv_scale;  // fixed point: value of one unit of the sums
+};
+
+// Accumulates the pieces of `tile` into the staged tile in shared memory
+// (cleared first): fixed-point integers, FP32 values on dense tiles, or FP32
+// values with their low-order parts (MODE 1).  Called by the whole block.
 template <int XM, int LMIN, int XW, int MODE, int NT>
-__global__ void __launch_bounds__(NT, 2) k_scatter4(
-    erpp_kparams kp, float* __restrict__ S, float* __restrict__ halo,
-    const int32_t* __restrict__ start, const int4* __restrict__ entries, int64_t ecap,
-    const float* __restrict__ xw, const float4* __restrict__ fscat) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ SchedState ss;
+__device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile,
+                                                const Carve<XW>& cv, SchedState& ss, float* red,
+                                                const int32_t* __restrict__ start,
+                                                const int4* __restrict__ entries, int64_t ecap,
+                                                const float* __restrict__ xw,
+                                                const float4* __restrict__ fscat) {
   constexpr int NW = NT / 32;
-  __shared__ float red[NW];
   constexpr int PB = Batch<XW>::kPB;
-  static_assert(PB <= NT, "a batch holds at most one piece per thread");
-  const int tile = blockIdx.x;
+  float* smem = cv.field;
   const int e0 = start[tile];
   const int e1 = (int)min((int64_t)start[tile + 1], ecap);
-  const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, MODE == 1 ? 6 : 3, false);
-  float* smem = cv.field;
-  int b[3], ext[3], tt[3];
-  tile_origin4(kp, tile, b, ext, tt);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int plane = kp.plane, px = kp.px, pxy = kp.pxy;
   const bool any = e0 < e1;
@@ -734,7 +794,6 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
   const int bs = any ? batch_size(e1 - e0, PB) : 1;
   const int4 rfirst = load_rec(entries, e0, min(bs, e1 - e0));  // overlaps the clearing
   float scale = 1.f, inv_scale = 1.f;
-  int* acc_i = reinterpret_cast<int*>(smem);
   {
     const int total = (MODE == 1 ? 6 : 3) * plane;
     float4* s4 = reinterpret_cast<float4*>(smem);
@@ -881,6 +940,32 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
       __syncthreads();
     }
   }
+  return TileAcc{any, fixedp, inv_scale};
+}
+
+template <int XM, int LMIN, int XW, int MODE, int NT, bool CL>
+__global__ void __launch_bounds__(NT, 2) k_scatter4(
+    erpp_kparams kp, float* __restrict__ S, float* __restrict__ halo,
+    const int32_t* __restrict__ start, const int4* __restrict__ entries, int64_t ecap,
+    const float* __restrict__ xw, const float4* __restrict__ fscat) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ SchedState ss;
+  constexpr int NW = NT / 32;
+  __shared__ float red[NW];
+  constexpr int PB = Batch<XW>::kPB;
+  static_assert(PB <= NT, "a batch holds at most one piece per thread");
+  const int tile = blockIdx.x;
+  const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, MODE == 1 ? 6 : 3, false);
+  float* smem = cv.field;
+  const TileAcc ta =
+      scatter_tile<XM, LMIN, XW, MODE, NT>(kp, tile, cv, ss, red, start, entries, ecap, xw, fscat);
+  const bool any = ta.any, fixedp = ta.fixedp;
+  const float inv_scale = ta.inv_scale;
+  int b[3], ext[3], tt[3];
+  tile_origin4(kp, tile, b, ext, tt);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int plane = kp.plane, px = kp.px, pxy = kp.pxy;
+  int* acc_i = reinterpret_cast<int*>(smem);
   // interior once (zeros for empty tiles); halo strips to the buffer:
   // x-strips [3][T_z][T_y + hy][hx] (all staged rows), y-strips [3][T_z][hy][W]
   // (16-byte aligned).
@@ -889,10 +974,10 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
   const int ny_st = ext[1] + hy;
   float* hxs = halo + (size_t)tile * kp.halo_per_tile;
   float* hys = hxs + kp.ystrip_off;
-  const bool vec = (kp.n[0] & 3) == 0 && (ext[0] & 3) == 0 && (b[0] & 3) == 0 &&
-                   (kp.T[0] & 3) == 0 && (((uintptr_t)S) & 15) == 0 &&
-                   (((uintptr_t)halo) & 15) == 0;
-  if (vec && hx <= 16) {
+  const bool vec = CL || ((kp.n[0] & 3) == 0 && (ext[0] & 3) == 0 && (b[0] & 3) == 0 &&
+                           (kp.T[0] & 3) == 0 && (((uintptr_t)S) & 15) == 0 &&
+                           (((uintptr_t)halo) & 15) == 0);
+  if (CL || (vec && hx <= 16)) {
     // Aligned rows: the final values are formed in place, then every staged
     // row's interior columns leave by one bulk asynchronous copy (to S, or to
     // the y-strip on a y-halo row) and the hx halo columns of all rows by
@@ -917,9 +1002,43 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
         s4[k] = v;
       }
     }
+    const unsigned fbase = shared_addr(smem);
+    if (CL) {
+      // every block of the row has its final values in place
+      cluster_arrive();
+      cluster_wait();
+      const int ntx = kp.nt[0];
+      const unsigned rank = cluster_ctarank();
+      const unsigned rl = rank == 0 ? ntx - 1 : rank - 1;
+      const unsigned rr = rank + 1 == (unsigned)ntx ? 0 : rank + 1;
+      const int extl = min((int)(rl + 1) * kp.T[0], kp.n[0]) - (int)rl * kp.T[0];
+      const unsigned lbase = mapa_shared(fbase, rl), rbase = mapa_shared(fbase, rr);
+      // rim columns: x < xhhi take the left tile's right halo (its column
+      // xoff + extl + x), x >= ext - xhlo the right tile's left halo (its
+      // column xoff + x - ext); a tile narrower than hx takes both
+      const bool allcols = ext[0] < hx;
+      const int ncol = allcols ? ext[0] : hx;
+      const int njob = 3 * ext[2] * ny_st * ncol;
+      for (int j = threadIdx.x; j < njob; j += NT) {
+        const int r = j / ncol;
+        const int q = j - r * ncol;
+        const int x = allcols || q < kp.xhhi ? q : ext[0] - hx + q;
+        const int cz = r / ny_st;
+        const int y = r - cz * ny_st;
+        const int cc = cz / ext[2];
+        const int z = cz - cc * ext[2];
+        const int row = cc * plane + z * pxy + y * px + kp.xoff;
+        float v = smem[row + x];
+        if (x < kp.xhhi) v += ld_cluster_f32(lbase + 4u * (unsigned)(row + extl + x));
+        if (x >= ext[0] - kp.xhlo) v += ld_cluster_f32(rbase + 4u * (unsigned)(row + x - ext[0]));
+        smem[row + x] = v;
+      }
+      // this block has read its neighbours' halos (they may leave once every
+      // block has arrived here)
+      cluster_arrive();
+    }
     fence_proxy_async_shared();
     __syncthreads();
-    const unsigned fbase = shared_addr(smem);
     const int nrow = 3 * ext[2] * ny_st;
     bool issued = false;
     for (int r = threadIdx.x; r < nrow; r += NT) {
@@ -938,6 +1057,11 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
       issued = true;
     }
     if (issued) bulk_commit_wait_read();
+    if (CL) {
+      // the neighbours have read this block's halo columns
+      cluster_wait();
+      return;
+    }
     const int rpw = 32 / hx;  // staged rows per warp pass
     const int rsub = lane / hx, h = lane - rsub * hx;
     const int col = h < kp.xhlo ? kp.xoff - kp.xhlo + h : kp.xoff + ext[0] + (h - kp.xhlo);
@@ -1197,27 +1321,77 @@ cudaError_t gather4(erpp_ctx* ctx, const float* u, cudaStream_t st) {
                                  : gather4_nt<XM, LMIN, XW, 256>(ctx, u, st);
 }
 
-template <int XM, int LMIN, int XW, int MODE, int NT>
+// Launches k_scatter4; CL: as thread-block clusters of the nt[0] x-tiles of a
+// tile row (returns cudaErrorNotSupported, launching nothing, when such
+// clusters cannot be resident).
+template <int XM, int LMIN, int XW, int MODE, int NT, bool CL>
 cudaError_t scatter4_mode(erpp_ctx* ctx, float* S, cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;
   const size_t sm = carve_bytes<XW>(kp.plane, MODE == 1 ? 6 : 3, false);
-  cudaError_t e = cudaFuncSetAttribute(k_scatter4<XM, LMIN, XW, MODE, NT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  auto kern = k_scatter4<XM, LMIN, XW, MODE, NT, CL>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
+  if (!CL) {
+    ++ctx->launches;
+    kern<<<kp.ntiles, NT, sm, st>>>(kp, S, ctx->halo, ctx->tile_start, ctx->entries,
+                                    ctx->entries_cap, ctx->xw, ctx->fscat);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)kp.ntiles);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)kp.nt[0];
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (ctx->cluster_probe == 0) {
+    int nclusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+    if (e != cudaSuccess) cudaGetLastError();
+    ctx->cluster_probe = (e == cudaSuccess && nclusters >= 1) ? 1 : 2;
+  }
+  if (ctx->cluster_probe != 1) return cudaErrorNotSupported;
   ++ctx->launches;
-  k_scatter4<XM, LMIN, XW, MODE, NT><<<kp.ntiles, NT, sm, st>>>(
-      kp, S, ctx->halo, ctx->tile_start, ctx->entries, ctx->entries_cap, ctx->xw, ctx->fscat);
-  return cudaGetLastError();
+  return cudaLaunchKernelEx(&cfg, kern, kp, S, ctx->halo, (const int32_t*)ctx->tile_start,
+                            (const int4*)ctx->entries, ctx->entries_cap, (const float*)ctx->xw,
+                            (const float4*)ctx->fscat);
 }
 
-template <int XM, int LMIN, int XW>
+template <int XM, int LMIN, int XW, bool CL>
 cudaError_t scatter4(erpp_ctx* ctx, float* S, cudaStream_t st) {
   const bool big = ctx->kp.nthreads == 512;
   if (ctx->kp.kahan)
-    return big ? scatter4_mode<XM, LMIN, XW, 1, 512>(ctx, S, st)
-               : scatter4_mode<XM, LMIN, XW, 1, 256>(ctx, S, st);
-  return big ? scatter4_mode<XM, LMIN, XW, 0, 512>(ctx, S, st)
-             : scatter4_mode<XM, LMIN, XW, 0, 256>(ctx, S, st);
+    return big ? scatter4_mode<XM, LMIN, XW, 1, 512, CL>(ctx, S, st)
+               : scatter4_mode<XM, LMIN, XW, 1, 256, CL>(ctx, S, st);
+  return big ? scatter4_mode<XM, LMIN, XW, 0, 512, CL>(ctx, S, st)
+             : scatter4_mode<XM, LMIN, XW, 0, 256, CL>(ctx, S, st);
+}
+
+template <bool CL>
+cudaError_t scatter4_variant(erpp_ctx* ctx, float* S, cudaStream_t st, int variant) {
+  switch (variant) {
+    case 0: return scatter4<7, 6, 8, CL>(ctx, S, st);
+    case 1: return scatter4<7, 5, 8, CL>(ctx, S, st);
+    case 2: return scatter4<10, 9, 16, CL>(ctx, S, st);
+    case 3: return scatter4<10, 8, 16, CL>(ctx, S, st);
+    default: return scatter4<16, 1, 16, CL>(ctx, S, st);
+  }
+}
+
+// The x-halo exchange through clusters needs whole 16-byte rows (every
+// tile's start and width a multiple of 4 nodes), aligned source and strips,
+// and a row of at most 8 x-tiles (the portable cluster size).
+bool cluster_eligible(const erpp_ctx* ctx, const float* S) {
+  const erpp_kparams& kp = ctx->kp;
+  return ctx->scatter_mode == ERPP_SCATTER_CLUSTER && kp.nt[0] >= 1 && kp.nt[0] <= 8 &&
+         (kp.n[0] & 3) == 0 && (kp.T[0] & 3) == 0 && (((uintptr_t)S) & 15) == 0 &&
+         (((uintptr_t)ctx->halo) & 15) == 0;
 }
 
 }  // namespace
@@ -1252,18 +1426,21 @@ cudaError_t launch_gather_f32_4(erpp_ctx* ctx, const float* u, cudaStream_t st) 
 }
 
 cudaError_t launch_scatter_f32_4(erpp_ctx* ctx, float* S, cudaStream_t st) {
-  cudaError_t e;
-  switch (variant4(ctx->kp)) {
-    case 0: e = scatter4<7, 6, 8>(ctx, S, st); break;
-    case 1: e = scatter4<7, 5, 8>(ctx, S, st); break;
-    case 2: e = scatter4<10, 9, 16>(ctx, S, st); break;
-    case 3: e = scatter4<10, 8, 16>(ctx, S, st); break;
-    default: e = scatter4<16, 1, 16>(ctx, S, st); break;
+  const int v = variant4(ctx->kp);
+  bool clustered = false;
+  cudaError_t e = cudaErrorNotSupported;
+  if (cluster_eligible(ctx, S)) {
+    e = scatter4_variant<true>(ctx, S, st, v);
+    clustered = e == cudaSuccess;
   }
+  if (e == cudaErrorNotSupported) e = scatter4_variant<false>(ctx, S, st, v);
   if (e != cudaSuccess) return e;
-  ctx->launches += 2;
+  ++ctx->launches;
   k_merge_rows<<<ctx->kp.ntiles, kMergeThreads, 0, st>>>(ctx->kp, S, ctx->halo);
-  k_merge_cols<<<ctx->kp.ntiles, kMergeThreads, 0, st>>>(ctx->kp, S, ctx->halo);
+  if (!clustered) {
+    ++ctx->launches;
+    k_merge_cols<<<ctx->kp.ntiles, kMergeThreads, 0, st>>>(ctx->kp, S, ctx->halo);
+  }
   return cudaGetLastError();
 }
 

@@ -272,6 +272,17 @@ class Context:
         _lib.check(self.lib.erpp_set_tiling(self._h, int(tile_y), int(tile_z), int(threads)),
                    "erpp_set_tiling")
 
+    def set_scatter_mode(self, mode="merge"):
+        """How the FP32 scatter adds tile halos to the neighbours: "merge"
+        (halo strips and two merge kernels, the default) or "cluster" (the
+        x-halo through thread-block clusters, the y-halo through strips)."""
+        _lib.check(self.lib.erpp_set_scatter_mode(self._h, _lib.SCATTER_MODES[mode]),
+                   "erpp_set_scatter_mode")
+        self._scatter_mode = mode
+
+    def scatter_mode(self):
+        return getattr(self, "_scatter_mode", "merge")
+
     def tiling(self):
         """(design, W, T_y, T_z, threads) of the tiles in use."""
         out = (ctypes.c_int32 * 5)()
@@ -296,6 +307,13 @@ class Context:
         _lib.check(self.lib.erpp_profile_read(self._h, ctypes.cast(ms, _lib._dp),
                                               ctypes.byref(n)), "erpp_profile_read")
         return list(ms), int(n.value)
+
+    def debug_set_wait(self, limit_ns=0, stall=False):
+        """Limit (nanoseconds, 0 = default) of the gather's bounded wait for its
+        staged tile; ``stall`` makes the wait run out on purpose (tests of the
+        ERPP_ETIMEOUT path)."""
+        _lib.check(self.lib.erpp_debug_set_wait(self._h, int(limit_ns), int(bool(stall))),
+                   "erpp_debug_set_wait")
 
     def debug_windows(self, x, stream=None):
         n = x.shape[1]

@@ -81,6 +81,10 @@ CASES = [
                                          2 * math.pi * 20 / 68)), 2000),
     ("odd_x_45x30x20", rep(I.CFG_SMALL, n=(45, 30, 20), kmax=3.0,
                            L=(2 * math.pi, 2 * math.pi * 30 / 45, 2 * math.pi * 20 / 45)), 1500),
+    # sigma_R = 1.5 dx on 24^3: y-tiles of 16 and 8 rows against a halo 9
+    # rows deep, so rows of the thin tile are rims on both sides
+    ("thin_y_tile_24cube_sigma1.5", rep(I.CFG_CLUSTERED, n=(24, 24, 24), n_particles=600,
+                                        n_clusters=5, cluster_std=0.4, kmax=3.0), 600),
     # sigma_R = 2.5 dx: windows of 15-16 nodes, the widest the FP32 x/y-halo
     # tiles take (16 x-weights per particle)
     ("wide_80x48x40_sigma2.5", rep(I.CFG_SMALL, n=(80, 48, 40), kmax=3.0, sigma_over_dx=2.5,
@@ -149,6 +153,34 @@ def test_scatter_reproducible(erpp, name, w, npart):
         assert torch.equal(S1, S2)
 
 
+@pytest.mark.parametrize("kahan", [False, True])
+@pytest.mark.parametrize("name,w,npart", CASES, ids=[c[0] for c in CASES])
+def test_scatter_modes(erpp, oracle_lib, kahan, name, w, npart):
+    """The two ways the FP32 scatter adds tile halos to the neighbours (strips
+    and two merge kernels; the x-halo through thread-block clusters): each
+    matches the oracle, each is reproducible bit for bit, and they differ
+    only by FP32 summation order."""
+    import torch
+    p = w.params()
+    _, st = _setup(w, npart)
+    D = I.make_forces(npart, 1.0, seed=13)
+    ref = oracle_lib.scatter(p, st.x, D)
+    x, Dt = cuda(st.x), cuda(D)
+    out = {}
+    for mode in ("merge", "cluster"):
+        ctx = erpp.Context(p, precision="fp32", kahan=kahan)
+        ctx.set_scatter_mode(mode)
+        S1 = ctx.scatter_source(x, Dt).clone()
+        S2 = ctx.scatter_source(x, Dt)
+        ctx.check()
+        if not kahan:
+            assert torch.equal(S1, S2), mode
+        assert rel(S1.cpu().numpy(), ref) < TOL["fp32"], mode
+        out[mode] = S1.cpu().numpy()
+        ctx.close()
+    assert rel(out["cluster"], out["merge"]) < 1e-6
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_step_launch_count(erpp, precision):
     """The library's own count of the kernels one step launches: FP32 =
@@ -166,7 +198,14 @@ def test_step_launch_count(erpp, precision):
     if precision == "fp64":
         assert n == 3
     else:
-        assert n in (9, 10)  # two merge kernels with x/y-halo tiles, one otherwise
+        # binning 5, gather, advance, scatter, then the halo merges: two
+        # through strips (10), one with the x-halo in clusters (9)
+        assert n == 10
+        for mode, want in (("cluster", 9), ("merge", 10)):
+            ctx.set_scatter_mode(mode)
+            ctx.step(grid_t(grid, precision), ps)
+            ctx.check()
+            assert ctx.last_step_launches() == want, mode
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
