@@ -56,9 +56,11 @@
 // the high word of G W + 2^31 (one wide multiply-add and one atomic per node
 // component).  A tile of one batch sums B from its staged forces, a larger
 // one by a pass over its entries first.  Tiles with more than 1024 pieces add
-// FP32 values instead, and ERPP_KAHAN adds FP32 values with the exact rounding
-// error of each addition (two-sum on the atomic's old value) kept in a second
-// array.  The final values are formed in shared memory and every staged row
+// FP32 values instead.  ERPP_KAHAN (the compensated mode) keeps 47 bits of
+// every exact 64-bit product G W (scale 2^31 / B, one bit finer) in two
+// 32-bit sums per node, the high words and the top bits of the low words: no
+// rounding of the sums, a truncation of each product far below the
+// rounding of its factors.  Tiles of 65536 pieces or more add FP32 values.  The final values are formed in shared memory and every staged row
 // leaves by one bulk asynchronous copy (interior rows to S, y-halo rows to a
 // strip buffer), the x-halo columns by plain stores; k_merge_rows and
 // k_merge_cols then add the strips to the neighbouring tiles in a fixed
@@ -79,6 +81,7 @@ namespace {
 // Threads per block of the tile kernels: 256 or 512 (a tiling option).
 constexpr int kMaxTz = 4;         // z-planes per tile (units per piece)
 constexpr int kDenseTile = 1024;  // pieces above which a tile accumulates in FP32
+constexpr int kSplitMaxPieces = 65535;  // compensated mode: most pieces of a split-word tile
 constexpr uint16_t kEmpty = 0xffffu;
 
 // Pieces per batch: smaller batches for the 16-float x-weight records keep
@@ -241,12 +244,6 @@ template <int OFF>
 __device__ __forceinline__ void red_f32(unsigned a, float v) {
   asm volatile("red.shared.add.f32 [%0+%1], %2;\n" ::"r"(a), "n"(OFF), "f"(v));
 }
-template <int OFF>
-__device__ __forceinline__ float atom_f32(unsigned a, float v) {
-  float old;
-  asm volatile("atom.shared.add.f32 %0, [%1+%2], %3;\n" : "=f"(old) : "r"(a), "n"(OFF), "f"(v));
-  return old;
-}
 __device__ __forceinline__ void red_f32_at(unsigned a, float v) {
   asm volatile("red.shared.add.f32 [%0], %1;\n" ::"r"(a), "f"(v));
 }
@@ -311,29 +308,31 @@ __device__ __forceinline__ void row_red_f32(unsigned a0, unsigned a1, unsigned a
   }
 }
 
-// Compensated: the value the atomic returned gives the exact rounding error
-// of the addition (two-sum), added to the low-order array at offset lo.
+// Compensated mode: the exact 64-bit product G_c(q) W = 2^32 H + L is added
+// as two 32-bit fixed-point words, the signed high word H to the node's high
+// sum and the top 15 bits of the low word L to its low sum (at offset lo):
+// both are sums of at most one term per piece (H below 2^30 + 1, L >> 17
+// below 2^15), which cannot overflow for fewer than 65536 pieces.
 template <int OFF>
-__device__ __forceinline__ void two_sum_add(unsigned a, unsigned lo, float vv) {
-  const float old = atom_f32<OFF>(a, vv);
-  const float s = old + vv;
-  const float bp = s - old;
-  const float err = (old - (s - bp)) + (vv - bp);
-  red_f32<OFF>(lo, err);
+__device__ __forceinline__ void red_split(unsigned a, unsigned lo, int g, int w) {
+  int h;
+  unsigned l;
+  asm("mul.hi.s32 %0, %2, %3;\n\tmul.lo.s32 %1, %2, %3;\n" : "=r"(h), "=r"(l) : "r"(g), "r"(w));
+  red_s32<OFF>(a, h);
+  red_s32<OFF>(a + lo, (int)(l >> 17));
 }
 
 template <int Q, int XM, int LMIN>
-__device__ __forceinline__ void row_red_kahan(unsigned a0, unsigned a1, unsigned a2, unsigned lo,
-                                              const float (&ex)[XM], float f0, float f1, float f2,
-                                              float wy, int lx) {
+__device__ __forceinline__ void row_red_split(unsigned a0, unsigned a1, unsigned a2, unsigned lo,
+                                              const int (&G0)[XM], const int (&G1)[XM],
+                                              const int (&G2)[XM], int W, int lx) {
   if constexpr (Q < XM) {
     if (Q < LMIN || Q < lx) {
-      const float wq = wy * ex[Q];
-      two_sum_add<4 * Q>(a0, a0 + lo, f0 * wq);
-      two_sum_add<4 * Q>(a1, a1 + lo, f1 * wq);
-      two_sum_add<4 * Q>(a2, a2 + lo, f2 * wq);
+      red_split<4 * Q>(a0, lo, G0[Q], W);
+      red_split<4 * Q>(a1, lo, G1[Q], W);
+      red_split<4 * Q>(a2, lo, G2[Q], W);
     }
-    row_red_kahan<Q + 1, XM, LMIN>(a0, a1, a2, lo, ex, f0, f1, f2, wy, lx);
+    row_red_split<Q + 1, XM, LMIN>(a0, a1, a2, lo, G0, G1, G2, W, lx);
   }
 }
 
@@ -755,7 +754,8 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
   }
 }
 
-// MODE 0: fixed point (FP32 atomics on dense tiles); MODE 1: compensated FP32.
+// MODE 0: 32-bit fixed point (FP32 atomics on dense tiles); MODE 1: split
+// high / low fixed-point words (the compensated mode).
 // CL: the launch groups the nt[0] x-tiles of one (y, z) tile row into a
 // thread-block cluster (rank = x-tile): once every block of the row has
 // formed its final values in shared memory, each block adds its x-neighbours'
@@ -773,8 +773,9 @@ struct TileAcc {
 };
 
 // Accumulates the pieces of `tile` into the staged tile in shared memory
-// (cleared first): fixed-point integers, FP32 values on dense tiles, or FP32
-// values with their low-order parts (MODE 1).  Called by the whole block.
+// (cleared first): 32-bit fixed-point integers or FP32 values on dense tiles
+// (MODE 0), or high / low fixed-point sums converted to FP32 in place at the
+// end (MODE 1).  Called by the whole block.
 template <int XM, int LMIN, int XW, int MODE, int NT>
 __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile,
                                                 const Carve<XW>& cv, SchedState& ss, float* red,
@@ -790,7 +791,7 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int plane = kp.plane, px = kp.px, pxy = kp.pxy;
   const bool any = e0 < e1;
-  const bool fixedp = MODE == 0 && (e1 - e0) <= kDenseTile;
+  const bool fixedp = (e1 - e0) <= (MODE == 0 ? kDenseTile : kSplitMaxPieces);
   const int bs = any ? batch_size(e1 - e0, PB) : 1;
   const int4 rfirst = load_rec(entries, e0, min(bs, e1 - e0));  // overlaps the clearing
   float scale = 1.f, inv_scale = 1.f;
@@ -799,11 +800,15 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
     float4* s4 = reinterpret_cast<float4*>(smem);
     for (int k = threadIdx.x; k < total / 4; k += NT) s4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  int wide_sh = 0;  // MODE 1: node sums are in units of 2^-(sh + 31)
   if (any) {
     // Fixed-point scale from the tile's force bound B = sum of max |f| over
-    // its pieces: B = m 2^ex2 (m in [0.5, 1)) gives contributions below
-    // 2^30 in magnitude.  A tile of one batch sums B from the staged forces,
-    // a larger one by a pass over its entries first.
+    // its pieces (a node receives at most one contribution per piece):
+    // B = m 2^ex2 (m in [0.5, 1)) gives factors G below 2^30 (MODE 0: no
+    // 32-bit node sum of the products' high words can overflow) or 2^31
+    // (MODE 1: no 64-bit node sum of the full products can), whatever the
+    // number of pieces.  A tile of one batch sums B from the staged forces, a
+    // larger one by a pass over its entries first.
     const bool single = (e1 - e0) <= PB;
     auto set_scale = [&](float part) {
 #pragma unroll
@@ -816,11 +821,12 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
       if (B > 0.f) {
         int ex2;
         frexpf(B, &ex2);
-        const int sh = min(30 - ex2, 120);
+        const int sh = min((MODE == 1 ? 31 : 30) - ex2, 120);
         scale = ldexpf(1.f, sh);
-        // node sums are in units of scale / 2 (the row weight carries 2^31,
-        // the high word drops 2^32)
+        // MODE 0: node sums are in units of scale / 2 (the row weight carries
+        // 2^31, the high word drops 2^32); MODE 1: in units of 2^-(sh + 31)
         inv_scale = ldexpf(2.f, -sh);
+        wide_sh = sh;
       }
     };
     if (fixedp && !single) {
@@ -879,7 +885,7 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
           f0 = fv.x * wz;
           f1 = fv.y * wz;
           f2 = fv.z * wz;
-          if (MODE == 0 && fixedp) {
+          if (fixedp) {
 #pragma unroll
             for (int q = 0; q < XM; ++q) {
               G0[q] = __float2int_rn(f0 * scale * ex[q]);
@@ -897,7 +903,20 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
         const unsigned aend = abase + px4 * (unsigned)ur.ly;
         unsigned ar = abase + px4 * (unsigned)ur.rot;
         float dy = ur.d0y + (float)ur.rot;
-        if (MODE == 0 && fixedp) {
+        if (MODE == 1 && fixedp) {
+          const unsigned lo = 3u * pl4;  // the low sums follow the three components
+#pragma unroll 1
+          for (int t = 0; t < rows; ++t) {
+            const float e = exp2f(-by * dy * dy);
+            const int W = t < ur.ly ? __float2int_rn(e * 2147483648.f) : 0;
+            row_red_split<0, XM, LMIN>(ar, ar + pl4, ar + 2 * pl4, lo, G0, G1, G2, W, ur.lx);
+            ar += px4;
+            dy += 1.f;
+            const bool wrap = ar == aend;
+            ar = wrap ? abase : ar;
+            dy = wrap ? ur.d0y : dy;
+          }
+        } else if (fixedp) {
 #pragma unroll 1
           for (int t = 0; t < rows; ++t) {
             const float e = exp2f(-by * dy * dy);
@@ -909,7 +928,7 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
             ar = wrap ? abase : ar;
             dy = wrap ? ur.d0y : dy;
           }
-        } else if (MODE == 0) {
+        } else {
 #pragma unroll 1
           for (int t = 0; t < rows; ++t) {
             const float e = exp2f(-by * dy * dy);
@@ -921,22 +940,18 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
             ar = wrap ? abase : ar;
             dy = wrap ? ur.d0y : dy;
           }
-        } else {
-          const unsigned lo = 3u * pl4;  // the low-order array follows the three components
-#pragma unroll 1
-          for (int t = 0; t < rows; ++t) {
-            const float e = exp2f(-by * dy * dy);
-            const float wy = t < ur.ly ? e : 0.f;
-            row_red_kahan<0, XM, LMIN>(ar, ar + pl4, ar + 2 * pl4, lo, ex, f0, f1, f2, wy,
-                                       ur.lx);
-            ar += px4;
-            dy += 1.f;
-            const bool wrap = ar == aend;
-            ar = wrap ? abase : ar;
-            dy = wrap ? ur.d0y : dy;
-          }
         }
       }
+      __syncthreads();
+    }
+    if (MODE == 1 && fixedp) {
+      // high and low sums to FP32 values in place: the node sum is
+      // (2^32 H + 2^17 L) 2^-(sh + 31)
+      int* hi = reinterpret_cast<int*>(smem);
+      const int* lo = hi + 3 * plane;
+      const float s_hi = ldexpf(1.f, 1 - wide_sh), s_lo = ldexpf(1.f, -14 - wide_sh);
+      for (int k = threadIdx.x; k < 3 * plane; k += NT)
+        smem[k] = fmaf((float)hi[k], s_hi, (float)lo[k] * s_lo);
       __syncthreads();
     }
   }
@@ -983,23 +998,12 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
     // the y-strip on a y-halo row) and the hx halo columns of all rows by
     // plain stores (to the x-strip, contiguous per component and plane).
     float4* s4 = reinterpret_cast<float4*>(smem);
-    if (any && (MODE == 1 || fixedp)) {
+    if (any && MODE == 0 && fixedp) {
       const int total4 = 3 * plane / 4;
       for (int k = threadIdx.x; k < total4; k += NT) {
-        float4 v;
-        if (MODE == 1) {
-          v = s4[k];
-          const float4 l = s4[total4 + k];
-          v.x += l.x;
-          v.y += l.y;
-          v.z += l.z;
-          v.w += l.w;
-        } else {
-          const int4 q = reinterpret_cast<const int4*>(smem)[k];
-          v = make_float4((float)q.x * inv_scale, (float)q.y * inv_scale, (float)q.z * inv_scale,
-                          (float)q.w * inv_scale);
-        }
-        s4[k] = v;
+        const int4 q = reinterpret_cast<const int4*>(smem)[k];
+        s4[k] = make_float4((float)q.x * inv_scale, (float)q.y * inv_scale,
+                            (float)q.z * inv_scale, (float)q.w * inv_scale);
       }
     }
     const unsigned fbase = shared_addr(smem);
@@ -1084,8 +1088,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
   const int jobs = nvec + (vec ? 0 : ext[0]) + hx;
   auto value = [&](int idx) -> float {
     if (!any) return 0.f;
-    if (MODE == 1) return smem[idx] + smem[3 * plane + idx];
-    if (fixedp) return (float)acc_i[idx] * inv_scale;
+    if (MODE == 0 && fixedp) return (float)acc_i[idx] * inv_scale;
     return smem[idx];
   };
   for (int cc = 0; cc < 3; ++cc) {
@@ -1111,13 +1114,6 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
                               (float)q.z * inv_scale, (float)q.w * inv_scale);
             } else {
               v = *reinterpret_cast<const float4*>(smem + i0);
-              if (MODE == 1) {
-                const float4 l = *reinterpret_cast<const float4*>(smem + 3 * plane + i0);
-                v.x += l.x;
-                v.y += l.y;
-                v.z += l.z;
-                v.w += l.w;
-              }
             }
             *reinterpret_cast<float4*>(drow + 4 * j) = v;
           } else {
