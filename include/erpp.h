@@ -409,7 +409,7 @@ erpp_status erpp_fluid_destroy(erpp_fluid* fluid);
 erpp_status erpp_set_tiling(erpp_ctx* ctx, int32_t tile_y, int32_t tile_z, int32_t threads);
 
 /* How the FP32 scatter (x/y-halo tiles) adds each tile's halo to its
- * neighbours (a tuning option: both modes compute the same sums up to the
+ * neighbours (a tuning option: every mode computes the same sums up to the
  * order of FP32 additions, and each is reproducible bit for bit):
  *   ERPP_SCATTER_MERGE (default): one block per tile writes its interior to S
  *     and its halo to strips in a context buffer; two merge kernels then add
@@ -421,8 +421,12 @@ erpp_status erpp_set_tiling(erpp_ctx* ctx, int32_t tile_y, int32_t tile_z, int32
  *     Needs rows of at most 8 x-tiles starting on multiples of 4 nodes (nx a
  *     multiple of 4) and a 16-byte aligned S, and enough resources for a
  *     cluster to be resident; otherwise the MERGE form runs.
+ *   ERPP_SCATTER_XCLIP: the binning cuts every x-window at x-tile boundaries
+ *     (a window that crosses one becomes two pieces, one per tile), so no
+ *     tile adds to its x-halo; only the y-halo goes through strips and one
+ *     merge kernel.  The gather uses the same pieces.
  * ERPP_EINVAL for other values. */
-enum { ERPP_SCATTER_MERGE = 0, ERPP_SCATTER_CLUSTER = 1 };
+enum { ERPP_SCATTER_MERGE = 0, ERPP_SCATTER_CLUSTER = 1, ERPP_SCATTER_XCLIP = 2 };
 erpp_status erpp_set_scatter_mode(erpp_ctx* ctx, int32_t mode);
 
 /* out[0] = tile design in use (4: x/y-halo tiles, 3: x-halo tiles cut in y

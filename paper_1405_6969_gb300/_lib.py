@@ -26,7 +26,7 @@ POINT_GATHER = 1 << 6
 LAG = 1 << 7
 FULL_FORCE = 1 << 8
 
-SCATTER_MODES = {"merge": 0, "cluster": 1}
+SCATTER_MODES = {"merge": 0, "cluster": 1, "xclip": 2}
 
 STATUS = {0: "ERPP_OK", 1: "ERPP_EINVAL", 2: "ERPP_ENOMEM", 3: "ERPP_ECUDA",
           4: "ERPP_ERANGE", 5: "ERPP_EBOUNDS", 6: "ERPP_ETIMEOUT", 7: "ERPP_ESTATE"}

@@ -10,7 +10,8 @@ the particle density, so it is
 measured: every candidate runs a few coupling steps (CUDA events, on copies of
 the particle state), then the three fastest shapes are timed again with the
 scatter's x-halo exchanged through thread-block clusters (scatter mode
-"cluster"), and the fastest (shape, mode) is applied and remembered in a JSON
+"cluster") and with the x-windows cut at x-tile boundaries (scatter mode
+"xclip"), and the fastest (shape, mode) is applied and remembered in a JSON
 cache keyed by (grid, r_c / dx, particles per node class, options).  Host
 logic only; every step it times runs in the CUDA library.
 """
@@ -110,15 +111,17 @@ def tune(ctx, u, state, S=None, candidates=CANDIDATES, steps=5, warmup=2, cache_
     for ty, tz, nt in candidates:
         ctx.set_tiling(ty, tz, nt)
         times[f"{ty}x{tz}x{nt}"] = _time_steps(ctx, u, state, S, steps, warmup)
-    ctx.set_scatter_mode("cluster")
-    for name in sorted(times, key=times.get)[:3]:
-        ty, tz, nt = (int(v) for v in name.split("x"))
-        ctx.set_tiling(ty, tz, nt)
-        times[f"{name}xcluster"] = _time_steps(ctx, u, state, S, steps, warmup)
+    top = sorted(times, key=times.get)[:3]
+    for mode in ("cluster", "xclip"):
+        ctx.set_scatter_mode(mode)
+        for name in top:
+            ty, tz, nt = (int(v) for v in name.split("x"))
+            ctx.set_tiling(ty, tz, nt)
+            times[f"{name}x{mode}"] = _time_steps(ctx, u, state, S, steps, warmup)
     best = min(times, key=times.get)
     parts = best.split("x")
     ty, tz, nt = (int(v) for v in parts[:3])
-    mode = "cluster" if len(parts) == 4 else "merge"
+    mode = parts[3] if len(parts) == 4 else "merge"
     ctx.set_tiling(ty, tz, nt)
     ctx.set_scatter_mode(mode)
     if use_cache:

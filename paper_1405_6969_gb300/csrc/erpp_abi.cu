@@ -387,6 +387,10 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
       k4.ystrip_off = ((int64_t)3 * k4.T[2] * (k4.T[1] + hy) * hx + 3) & ~(int64_t)3;
       k4.halo_per_tile = (k4.ystrip_off + (int64_t)3 * k4.T[2] * hy * k4.T[0] + 3) & ~(int64_t)3;
       kp = k4;
+      // x: one piece per window, or two with the windows cut at x-tile
+      // boundaries (room for both, so that the scatter mode can change)
+      kp.xclip = c->scatter_mode == ERPP_SCATTER_XCLIP ? 1 : 0;
+      c->maxseg[0] = max_pieces(n[0], kp.T[0], kp.hlo, kp.xs);
       c->maxseg[1] = 1;
       c->maxseg[2] = max_pieces(n[2], kp.T[2], kp.hlo, kp.xs);
     }
@@ -480,8 +484,11 @@ erpp_status erpp_set_tiling(erpp_ctx* c, int32_t tile_y, int32_t tile_z, int32_t
 }
 
 erpp_status erpp_set_scatter_mode(erpp_ctx* c, int32_t mode) {
-  if (!c || (mode != ERPP_SCATTER_MERGE && mode != ERPP_SCATTER_CLUSTER)) return ERPP_EINVAL;
+  if (!c || (mode != ERPP_SCATTER_MERGE && mode != ERPP_SCATTER_CLUSTER &&
+             mode != ERPP_SCATTER_XCLIP))
+    return ERPP_EINVAL;
   c->scatter_mode = mode;
+  c->kp.xclip = (c->kp.design == 4 && mode == ERPP_SCATTER_XCLIP) ? 1 : 0;
   return ERPP_OK;
 }
 

@@ -58,21 +58,45 @@ __device__ __forceinline__ void for_each_piece(const erpp_kparams& kp, int cx, c
   }
 }
 
-// Design 4: the x- and y-tiles are the ones holding the particle's home cell
-// (tiles are staged with x- and y-halos); only the z-window is cut at tile
-// boundaries and periodic images.  Calls f(tile, jz, ez) per piece.
+// Design 4: the y-tile is the one holding the particle's home cell (tiles are
+// staged with a y-halo); the z-window is cut at tile boundaries and periodic
+// images.  In x the home cell's tile holds the whole window (x-halo tiles), or,
+// with kp.xclip, the x-window is cut at x-tile boundaries and periodic images
+// too, so that every piece stays inside its tile's columns.  Calls
+// f(tile, qa, lx, x0, jz, ez, z0) per piece: window positions [qa, qa + lx)
+// in x starting at staged column x0, planes [jz, ez] (z0 the first plane in
+// the tile).
 template <typename F>
 __device__ __forceinline__ void for_each_piece4(const erpp_kparams& kp, const int c[3],
                                                 const int jlo[3], const int nw[3], F f) {
-  const int tx = c[0] / kp.T[0], ty = c[1] / kp.T[1];
-  const int jhz = jlo[2] + nw[2] - 1;
-  for (int jz = jlo[2]; jz <= jhz;) {
-    const int mz = erpp_floordiv(jz, kp.n[2]);
-    const int wz = jz - mz * kp.n[2];
-    const int tz = wz / kp.T[2];
-    const int ez = min(min((tz + 1) * kp.T[2], kp.n[2]) - wz + jz - 1, jhz);
-    f((tz * kp.nt[1] + ty) * kp.nt[0] + tx, jz, ez, wz - tz * kp.T[2]);
-    jz = ez + 1;
+  const int ty = c[1] / kp.T[1];
+  const int jhx = jlo[0] + nw[0] - 1, jhz = jlo[2] + nw[2] - 1;
+  for (int jx = jlo[0]; jx <= jhx;) {
+    int tx, qa, lx, x0, ex;
+    if (kp.xclip) {
+      const int mx = erpp_floordiv(jx, kp.n[0]);
+      const int wx = jx - mx * kp.n[0];
+      tx = wx / kp.T[0];
+      ex = min(min((tx + 1) * kp.T[0], kp.n[0]) - wx + jx - 1, jhx);
+      qa = jx - jlo[0];
+      lx = ex - jx + 1;
+      x0 = kp.xoff + wx - tx * kp.T[0];
+    } else {
+      tx = c[0] / kp.T[0];
+      ex = jhx;
+      qa = 0;
+      lx = nw[0];
+      x0 = jlo[0] - (tx * kp.T[0] - kp.xoff);
+    }
+    for (int jz = jlo[2]; jz <= jhz;) {
+      const int mz = erpp_floordiv(jz, kp.n[2]);
+      const int wz = jz - mz * kp.n[2];
+      const int tz = wz / kp.T[2];
+      const int ez = min(min((tz + 1) * kp.T[2], kp.n[2]) - wz + jz - 1, jhz);
+      f((tz * kp.nt[1] + ty) * kp.nt[0] + tx, qa, lx, x0, jz, ez, wz - tz * kp.T[2]);
+      jz = ez + 1;
+    }
+    jx = ex + 1;
   }
 }
 
@@ -164,7 +188,7 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
     ++k;
   };
   if (kp.design == 4)
-    for_each_piece4(kp, c, jlo, nw, [&](int tile, int, int, int) { place(tile); });
+    for_each_piece4(kp, c, jlo, nw, [&](int tile, int, int, int, int, int, int) { place(tile); });
   else
     for_each_piece(kp, c[0], jlo, nw, [&](int bin, const PieceSeg&) { place(bin); });
 }
@@ -195,19 +219,21 @@ __global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict_
     return pos;
   };
   if (kp.design == 4) {
-    // record: {p, x0 | y0 << 7 | z0 << 13 | lz << 17 | lx << 22 | ly << 27,
-    //          d0y bits, d0z bits}: x0, y0 the staged x/y index of the
-    // window's first node, z0 its first plane in the tile, lz the planes in
-    // the tile, d0 distances (grid units) of the first y node / first plane
-    const int tx = c[0] / kp.T[0], ty = c[1] / kp.T[1];
-    const int x0 = jlo[0] - (tx * kp.T[0] - kp.xoff);
+    // record: {p, x0 | y0 << 7 | z0 << 13 | lz << 15 | qa << 18 | lx << 22 |
+    //          ly << 27, d0y bits, d0z bits}: x0, y0 the staged x/y index of
+    // the piece's first node, z0 its first plane in the tile, lz the planes in
+    // the tile, [qa, qa + lx) the piece's positions in the particle's
+    // x-window, ly the y-window length, d0 distances (grid units) of the first
+    // y node / first plane
+    const int ty = c[1] / kp.T[1];
     const int y0 = jlo[1] - (ty * kp.T[1] - kp.yhlo);
     const float d0y = (float)(jlo[1] - c[1]) - gt.y;
-    const uint32_t fixed = (uint32_t)x0 | ((uint32_t)y0 << 7) | ((uint32_t)nw[0] << 22) |
-                           ((uint32_t)nw[1] << 27);
-    for_each_piece4(kp, c, jlo, nw, [&](int tile, int jz, int ez, int z0) {
+    const uint32_t fixed = ((uint32_t)y0 << 7) | ((uint32_t)nw[1] << 27);
+    for_each_piece4(kp, c, jlo, nw, [&](int tile, int qa, int lx, int x0, int jz, int ez, int z0) {
       const float d0z = (float)(jz - c[2]) - gt.z;
-      const uint32_t pk = fixed | ((uint32_t)z0 << 13) | ((uint32_t)(ez - jz + 1) << 17);
+      const uint32_t pk = fixed | (uint32_t)x0 | ((uint32_t)z0 << 13) |
+                          ((uint32_t)(ez - jz + 1) << 15) | ((uint32_t)qa << 18) |
+                          ((uint32_t)lx << 22);
       const int64_t pos = place(tile);
       if (pos < cap)
         entries[pos] = make_int4((int)i, (int)pk, __float_as_int(d0y), __float_as_int(d0z));

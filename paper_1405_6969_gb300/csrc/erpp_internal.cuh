@@ -74,6 +74,8 @@ struct erpp_kparams {
   int32_t weights;   // ERPP_W_GAUSS, ERPP_W_PIC or ERPP_W_POINT
   int32_t lag;       // ERPP_LAG: source delay in steps, round(eps_R / dt) >= 1; else 0
   int32_t full_force;// ERPP_FULL_FORCE
+  int32_t xclip;     // design 4: x-windows cut at x-tile boundaries (no x-halo
+                     // contributions, so no x-strips and no column merge)
   int32_t debug_stall;// test hook: after its copies land, the gather also waits
                       // on a barrier that nothing completes (the wait runs out)
   int64_t wait_ns;   // limit of every bounded device-side wait, nanoseconds

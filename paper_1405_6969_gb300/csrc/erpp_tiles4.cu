@@ -92,10 +92,12 @@ struct Batch {
   static constexpr int kUnits = kPB * kMaxTz;
 };
 
-// Piece record (from the binning): p, packed geometry, d0y, d0z.
+// Piece record (from the binning): p, packed geometry, d0y, d0z.  The piece
+// covers positions [qa, qa + lx) of the particle's x-window (qa > 0 or a
+// shorter lx only when the window is cut at x-tile boundaries).
 struct Piece4 {
   int p;
-  int x0, y0, z0, lz, lx, ly;
+  int x0, y0, z0, lz, qa, lx, ly;
   float d0y, d0z;
 };
 
@@ -105,13 +107,39 @@ __device__ __forceinline__ Piece4 unpack4(int4 r) {
   const uint32_t v = (uint32_t)r.y;
   pc.x0 = (int)(v & 127u);
   pc.y0 = (int)((v >> 7) & 63u);
-  pc.z0 = (int)((v >> 13) & 15u);
-  pc.lz = (int)((v >> 17) & 31u);
+  pc.z0 = (int)((v >> 13) & 3u);
+  pc.lz = (int)((v >> 15) & 7u);
+  pc.qa = (int)((v >> 18) & 15u);
   pc.lx = (int)((v >> 22) & 31u);
   pc.ly = (int)(v >> 27);
   pc.d0y = __int_as_float(r.z);
   pc.d0z = __int_as_float(r.w);
   return pc;
+}
+
+// The x-weights of a unit: the piece's x-weight record (XW floats in shared
+// memory, float4 aligned) shifted down by qa (a barrel shift of selects), so
+// that ex[q] weights slot q of the piece; slots from lx on get 0.
+template <int XM, int XW>
+__device__ __forceinline__ void load_ex(const float* xrow, int qa, int lx, float (&ex)[XM]) {
+  float v[XW];
+  const float4* xs = reinterpret_cast<const float4*>(xrow);
+#pragma unroll
+  for (int j = 0; j < XW / 4; ++j) {
+    const float4 t = xs[j];
+    v[4 * j] = t.x;
+    v[4 * j + 1] = t.y;
+    v[4 * j + 2] = t.z;
+    v[4 * j + 3] = t.w;
+  }
+#pragma unroll
+  for (int b = 1; b < XW; b <<= 1) {
+    const bool sh = (qa & b) != 0;
+#pragma unroll
+    for (int q = 0; q < XW; ++q) v[q] = sh ? (q + b < XW ? v[q + b] : 0.f) : v[q];
+  }
+#pragma unroll
+  for (int q = 0; q < XM; ++q) ex[q] = (q < XW && q < lx) ? v[q] : 0.f;
 }
 
 // ---- asynchronous global -> shared copies (cp.async) ----
@@ -261,21 +289,19 @@ __device__ __forceinline__ int mul_hi_round(int g, int w) {
 }
 
 // One row of a unit, slot Q onwards.  Gather: x_c += e_x(q) u_c(q) over the
-// row (words past the window are selected away, not scaled).  Scatter (fixed
-// point): u_c(q) += high word of G_c(q) W.  Scatter (FP32): u_c(q) += f_c w
-// e_x(q).  a0..a2: shared addresses of the row's first node per component.
-template <int Q, int XM, int LMIN>
+// row (the weights of slots past the piece are 0, and every word a slot can
+// reach holds a finite value: staged field, or zeros the gather wrote).
+// Scatter (fixed point): u_c(q) += high word of G_c(q) W.  Scatter (FP32):
+// u_c(q) += f_c w e_x(q).  a0..a2: shared addresses of the row's first node
+// per component.
+template <int Q, int XM>
 __device__ __forceinline__ void row_dot(unsigned a0, unsigned a1, unsigned a2, const float (&ex)[XM],
-                                        int lx, float& x0, float& x1, float& x2) {
+                                        float& x0, float& x1, float& x2) {
   if constexpr (Q < XM) {
-    const bool in = Q < LMIN || Q < lx;
-    const float v0 = lds_f32<4 * Q>(a0);
-    const float v1 = lds_f32<4 * Q>(a1);
-    const float v2 = lds_f32<4 * Q>(a2);
-    x0 = fmaf(ex[Q], in ? v0 : 0.f, x0);
-    x1 = fmaf(ex[Q], in ? v1 : 0.f, x1);
-    x2 = fmaf(ex[Q], in ? v2 : 0.f, x2);
-    row_dot<Q + 1, XM, LMIN>(a0, a1, a2, ex, lx, x0, x1, x2);
+    x0 = fmaf(ex[Q], lds_f32<4 * Q>(a0), x0);
+    x1 = fmaf(ex[Q], lds_f32<4 * Q>(a1), x1);
+    x2 = fmaf(ex[Q], lds_f32<4 * Q>(a2), x2);
+    row_dot<Q + 1, XM>(a0, a1, a2, ex, x0, x1, x2);
   }
 }
 
@@ -350,10 +376,14 @@ struct Carve {
   float* pacc;
 };
 
+// Floats after the staged field that the gather keeps at zero: a unit's last
+// slots may reach past the last staged row.
+constexpr int kFieldPad = 16;
+
 template <int XW>
 __host__ __device__ inline size_t carve_bytes(int plane, int copies, bool gather) {
   constexpr int PB = Batch<XW>::kPB, NU = Batch<XW>::kUnits;
-  size_t b = (size_t)copies * plane * 4;
+  size_t b = ((size_t)copies * plane + kFieldPad) * 4;
   b += (size_t)PB * 16;          // rec
   b += (size_t)PB * XW * 4;      // xwb
   if (!gather) b += (size_t)PB * 16;  // fsb
@@ -370,7 +400,7 @@ __device__ inline Carve<XW> carve(unsigned char* base, int plane, int copies, bo
   Carve<XW> c;
   size_t o = 0;
   c.field = reinterpret_cast<float*>(base);
-  o += (size_t)copies * plane * 4;
+  o += ((size_t)copies * plane + kFieldPad) * 4;
   c.rec = reinterpret_cast<int4*>(base + o);
   o += (size_t)PB * 16;
   c.xwb = reinterpret_cast<float*>(base + o);
@@ -408,8 +438,8 @@ __device__ __forceinline__ void tile_origin4(const erpp_kparams& kp, int tile, i
   }
 }
 
-// Issues the copies that stage the tile with its x/y halo (periodic wrap).
-// Columns outside [xoff - xhlo, xoff + ext_x + xhhi) are never read.
+// Issues the copies that stage the tile with its x/y halo (periodic wrap);
+// the columns outside [xoff - xhlo, xoff + ext_x + xhhi) are set to zero.
 template <int NT>
 __device__ void stage_tile4(const erpp_kparams& kp, const float* __restrict__ u, float* field,
                             const int b[3], const int ext[3]) {
@@ -432,6 +462,9 @@ __device__ void stage_tile4(const erpp_kparams& kp, const float* __restrict__ u,
         gy = gy < 0 ? gy + kp.n[1] : (gy >= kp.n[1] ? gy - kp.n[1] : gy);
         const float* grow = gplane + (size_t)gy * kp.n[0];
         float* srow = splane + y * kp.px;
+        // columns left of and right of the staged range: zeros
+        const int clo = kp.xoff - kp.xhlo, chi = kp.xoff + ext[0] + kp.xhhi;
+        for (int j = lane; j < clo + (kp.px - chi); j += 32) srow[j < clo ? j : chi + (j - clo)] = 0.f;
         for (int j = lane; j < jobs; j += 32) {
           if (j < nvec) {
             cp_async16(srow + kp.xoff + 4 * j, grow + b[0] + 4 * j);
@@ -649,6 +682,23 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
   } else if (!tma) {
     stage_tile4<NT>(kp, u, cv.field, b, ext);
   }
+  {
+    // the unit rows read every slot of the longest window: the words after
+    // each plane's last staged row (up to the next plane) and the pad after
+    // the field are zeroed, so that every word a slot can reach is finite
+    const int ny_st = ext[1] + kp.yhlo + kp.yhhi;
+    const int gap = min(kp.pxy - ny_st * kp.px, kFieldPad);
+    const int nplanes = 3 * ext[2];
+    for (int k = threadIdx.x; k < nplanes * gap + kFieldPad; k += NT) {
+      const int pl = k / max(gap, 1);
+      if (k < nplanes * gap) {
+        const int cc = pl / ext[2], z = pl - cc * ext[2];
+        cv.field[cc * kp.plane + z * kp.pxy + ny_st * kp.px + (k - pl * gap)] = 0.f;
+      } else {
+        cv.field[3 * kp.plane + (k - nplanes * gap)] = 0.f;
+      }
+    }
+  }
   bool staged = false;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int plane = kp.plane, px = kp.px, pxy = kp.pxy;
@@ -694,15 +744,7 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
         k = (int)(w & 1023u);
         const int z = (int)((w >> 10) & 15u);
         const Piece4 pc = unpack4(cv.rec[k]);
-        const float4* xs = reinterpret_cast<const float4*>(cv.xwb + k * XW);
-#pragma unroll
-        for (int j = 0; j < (XM + 3) / 4; ++j) {
-          const float4 v = xs[j];
-          if (4 * j < XM) ex[4 * j] = v.x;
-          if (4 * j + 1 < XM) ex[4 * j + 1] = v.y;
-          if (4 * j + 2 < XM) ex[4 * j + 2] = v.z;
-          if (4 * j + 3 < XM) ex[4 * j + 3] = v.w;
-        }
+        load_ex<XM, XW>(cv.xwb + k * XW, pc.qa, pc.lx, ex);
         ur.base = (pc.z0 + z) * pxy + pc.y0 * px + pc.x0;
         ur.ly = pc.ly;
         ur.lx = pc.lx;
@@ -726,7 +768,7 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
         const float e = exp2f(-fmaf(by * dy, dy, ur.ezz));
         const float wr = t < ur.ly ? e : 0.f;
         float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-        row_dot<0, XM, LMIN>(ar, ar + pl4, ar + 2 * pl4, ex, ur.lx, x0, x1, x2);
+        row_dot<0, XM>(ar, ar + pl4, ar + 2 * pl4, ex, x0, x1, x2);
         a0 = fmaf(wr, x0, a0);
         a1 = fmaf(wr, x1, a1);
         a2 = fmaf(wr, x2, a2);
@@ -865,15 +907,7 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
           const int k = (int)(w & 1023u);
           const int z = (int)((w >> 10) & 15u);
           const Piece4 pc = unpack4(cv.rec[k]);
-          const float4* xs = reinterpret_cast<const float4*>(cv.xwb + k * XW);
-#pragma unroll
-          for (int j = 0; j < (XM + 3) / 4; ++j) {
-            const float4 v = xs[j];
-            if (4 * j < XM) ex[4 * j] = v.x;
-            if (4 * j + 1 < XM) ex[4 * j + 1] = v.y;
-            if (4 * j + 2 < XM) ex[4 * j + 2] = v.z;
-            if (4 * j + 3 < XM) ex[4 * j + 3] = v.w;
-          }
+          load_ex<XM, XW>(cv.xwb + k * XW, pc.qa, pc.lx, ex);
           ur.base = (pc.z0 + z) * pxy + pc.y0 * px + pc.x0;
           ur.ly = pc.ly;
           ur.lx = pc.lx;
@@ -1066,6 +1100,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
       cluster_wait();
       return;
     }
+    if (kp.xclip) return;  // no contributions to the x-halo columns
     const int rpw = 32 / hx;  // staged rows per warp pass
     const int rsub = lane / hx, h = lane - rsub * hx;
     const int col = h < kp.xhlo ? kp.xoff - kp.xhlo + h : kp.xoff + ext[0] + (h - kp.xhlo);
@@ -1085,7 +1120,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
   // everything is aligned, else single words; then the hx halo columns (to
   // the x-strip).
   const int nvec = vec ? ext[0] >> 2 : 0;
-  const int jobs = nvec + (vec ? 0 : ext[0]) + hx;
+  const int jobs = nvec + (vec ? 0 : ext[0]) + (kp.xclip ? 0 : hx);
   auto value = [&](int idx) -> float {
     if (!any) return 0.f;
     if (MODE == 0 && fixedp) return (float)acc_i[idx] * inv_scale;
@@ -1376,8 +1411,13 @@ cudaError_t scatter4_variant(erpp_ctx* ctx, float* S, cudaStream_t st, int varia
     case 1: return scatter4<7, 5, 8, CL>(ctx, S, st);
     case 2: return scatter4<10, 9, 16, CL>(ctx, S, st);
     case 3: return scatter4<10, 8, 16, CL>(ctx, S, st);
-    default: return scatter4<16, 1, 16, CL>(ctx, S, st);
+    default: break;
   }
+  if constexpr (!CL) {  // windows cut at x-tile boundaries (never clustered)
+    if (variant == 5) return scatter4<7, 1, 8, CL>(ctx, S, st);
+    if (variant == 6) return scatter4<10, 1, 16, CL>(ctx, S, st);
+  }
+  return scatter4<16, 1, 16, CL>(ctx, S, st);
 }
 
 // The x-halo exchange through clusters needs whole 16-byte rows (every
@@ -1385,7 +1425,8 @@ cudaError_t scatter4_variant(erpp_ctx* ctx, float* S, cudaStream_t st, int varia
 // and a row of at most 8 x-tiles (the portable cluster size).
 bool cluster_eligible(const erpp_ctx* ctx, const float* S) {
   const erpp_kparams& kp = ctx->kp;
-  return ctx->scatter_mode == ERPP_SCATTER_CLUSTER && kp.nt[0] >= 1 && kp.nt[0] <= 8 &&
+  return ctx->scatter_mode == ERPP_SCATTER_CLUSTER && !kp.xclip && kp.nt[0] >= 1 &&
+         kp.nt[0] <= 8 &&
          (kp.n[0] & 3) == 0 && (kp.T[0] & 3) == 0 && (((uintptr_t)S) & 15) == 0 &&
          (((uintptr_t)ctx->halo) & 15) == 0;
 }
@@ -1398,6 +1439,9 @@ namespace erpp {
 // (cutoff 3 sigma_R at sigma_R = dx; 5-7 when rounding leaves c' just below 3)
 // and 9-10 nodes (sigma_R = 1.5 dx), else a generic form testing every slot.
 int variant4(const erpp_kparams& kp) {
+  // windows cut at x-tile boundaries can be shorter than any window: every
+  // slot is tested
+  if (kp.xclip) return kp.xxs <= 7 ? 5 : (kp.xxs <= 10 ? 6 : 4);
   if (kp.xxs <= 7 && kp.xlmin >= 6) return 0;
   if (kp.xxs <= 7 && kp.xlmin >= 5) return 1;
   if (kp.xxs <= 10 && kp.xlmin >= 9) return 2;
@@ -1417,6 +1461,8 @@ cudaError_t launch_gather_f32_4(erpp_ctx* ctx, const float* u, cudaStream_t st) 
     case 1: return gather4<7, 5, 8>(ctx, u, st);
     case 2: return gather4<10, 9, 16>(ctx, u, st);
     case 3: return gather4<10, 8, 16>(ctx, u, st);
+    case 5: return gather4<7, 1, 8>(ctx, u, st);
+    case 6: return gather4<10, 1, 16>(ctx, u, st);
     default: return gather4<16, 1, 16>(ctx, u, st);
   }
 }
@@ -1433,7 +1479,7 @@ cudaError_t launch_scatter_f32_4(erpp_ctx* ctx, float* S, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   ++ctx->launches;
   k_merge_rows<<<ctx->kp.ntiles, kMergeThreads, 0, st>>>(ctx->kp, S, ctx->halo);
-  if (!clustered) {
+  if (!clustered && !ctx->kp.xclip) {
     ++ctx->launches;
     k_merge_cols<<<ctx->kp.ntiles, kMergeThreads, 0, st>>>(ctx->kp, S, ctx->halo);
   }

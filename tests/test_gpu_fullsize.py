@@ -4,7 +4,8 @@ The homogeneous-shear-like box (4pi x 2pi x 2pi, 512 x 256 x 256 nodes,
 1,000,000 particles, Stokes mix {0.1, 1, 10}, mass loading 0.4, mean shear
 1) and the 256^3 box with 1M particles, in the launch configurations the
 benchmark times (the default tiles, the autotuner's usual pick 16x2x256 and a
-512-thread shape; the fixed-point and the compensated scatter).  One coupling
+512-thread shape; the fixed-point and the compensated scatter; the three
+ways of handling tile halos).  One coupling
 step (gather, self removal, drag, Euler advance, scatter) against the FP64
 oracle over every particle and every node:
 
@@ -68,25 +69,31 @@ def _workload(name, oracle_lib):
     return _CACHE[name]
 
 
-# (workload, tiling T_y x T_z x threads (0 = default), compensated scatter)
+# (workload, tiling T_y x T_z x threads (0 = default), compensated scatter,
+# scatter mode)
 CASES = [
-    ("shear512", (0, 0, 0), False),
-    ("shear512", (16, 2, 256), False),
-    ("shear512", (32, 2, 512), False),
-    ("shear512", (16, 2, 256), True),
-    ("cube256", (0, 0, 0), False),
-    ("cube256", (16, 2, 256), False),
-    ("cube256", (16, 2, 256), True),
+    ("shear512", (0, 0, 0), False, "merge"),
+    ("shear512", (16, 2, 256), False, "merge"),
+    ("shear512", (32, 2, 512), False, "merge"),
+    ("shear512", (16, 2, 256), True, "merge"),
+    ("shear512", (16, 2, 256), False, "xclip"),
+    ("shear512", (16, 2, 256), True, "xclip"),
+    ("shear512", (32, 2, 512), False, "cluster"),
+    ("cube256", (0, 0, 0), False, "merge"),
+    ("cube256", (16, 2, 256), False, "merge"),
+    ("cube256", (16, 2, 256), True, "merge"),
+    ("cube256", (16, 2, 256), False, "xclip"),
 ]
 
 
-@pytest.mark.parametrize("name,tile,kahan", CASES,
-                         ids=[f"{c[0]}-{'x'.join(map(str, c[1]))}-{'kahan' if c[2] else 'fixed'}"
-                              for c in CASES])
-def test_full_size_step(erpp, oracle_lib, name, tile, kahan):
+@pytest.mark.parametrize("name,tile,kahan,mode", CASES,
+                         ids=[f"{c[0]}-{'x'.join(map(str, c[1]))}-"
+                              f"{'kahan' if c[2] else 'fixed'}-{c[3]}" for c in CASES])
+def test_full_size_step(erpp, oracle_lib, name, tile, kahan, mode):
     import torch
     w, p, grid, st, ref, S_ref = _workload(name, oracle_lib)
     ctx = erpp.Context(p, precision="fp32", kahan=kahan)
+    ctx.set_scatter_mode(mode)
     if any(tile):
         ctx.set_tiling(*tile)
     assert ctx.tiling()[0] == 4
@@ -103,7 +110,7 @@ def test_full_size_step(erpp, oracle_lib, name, tile, kahan):
     ctx.check()
     errs = {"S": _rel(S.cpu().numpy(), S_ref), "D": _rel(ps.D.cpu().numpy(), ref.D),
             "v": _rel(ps.v.cpu().numpy(), ref.v)}
-    print(f"\n{name} tiles {ctx.tiling()} kahan={kahan}: " +
+    print(f"\n{name} tiles {ctx.tiling()} kahan={kahan} {mode}: " +
           ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
     assert errs["S"] < TOL and errs["D"] < TOL and errs["v"] < TOL
     np.testing.assert_array_equal(ps.x_prev.cpu().numpy(), st.x)

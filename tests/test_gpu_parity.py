@@ -156,10 +156,10 @@ def test_scatter_reproducible(erpp, name, w, npart):
 @pytest.mark.parametrize("kahan", [False, True])
 @pytest.mark.parametrize("name,w,npart", CASES, ids=[c[0] for c in CASES])
 def test_scatter_modes(erpp, oracle_lib, kahan, name, w, npart):
-    """The two ways the FP32 scatter adds tile halos to the neighbours (strips
-    and two merge kernels; the x-halo through thread-block clusters): each
-    matches the oracle, each is reproducible bit for bit, and they differ
-    only by FP32 summation order."""
+    """The ways the FP32 scatter handles tile halos (strips and two merge
+    kernels; the x-halo through thread-block clusters; x-windows cut at
+    x-tile boundaries, y-halo through strips): each matches the oracle and
+    each is reproducible bit for bit."""
     import torch
     p = w.params()
     _, st = _setup(w, npart)
@@ -167,7 +167,7 @@ def test_scatter_modes(erpp, oracle_lib, kahan, name, w, npart):
     ref = oracle_lib.scatter(p, st.x, D)
     x, Dt = cuda(st.x), cuda(D)
     out = {}
-    for mode in ("merge", "cluster"):
+    for mode in ("merge", "cluster", "xclip"):
         ctx = erpp.Context(p, precision="fp32", kahan=kahan)
         ctx.set_scatter_mode(mode)
         S1 = ctx.scatter_source(x, Dt).clone()
@@ -178,7 +178,28 @@ def test_scatter_modes(erpp, oracle_lib, kahan, name, w, npart):
         assert rel(S1.cpu().numpy(), ref) < TOL["fp32"], mode
         out[mode] = S1.cpu().numpy()
         ctx.close()
+    # the same pieces and scales: only the order of the halo additions differs
+    # (cut windows change each tile's pieces and fixed-point scale, so the
+    # cut form is held to the oracle only)
     assert rel(out["cluster"], out["merge"]) < 1e-6
+
+
+@pytest.mark.parametrize("name,w,npart", CASES, ids=[c[0] for c in CASES])
+def test_step_xclip(erpp, oracle_lib, name, w, npart):
+    """The coupling step with x-windows cut at x-tile boundaries (gather and
+    scatter on the cut pieces) against the oracle."""
+    p = w.params(gravity=(0.0, -9.81, 0.0))
+    grid, st = _setup(w, npart)
+    ctx = erpp.Context(p, precision="fp32")
+    ctx.set_scatter_mode("xclip")
+    ps = erpp.ParticleState.from_numpy(st)
+    S = ctx.step(grid_t(grid, "fp32"), ps, first_step=False)
+    ctx.check()
+    ref = st.copy()
+    S_ref = oracle_lib.step(p, grid, ref, first_step=False)
+    assert rel(S.cpu().numpy(), S_ref) < TOL["fp32"]
+    assert rel(ps.D.cpu().numpy(), ref.D) < TOL["fp32"]
+    assert rel(ps.v.cpu().numpy(), ref.v) < TOL["fp32"]
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
@@ -201,7 +222,7 @@ def test_step_launch_count(erpp, precision):
         # binning 5, gather, advance, scatter, then the halo merges: two
         # through strips (10), one with the x-halo in clusters (9)
         assert n == 10
-        for mode, want in (("cluster", 9), ("merge", 10)):
+        for mode, want in (("cluster", 9), ("xclip", 9), ("merge", 10)):
             ctx.set_scatter_mode(mode)
             ctx.step(grid_t(grid, precision), ps)
             ctx.check()

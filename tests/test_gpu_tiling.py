@@ -96,9 +96,10 @@ def test_autotune_picks_and_caches(erpp, oracle_lib, tmp_path):
     x0 = ps.x.clone()
     path = str(tmp_path / "tune.json")
     r1 = autotune.tune(ctx, u, ps, steps=2, warmup=1, cache_path=path)
-    # every shape with the merge scatter, the three fastest again with clusters
-    assert not r1["cached"] and len(r1["ms"]) == len(autotune.CANDIDATES) + 3
-    assert r1["mode"] in ("merge", "cluster") and ctx.scatter_mode() == r1["mode"]
+    # every shape with the merge scatter, the three fastest again with
+    # clusters and with cut x-windows
+    assert not r1["cached"] and len(r1["ms"]) == len(autotune.CANDIDATES) + 6
+    assert r1["mode"] in ("merge", "cluster", "xclip") and ctx.scatter_mode() == r1["mode"]
     assert torch.equal(ps.x, x0)  # tuning works on copies of the state
     r2 = autotune.tune(ctx, u, ps, cache_path=path)
     assert r2["cached"] and r2["tile"] == r1["tile"] and r2["mode"] == r1["mode"]
