@@ -294,18 +294,23 @@ erpp_status erpp_debug_set_wait(erpp_ctx* ctx, int64_t limit_ns, int32_t stall);
  * Computes exactly what erpp_interpolate computes with an ERPP_FP32 context
  * made from the same params (u is a float grid, u_p n doubles per component),
  * but takes the parameters directly and needs no context: its scratch lives
- * in one fixed 5.2 MiB array inside the library image, which every GPU that
+ * in one fixed 7.2 MiB array inside the library image, which every GPU that
  * loads the library holds until the process exits.  No cudaMalloc, cudaFree
  * or other allocating call is made.
  * Limits: n <= 16384 particles, at most 131072 stencil pieces (n times the
  * largest number of tiles one window can touch) and 4096 grid tiles; larger
  * problems, an ERPP_FP64 flag or invalid params return ERPP_EINVAL before any
- * launch.  Asynchronous on `stream`.  The first call on each device looks up
- * the array's device address with that device current; make that first call
- * before any stream capture.  Every call, from any thread or stream, uses the
- * same array and leaves its contents behind: calls that overlap on the GPU
- * race and must be serialised (one stream, or events).  Positions outside
- * [0, L) are not reported (no error word is readable); their u_p is zero. */
+ * launch.  Asynchronous on `stream`.  The first call in each CUDA context
+ * (per device, and again in a context created later, e.g. after a device
+ * reset) looks up the array's device address with that device current; make
+ * that first call before any stream capture.  With lazy module loading (the
+ * CUDA default) that first call is also when the array is actually placed
+ * in device memory: make a first (warm-up) call before the phase in which
+ * the device memory may be exhausted.  Every call, from any thread or
+ * stream, uses the same array and leaves its contents behind: calls that
+ * overlap on the GPU race and must be serialised (one stream, or events).
+ * Positions outside [0, L) are not reported (no error word is readable);
+ * their u_p is zero. */
 erpp_status erpp_interpolate_noalloc(const erpp_params* params, const void* u, int64_t n,
                                      const double* const x[3], double* const u_p[3],
                                      erpp_stream stream);

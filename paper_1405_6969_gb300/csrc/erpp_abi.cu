@@ -47,6 +47,8 @@ void free_scratch(erpp_ctx* c) {
   cudaFree(c->geo_c);
   cudaFree(c->xw);
   cudaFree(c->up_acc);
+  cudaFree(c->up_part);
+  c->up_part = nullptr;
   cudaFree(c->fscat);
   cudaFree(c->entries);
   cudaFree(c->piece_slot);
@@ -109,6 +111,8 @@ erpp_status ensure_capacity(erpp_ctx* c, int64_t n) {
     if (e == cudaSuccess) e = cudaMalloc(&c->up_acc, sizeof(float) * 3 * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->fscat, sizeof(float4) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->entries, sizeof(int4) * (size_t)ecap);
+    if (e == cudaSuccess && c->kp.design == 4)
+      e = cudaMalloc(&c->up_part, sizeof(float4) * (size_t)ecap);
     if (e == cudaSuccess) e = cudaMalloc(&c->piece_slot, sizeof(int32_t) * (size_t)ecap);
     c->entries_cap = ecap;
   }

@@ -109,7 +109,7 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double xv[3] = {x0[i], x1[i], x2[i]};
-  if (up_acc) {
+  if (up_acc && kp.design != 4) {
     up_acc[i] = 0.f;
     up_acc[acc_stride + i] = 0.f;
     up_acc[2 * acc_stride + i] = 0.f;
@@ -165,7 +165,6 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
     pack |= (uint32_t)(-off[a]) << (4 * a);
     pack |= (uint32_t)nw[a] << (12 + 5 * a);
   }
-  geo_t[i] = make_float4(t[0], t[1], t[2], 0.f);
   geo_c[i] = make_int4(c[0], c[1], c[2], (int)pack);
   const float d0 = (float)off[0] - t[0];
   for (int k = 0; k < xw_len / 4; ++k) {
@@ -191,13 +190,15 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
     for_each_piece4(kp, c, jlo, nw, [&](int tile, int, int, int, int, int, int) { place(tile); });
   else
     for_each_piece(kp, c[0], jlo, nw, [&](int bin, const PieceSeg&) { place(bin); });
+  geo_t[i] = make_float4(t[0], t[1], t[2], __int_as_float(min(k, ms)));
 }
 
 // Writes one record per piece, at its bin's start plus the place the piece
-// took in k_bin_count (pieces visited in the same order).
+// took in k_bin_count (pieces visited in the same order); x/y-halo tiles keep
+// that record position in slot[k][i] for the gather's per-piece sums.
 __global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict__ geo_t,
                            const int4* __restrict__ geo_c, const int32_t* __restrict__ start,
-                           const int32_t* __restrict__ slot, int ms,
+                           int32_t* __restrict__ slot, int ms,
                            int4* __restrict__ entries, int64_t cap, uint32_t* err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -213,8 +214,14 @@ __global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict_
     nw[a] = erpp_geo_nw(pack, a);
   }
   int k = 0;
+  // x/y-halo tiles: each piece's place replaces its place in its bin, for the
+  // gather's per-piece sums
   auto place = [&](int bin) -> int64_t {
-    const int64_t pos = k < ms ? (int64_t)start[bin] + slot[(int64_t)k * n + i] : cap;
+    int64_t pos = cap;
+    if (k < ms) {
+      pos = (int64_t)start[bin] + slot[(int64_t)k * n + i];
+      if (kp.design == 4) slot[(int64_t)k * n + i] = pos < cap ? (int32_t)pos : 0;
+    }
     ++k;
     return pos;
   };

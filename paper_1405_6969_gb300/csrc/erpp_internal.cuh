@@ -1,8 +1,9 @@
 // erpp_internal.cuh -- shared declarations of the ERPP CUDA library.
 //
 // Layout of the per-step data in HBM (FP32 tiled path):
-//   geo_t[i]  float4  (t_x, t_y, t_z, -): fractional position of particle i
-//                     inside its home cell
+//   geo_t[i]  float4  (t_x, t_y, t_z, pieces): fractional position of
+//                     particle i inside its home cell; x/y-halo tiles: the
+//                     number of pieces of its stencil (int bits)
 //   geo_c[i]  int4    (c_x, c_y, c_z, pack): home cell and packed window
 //                     (offset of the first node below the cell, window length)
 //   xw[i]     float[XW] the particle's x-weights 2^(-beta_x d^2) over its
@@ -16,7 +17,11 @@
 //                     A particle belongs to the x-tile of its home cell and
 //                     keeps its whole x-window there (tiles are staged with an
 //                     x-halo); only y and z windows are cut at tile boundaries.
-//   up_acc    float[3][n]  gathered velocity before normalisation
+//   up_acc    float[3][n]  gathered velocity before normalisation (x-halo
+//                     tiles); x/y-halo tiles instead keep each piece's sums
+//                     in up_part[place of the piece's record], and
+//                     piece_slot[k][n] holds the place of particle i's k-th
+//                     piece once the binning is done
 //   fscat[i]  float4  -(1/rho_f) D_i norm / dV, max|component|
 //   halo      float   per tile, the scatter's x-halo columns (left hlo,
 //                     right hhi), [tile][3][T_z][T_y][hlo + hhi]
@@ -127,7 +132,9 @@ struct erpp_ctx {
   int4* geo_c;
   float* xw;              // [cap][xw_len] x-weights per particle
   int xw_len;
-  float* up_acc;          // [3][cap]
+  float* up_acc;          // [3][cap] gathered velocity (x-halo tiles cut in y and z)
+  float4* up_part;        // [entries_cap] x/y-halo tiles: each piece's gathered sums,
+                          // at its place in the piece records
   float4* fscat;
   double* up64;           // FP64 mode or other weights: gathered velocity [3][cap]
   int32_t* w_key;         // other weights: sort key, place and order of each particle [cap]
@@ -163,6 +170,15 @@ constexpr int kProfSets = 1024;
 // Default limit of a bounded device-side wait (a staged tile's copies land
 // within microseconds; the limit only guards against a copy that never does).
 constexpr int64_t kDefaultWaitNs = 250000000;
+
+// Where the FP32 tile gather leaves its sums (see the layout above).
+struct erpp_acc {
+  const float* up_acc;      // x-halo tiles: [3][stride]
+  int64_t stride;
+  const float4* up_part;    // x/y-halo tiles: per piece
+  const int32_t* piece_slot;// [k][n]: place of particle i's k-th piece
+  int64_t n;
+};
 
 // ---- host-side launchers (stream-ordered, no synchronisation) ----
 namespace erpp {
@@ -289,6 +305,30 @@ __device__ __forceinline__ float erpp_norm(const erpp_kparams& kp, float4 gt, in
     prod *= sum;
   }
   return 1.f / prod;
+}
+
+// The gathered sums of particle i (before normalisation): x/y-halo tiles add
+// the sums of its pieces in piece order (deterministic), x-halo tiles read
+// the atomically accumulated sums.
+__device__ __forceinline__ void erpp_gathered(const erpp_kparams& kp, const erpp_acc& acc,
+                                              float4 gt, int64_t i, float out[3]) {
+  if (kp.design == 4) {
+    const int np = __float_as_int(gt.w);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (int k = 0; k < np; ++k) {
+      const float4 v = acc.up_part[acc.piece_slot[(int64_t)k * acc.n + i]];
+      a0 += v.x;
+      a1 += v.y;
+      a2 += v.z;
+    }
+    out[0] = a0;
+    out[1] = a1;
+    out[2] = a2;
+  } else {
+    out[0] = acc.up_acc[i];
+    out[1] = acc.up_acc[acc.stride + i];
+    out[2] = acc.up_acc[2 * acc.stride + i];
+  }
 }
 
 __device__ __forceinline__ int erpp_floordiv(int a, int n) {

@@ -34,7 +34,8 @@ constexpr size_t kOffCnt = kOffEntries + align256(16 * kNoallocPieces);
 constexpr size_t kOffStart = kOffCnt + align256(4 * kNoallocBins);
 constexpr size_t kOffSlot = kOffStart + align256(4 * (kNoallocBins + 1));
 constexpr size_t kOffScan = kOffSlot + align256(4 * kNoallocPieces);
-constexpr size_t kOffErr = kOffScan + align256(4 * (kNoallocBins / 4096 + 1));
+constexpr size_t kOffPart = kOffScan + align256(4 * (kNoallocBins / 4096 + 1));
+constexpr size_t kOffErr = kOffPart + align256(16 * kNoallocPieces);
 constexpr size_t kScratchBytes = kOffErr + 256;
 
 // Held by every GPU that loads the library, until the process exits.
@@ -43,21 +44,56 @@ static_assert(kScratchBytes < 10u * 1024u * 1024u, "no-alloc scratch must stay m
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// Per device: the unique id of the CUDA context the address was looked up in,
+// and the address.  A context created later on the same device (after a
+// reset, or another context) has another id and its own copy of the array.
+unsigned long long g_ctx_id[kMaxDevices] = {0};
 unsigned char* g_dev_addr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch on the current device (looked up once per
-// device, with that device current).
+typedef int (*ctx_get_current_fn)(void**);
+typedef int (*ctx_get_id_fn)(void*, unsigned long long*);
+
+// Unique id of the calling thread's current CUDA context (driver entry points
+// through the runtime, no link against the driver library); 0 when unknown.
+unsigned long long current_ctx_id() {
+  static ctx_get_current_fn get_current = nullptr;
+  static ctx_get_id_fn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<ctx_get_current_fn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<ctx_get_id_fn>(p);
+    cudaGetLastError();
+  });
+  if (!get_current || !get_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch in the current context, looked up (with the
+// device current) the first time each context calls; without a context id
+// the address is looked up on every call.
 cudaError_t scratch_address(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  const unsigned long long id = current_ctx_id();
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_dev_addr[dev]) {
+  if (id == 0 || g_ctx_id[dev] != id || !g_dev_addr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_dev_addr[dev] = (unsigned char*)p;
+    g_ctx_id[dev] = id;
   }
   *out = g_dev_addr[dev];
   return cudaSuccess;
@@ -95,6 +131,7 @@ extern "C" erpp_status erpp_interpolate_noalloc(const erpp_params* params, const
   c.tile_start = reinterpret_cast<int32_t*>(base + kOffStart);
   c.piece_slot = reinterpret_cast<int32_t*>(base + kOffSlot);
   c.scan_tmp = reinterpret_cast<int32_t*>(base + kOffScan);
+  c.up_part = reinterpret_cast<float4*>(base + kOffPart);
   c.err = reinterpret_cast<uint32_t*>(base + kOffErr);
   cudaStream_t st = (cudaStream_t)stream;
   // The per-tile counts are cleared by the binning itself and the gather

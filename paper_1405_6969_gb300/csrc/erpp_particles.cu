@@ -284,8 +284,7 @@ __global__ void __launch_bounds__(256) k_advance_full(erpp_kparams kp, int64_t n
 // velocity and position updates themselves stay in FP64.
 template <bool FROM_ACC, bool F32>
 __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, PartPtrs P,
-                                                 UpPtrs U, const float* __restrict__ up_acc,
-                                                 int64_t acc_stride,
+                                                 UpPtrs U, erpp_acc acc,
                                                  const float4* __restrict__ geo_t,
                                                  const int4* __restrict__ geo_c,
                                                  float4* __restrict__ fscat, int first_step) {
@@ -303,9 +302,11 @@ __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, Par
   float upf[3] = {0.f, 0.f, 0.f};
   float norm = 0.f;
   if (FROM_ACC) {
-    norm = erpp_norm(kp, geo_t[i], geo_c[i]);
+    const float4 gt = geo_t[i];
+    norm = erpp_norm(kp, gt, geo_c[i]);
+    erpp_gathered(kp, acc, gt, i, upf);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) upf[a] = up_acc[a * acc_stride + i] * norm;
+    for (int a = 0; a < 3; ++a) upf[a] *= norm;
   } else {
 #pragma unroll
     for (int a = 0; a < 3; ++a) up[a] = U.up[a][i];
@@ -386,16 +387,29 @@ __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, Par
   }
 }
 
-__global__ void k_finalize_up(erpp_kparams kp, int64_t n, const float* __restrict__ up_acc,
-                              int64_t acc_stride, const float4* __restrict__ geo_t,
-                              const int4* __restrict__ geo_c, const double* __restrict__ y,
-                              double* up0, double* up1, double* up2) {
+__global__ void k_finalize_up(erpp_kparams kp, int64_t n, erpp_acc acc,
+                              const float4* __restrict__ geo_t, const int4* __restrict__ geo_c,
+                              const double* __restrict__ y, double* up0, double* up1,
+                              double* up2) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const float norm = erpp_norm(kp, geo_t[i], geo_c[i]);
-  up0[i] = (double)(up_acc[i] * norm) + kp.shear_rate * y[i];
-  up1[i] = (double)(up_acc[acc_stride + i] * norm);
-  up2[i] = (double)(up_acc[2 * acc_stride + i] * norm);
+  const float4 gt = geo_t[i];
+  const float norm = erpp_norm(kp, gt, geo_c[i]);
+  float g[3];
+  erpp_gathered(kp, acc, gt, i, g);
+  up0[i] = (double)(g[0] * norm) + kp.shear_rate * y[i];
+  up1[i] = (double)(g[1] * norm);
+  up2[i] = (double)(g[2] * norm);
+}
+
+erpp_acc acc_of(const erpp_ctx* ctx, int64_t n) {
+  erpp_acc a;
+  a.up_acc = ctx->up_acc;
+  a.stride = ctx->cap;
+  a.up_part = ctx->up_part;
+  a.piece_slot = ctx->piece_slot;
+  a.n = n;
+  return a;
 }
 
 __global__ void k_prep_fscat(erpp_kparams kp, int64_t n, const double* __restrict__ D0,
@@ -541,13 +555,13 @@ cudaError_t launch_advance(erpp_ctx* ctx, const erpp_particles* P, const double*
   const bool f32 = !ctx->fp64;
   ++ctx->launches;
   if (from_acc) {
-    k_advance<true, true><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, ctx->up_acc, ctx->cap,
-                                                  ctx->geo_t, ctx->geo_c, fs, first_step);
+    k_advance<true, true><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, acc_of(ctx, n), ctx->geo_t,
+                                                  ctx->geo_c, fs, first_step);
   } else if (f32) {
-    k_advance<false, true><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, nullptr, 0, nullptr,
+    k_advance<false, true><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, erpp_acc{}, nullptr,
                                                    nullptr, nullptr, first_step);
   } else {
-    k_advance<false, false><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, nullptr, 0, nullptr,
+    k_advance<false, false><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, erpp_acc{}, nullptr,
                                                     nullptr, nullptr, first_step);
   }
   return cudaGetLastError();
@@ -601,8 +615,8 @@ cudaError_t launch_finalize_up(erpp_ctx* ctx, int64_t n, const double* const x[3
                                double* const up[3], cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int blocks = (int)((n + 255) / 256);
-  k_finalize_up<<<blocks, 256, 0, st>>>(ctx->kp, n, ctx->up_acc, ctx->cap, ctx->geo_t,
-                                        ctx->geo_c, x[1], up[0], up[1], up[2]);
+  k_finalize_up<<<blocks, 256, 0, st>>>(ctx->kp, n, acc_of(ctx, n), ctx->geo_t, ctx->geo_c,
+                                        x[1], up[0], up[1], up[2]);
   return cudaGetLastError();
 }
 

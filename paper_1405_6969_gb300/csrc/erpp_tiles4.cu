@@ -46,8 +46,9 @@
 // e_x the particle's x-weights (precomputed by the binning), d in grid units.
 //
 // Gather: a lane sums w*u over its unit, adds the three totals to the piece's
-// shared accumulator, and the block adds the piece accumulators to the
-// particle's global accumulator once per batch.
+// shared accumulator, and the block stores each piece's sums at the place of
+// its record; the particle adds its pieces in piece order afterwards (no
+// global atomics, so the gathered velocity is reproducible bit for bit).
 //
 // Scatter: 32-bit fixed point with shared-memory integer atomics (order
 // independent), per-tile scale 2^30 / B with B = sum over the tile's pieces of
@@ -640,8 +641,7 @@ template <int XM, int LMIN, int XW, int NT>
 __global__ void __launch_bounds__(NT, 2) k_gather4(
     erpp_kparams kp, const float* __restrict__ u, const __grid_constant__ CUtensorMap tmap,
     int use_tma, const int32_t* __restrict__ start, const int4* __restrict__ entries,
-    int64_t ecap, const float* __restrict__ xw, float* __restrict__ up_acc, int64_t acc_stride,
-    uint32_t* err) {
+    int64_t ecap, const float* __restrict__ xw, float4* __restrict__ up_part, uint32_t* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SchedState ss;
   __shared__ __align__(8) uint64_t tma_bar;
@@ -786,12 +786,10 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
       }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < np; k += NT) {
-      const int p = cv.rec[k].x;
-      atomicAdd(up_acc + p, cv.pacc[k]);
-      atomicAdd(up_acc + acc_stride + p, cv.pacc[PB + k]);
-      atomicAdd(up_acc + 2 * acc_stride + p, cv.pacc[2 * PB + k]);
-    }
+    // each piece's sums at the place of its record (the particle adds its
+    // pieces later, in piece order)
+    for (int k = threadIdx.x; k < np; k += NT)
+      up_part[b0 + k] = make_float4(cv.pacc[k], cv.pacc[PB + k], cv.pacc[2 * PB + k], 0.f);
     __syncthreads();
   }
 }
@@ -1342,7 +1340,7 @@ cudaError_t gather4_nt(erpp_ctx* ctx, const float* u, cudaStream_t st) {
   ++ctx->launches;
   k_gather4<XM, LMIN, XW, NT><<<kp.ntiles, NT, sm, st>>>(kp, u, map, use_tma, ctx->tile_start,
                                                          ctx->entries, ctx->entries_cap, ctx->xw,
-                                                         ctx->up_acc, ctx->cap, ctx->err);
+                                                         ctx->up_part, ctx->err);
   return cudaGetLastError();
 }
 

@@ -13,7 +13,7 @@ oracle over every particle and every node:
 * the source S, the forces D and the velocities v within the FP32
   tolerance (1e-5 relative L2), x_prev bit-exact, x within the bound of the
   FP64 integration of those velocities;
-* repeated fixed-point scatters of the same forces bit-identical.
+* the step repeated from the same state bit-identical (fixed-point scatter).
 
 The oracle runs on the host cores (``oracle.step_threads``: the unchanged
 oracle step on particle chunks, partial sources summed), once per workload.
@@ -119,15 +119,15 @@ def test_full_size_step(erpp, oracle_lib, name, tile, kahan, mode):
     dxp = np.minimum(dxp, np.array(w.L)[:, None] - dxp)
     assert dxp.max() < 1e-12 * 10 * max(w.L)
     if not kahan:
-        # the scatter of the same forces at the same positions, twice: the
-        # fixed-point sums and the fixed merge order give the same bits (the
-        # step as a whole is not bit-reproducible: the gather adds a
-        # particle's pieces with FP32 atomics in arrival order)
-        S1 = ctx.scatter_source(ps.x_prev, ps.D).clone()
-        ctx.scatter_source(ps.x_prev, ps.D, S=S)
+        # the same step again from the same state: the per-piece gather sums
+        # added in piece order, the fixed-point scatter sums and the fixed
+        # merge order give the same bits
+        S1, D1 = S.clone(), ps.D.clone()
+        ps = erpp.ParticleState.from_numpy(st)
+        ctx.step(u, ps, S=S, first_step=False)
         ctx.check()
-        assert torch.equal(S, S1)
-        del S1
+        assert torch.equal(S, S1) and torch.equal(ps.D, D1)
+        del S1, D1
     del S, u, ps
     ctx.close()
     torch.cuda.empty_cache()

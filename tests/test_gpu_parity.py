@@ -202,6 +202,27 @@ def test_step_xclip(erpp, oracle_lib, name, w, npart):
     assert rel(ps.v.cpu().numpy(), ref.v) < TOL["fp32"]
 
 
+@pytest.mark.parametrize("name,w,npart", CASES, ids=[c[0] for c in CASES])
+def test_step_reproducible(erpp, name, w, npart):
+    """The whole FP32 step is reproducible bit for bit: the gather stores
+    each piece's sums at its record and every particle adds its pieces in
+    piece order, and the scatter's fixed-point sums do not depend on the
+    order of the pieces."""
+    import torch
+    p = w.params()
+    grid, st = _setup(w, npart)
+    ctx = erpp.Context(p, precision="fp32")
+    u = grid_t(grid, "fp32")
+    out = []
+    for _ in range(2):
+        ps = erpp.ParticleState.from_numpy(st)
+        S = ctx.step(u, ps, first_step=False)
+        ctx.check()
+        out.append((S.clone(), ps.D.clone(), ps.v.clone(), ps.x.clone()))
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_step_launch_count(erpp, precision):
     """The library's own count of the kernels one step launches: FP32 =
