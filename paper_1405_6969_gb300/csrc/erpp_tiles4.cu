@@ -45,10 +45,11 @@
 // Weights are separable, w = e_x(q) * 2^(-(beta_y d_y^2 + beta_z d_z^2)) with
 // e_x the particle's x-weights (precomputed by the binning), d in grid units.
 //
-// Gather: a lane sums w*u over its unit, adds the three totals to the piece's
-// shared accumulator, and the block stores each piece's sums at the place of
-// its record; the particle adds its pieces in piece order afterwards (no
-// global atomics, so the gathered velocity is reproducible bit for bit).
+// Gather: a lane sums w*u over its unit and stores the three totals in the
+// unit's own (piece, plane) slot; the block adds each piece's planes in
+// plane order and stores the sums at the place of the piece's record, and the
+// particle adds its pieces in piece order afterwards (no atomics, so the
+// gathered velocity is reproducible bit for bit).
 //
 // Scatter: 32-bit fixed point with shared-memory integer atomics (order
 // independent), per-tile scale 2^30 / B with B = sum over the tile's pieces of
@@ -273,9 +274,6 @@ template <int OFF>
 __device__ __forceinline__ void red_f32(unsigned a, float v) {
   asm volatile("red.shared.add.f32 [%0+%1], %2;\n" ::"r"(a), "n"(OFF), "f"(v));
 }
-__device__ __forceinline__ void red_f32_at(unsigned a, float v) {
-  asm volatile("red.shared.add.f32 [%0], %1;\n" ::"r"(a), "f"(v));
-}
 
 // round(g w / 2^32) = high word of g w + 2^31: the low word of the product
 // plus 2^31 (carry out), then the signed high word plus that carry.
@@ -391,7 +389,7 @@ __host__ __device__ inline size_t carve_bytes(int plane, int copies, bool gather
   b += (size_t)NU * 4;           // unit
   b += (size_t)NU * 2;           // sched
   b = (b + 15) & ~(size_t)15;
-  if (gather) b += (size_t)3 * PB * 4;  // pacc
+  if (gather) b += (size_t)3 * kMaxTz * PB * 4;  // pacc
   return b;
 }
 
@@ -703,11 +701,10 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int plane = kp.plane, px = kp.px, pxy = kp.pxy;
   const float by = kp.beta[1], bz = kp.beta[2];
-  const unsigned fbase = shared_addr(cv.field), pbase = shared_addr(cv.pacc);
+  const unsigned fbase = shared_addr(cv.field);
   for (int b0 = e0; b0 < e1; b0 += bs) {
     const int np = min(bs, e1 - b0);
     stage_batch<XW, false>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, xw, nullptr);
-    for (int k = threadIdx.x; k < 3 * PB; k += NT) cv.pacc[k] = 0.f;
     const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
     cp_async_wait_all();                            // field (first batch), x-weights
     // One thread waits (bounded) for the staged field; the block learns the
@@ -735,7 +732,7 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
       const uint16_t ui = cv.sched[r * NT + warp * 32 + lane];
       const bool active = ui != kEmpty;
       UnitRows ur = {0, 0, 0, 0, 0.f, 0.f};
-      int k = 0;
+      int k = 0, uz = 0;
       float ex[XM];
 #pragma unroll
       for (int q = 0; q < XM; ++q) ex[q] = 0.f;
@@ -743,6 +740,7 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
         const uint32_t w = cv.unit[ui];
         k = (int)(w & 1023u);
         const int z = (int)((w >> 10) & 15u);
+        uz = z;
         const Piece4 pc = unpack4(cv.rec[k]);
         load_ex<XM, XW>(cv.xwb + k * XW, pc.qa, pc.lx, ex);
         ur.base = (pc.z0 + z) * pxy + pc.y0 * px + pc.x0;
@@ -756,8 +754,10 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
       const int rows = __reduce_max_sync(0xffffffffu, (unsigned)ur.ly);
       // Straight-line rows: rows past the unit's own length get weight 0,
       // the rotated walk wraps by a select.  Empty lanes read from column
-      // `lane` (their own bucket) and their sums are dropped.
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      // `lane` (their own bucket) and their sums are dropped.  Rows 1.. are
+      // summed in row order and the first row's term is added at the end, so
+      // that the unit's sum does not depend on where its walk started.
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, r0 = 0.f, r1 = 0.f, r2 = 0.f;
       const unsigned pl4 = 4u * (unsigned)plane, px4 = 4u * (unsigned)px;
       const unsigned abase = fbase + 4u * (unsigned)(active ? ur.base : lane);
       const unsigned aend = abase + px4 * (unsigned)ur.ly;
@@ -766,12 +766,19 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
 #pragma unroll 1
       for (int t = 0; t < rows; ++t) {
         const float e = exp2f(-fmaf(by * dy, dy, ur.ezz));
-        const float wr = t < ur.ly ? e : 0.f;
+        const bool in = t < ur.ly;
+        const float wr = in ? e : 0.f;
         float x0 = 0.f, x1 = 0.f, x2 = 0.f;
         row_dot<0, XM>(ar, ar + pl4, ar + 2 * pl4, ex, x0, x1, x2);
-        a0 = fmaf(wr, x0, a0);
-        a1 = fmaf(wr, x1, a1);
-        a2 = fmaf(wr, x2, a2);
+        if (in && ar == abase) {
+          r0 = wr * x0;
+          r1 = wr * x1;
+          r2 = wr * x2;
+        } else {
+          a0 = fmaf(wr, x0, a0);
+          a1 = fmaf(wr, x1, a1);
+          a2 = fmaf(wr, x2, a2);
+        }
         ar += px4;
         dy += 1.f;
         const bool wrap = ar == aend;
@@ -779,17 +786,27 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
         dy = wrap ? ur.d0y : dy;
       }
       if (active) {
-        const unsigned pa = pbase + 4u * (unsigned)k;
-        red_f32_at(pa, a0);
-        red_f32_at(pa + 4u * PB, a1);
-        red_f32_at(pa + 8u * PB, a2);
+        // the unit's own slot (piece k, plane uz): no two units share one
+        float* pa = cv.pacc + uz * PB + k;
+        pa[0] = a0 + r0;
+        pa[kMaxTz * PB] = a1 + r1;
+        pa[2 * kMaxTz * PB] = a2 + r2;
       }
     }
     __syncthreads();
-    // each piece's sums at the place of its record (the particle adds its
-    // pieces later, in piece order)
-    for (int k = threadIdx.x; k < np; k += NT)
-      up_part[b0 + k] = make_float4(cv.pacc[k], cv.pacc[PB + k], cv.pacc[2 * PB + k], 0.f);
+    // each piece's sums, its planes added in plane order, at the place of its
+    // record (the particle adds its pieces later, in piece order): the result
+    // does not depend on the order in which units ran
+    for (int k = threadIdx.x; k < np; k += NT) {
+      const int lz = unpack4(cv.rec[k]).lz;
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+      for (int z = 0; z < lz; ++z) {
+        s0 += cv.pacc[z * PB + k];
+        s1 += cv.pacc[(kMaxTz + z) * PB + k];
+        s2 += cv.pacc[(2 * kMaxTz + z) * PB + k];
+      }
+      up_part[b0 + k] = make_float4(s0, s1, s2, 0.f);
+    }
     __syncthreads();
   }
 }
@@ -850,14 +867,35 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
     // number of pieces.  A tile of one batch sums B from the staged forces, a
     // larger one by a pass over its entries first.
     const bool single = (e1 - e0) <= PB;
-    auto set_scale = [&](float part) {
+    // B is summed exactly, so that it (and the scale) does not depend on the
+    // order of the tile's pieces: the block first takes the largest max|f|,
+    // then adds every piece's max|f| as a fixed-point integer scaled to it
+    // (each below 2^29, summed in 64 bits).
+    // get(j) reads the j-th value of this thread, for j < cnt.
+    auto set_scale = [&](auto get, int cnt) {
+      float m = 0.f;
+      for (int j = 0; j < cnt; ++j) m = fmaxf(m, get(j));
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      if (lane == 0) red[warp] = part;
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) red[warp] = m;
       __syncthreads();
-      float B = 0.f;
+      float mx = 0.f;
 #pragma unroll
-      for (int w = 0; w < NW; ++w) B += red[w];
+      for (int w = 0; w < NW; ++w) mx = fmaxf(mx, red[w]);
+      __syncthreads();
+      int emx = 0;
+      frexpf(mx, &emx);
+      long long q = 0;
+      if (mx > 0.f)
+        for (int j = 0; j < cnt; ++j) q += __float2int_rn(ldexpf(get(j), 29 - emx));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      if (lane == 0) reinterpret_cast<long long*>(red)[warp] = q;
+      __syncthreads();
+      long long qs = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) qs += reinterpret_cast<long long*>(red)[w];
+      const float B = ldexpf(__ll2float_rn(qs), emx - 29);
       if (B > 0.f) {
         int ex2;
         frexpf(B, &ex2);
@@ -870,10 +908,9 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
       }
     };
     if (fixedp && !single) {
-      float bsum = 0.f;
-      for (int e = e0 + threadIdx.x; e < e1; e += NT)
-        bsum += __ldg(&fscat[__ldg(&entries[e].x)]).w;
-      set_scale(bsum);
+      const int cnt = (e1 - e0 - (int)threadIdx.x + NT - 1) / NT;
+      set_scale([&](int j) { return __ldg(&fscat[__ldg(&entries[e0 + threadIdx.x + j * NT].x)]).w; },
+                max(cnt, 0));
     }
     const float by = kp.beta[1], bz = kp.beta[2];
     const unsigned fbase = shared_addr(smem);
@@ -884,9 +921,8 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
       cp_async_wait_all();
       __syncthreads();
       if (fixedp && single) {
-        float bsum = 0.f;
-        for (int k = threadIdx.x; k < np; k += NT) bsum += cv.fsb[k].w;
-        set_scale(bsum);
+        const int cnt = (np - (int)threadIdx.x + NT - 1) / NT;
+        set_scale([&](int j) { return cv.fsb[threadIdx.x + j * NT].w; }, max(cnt, 0));
       }
       for (int r = 0; r < R; ++r) {
         const uint16_t ui = cv.sched[r * NT + warp * 32 + lane];
@@ -998,7 +1034,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SchedState ss;
   constexpr int NW = NT / 32;
-  __shared__ float red[NW];
+  __shared__ __align__(8) float red[2 * NW];  // per-warp partials (8-byte ones too)
   constexpr int PB = Batch<XW>::kPB;
   static_assert(PB <= NT, "a batch holds at most one piece per thread");
   const int tile = blockIdx.x;
