@@ -268,8 +268,12 @@ erpp_status erpp_check(erpp_ctx* ctx, erpp_stream stream);
 
 /* Stencil windows as the kernels compute them: for each particle and axis,
  * the first and last node index (unwrapped, may be < 0 or >= N) whose
- * distance from x is at most cutoff * sigma_R.  jlo, jhi: device int32
- * arrays of 3*n (component-major). */
+ * distance from x is at most cutoff * sigma_R (Sec. 2.4, truncated support).
+ * jlo, jhi: device int32 arrays of 3*n (component-major).  The binning takes
+ * the window with one FP64 product and exact integer/FP32 work; this call
+ * also evaluates the plain FP64 form and writes INT32_MIN to both ends of any
+ * axis where the two disagree in the home cell, the ends or the fractional
+ * position (a self-check that is never expected to fire). */
 erpp_status erpp_debug_windows(erpp_ctx* ctx, int64_t n, const double* const x[3],
                                int32_t* jlo, int32_t* jhi, erpp_stream stream);
 

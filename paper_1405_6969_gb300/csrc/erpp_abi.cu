@@ -48,7 +48,9 @@ void free_scratch(erpp_ctx* c) {
   cudaFree(c->xw);
   cudaFree(c->up_acc);
   cudaFree(c->up_part);
+  cudaFree(c->fs_piece);
   c->up_part = nullptr;
+  c->fs_piece = nullptr;
   cudaFree(c->fscat);
   cudaFree(c->entries);
   cudaFree(c->piece_slot);
@@ -113,6 +115,8 @@ erpp_status ensure_capacity(erpp_ctx* c, int64_t n) {
     if (e == cudaSuccess) e = cudaMalloc(&c->entries, sizeof(int4) * (size_t)ecap);
     if (e == cudaSuccess && c->kp.design == 4)
       e = cudaMalloc(&c->up_part, sizeof(float4) * (size_t)ecap);
+    if (e == cudaSuccess && c->kp.design == 4)
+      e = cudaMalloc(&c->fs_piece, sizeof(float4) * (size_t)ecap);
     if (e == cudaSuccess) e = cudaMalloc(&c->piece_slot, sizeof(int32_t) * (size_t)ecap);
     c->entries_cap = ecap;
   }
@@ -240,6 +244,8 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
     kp.inv_dx[a] = (double)n[a] / L[a];
     kp.dx[a] = L[a] / (double)n[a];
     kp.cp[a] = rc * kp.inv_dx[a];
+    kp.cp_int[a] = (int)floor(kp.cp[a]);
+    kp.cp_frac[a] = (float)(kp.cp[a] - floor(kp.cp[a]));
     if (!(2.0 * rc < L[a])) return ERPP_EINVAL;
     cpmax = std::max(cpmax, kp.cp[a]);
   }

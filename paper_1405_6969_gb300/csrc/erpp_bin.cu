@@ -127,15 +127,14 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
   if (ok) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      // the FP64 window of erpp_axis_window, with each rounding to an
-      // integer done by the conversion itself
-      const double s = __dmul_rn(xv[a], kp.inv_dx[a]);
-      int ci = __double2int_rd(s);
-      const int lo = __double2int_ru(__dadd_rn(s, -kp.cp[a]));
-      const int hi = __double2int_rd(__dadd_rn(s, kp.cp[a]));
-      off[a] = lo - ci;
-      nw[a] = hi - lo + 1;
-      t[a] = __double2float_rn(__dadd_rn(s, -(double)ci));
+      // the window of erpp_axis_window (one FP64 product, the rest exact
+      // integer and FP32 work)
+      const erpp_axis_win aw =
+          erpp_axis_window_lean(xv[a], kp.inv_dx[a], kp.cp[a], kp.cp_int[a], kp.cp_frac[a]);
+      int ci = aw.ci;
+      off[a] = aw.lo - ci;
+      nw[a] = aw.hi - aw.lo + 1;
+      t[a] = aw.t;
       // s can round up to exactly N for x just below L: the cell is then the
       // first one of the next image, which is the same node set shifted by N.
       if (ci >= kp.n[a]) ci -= kp.n[a];
@@ -152,11 +151,13 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
   } else {
     erpp_set_err(err, ERPP_ERRBIT_RANGE);
   }
-  float4* xw4 = reinterpret_cast<float4*>(xw + (size_t)i * xw_len);
+  // x-halo tiles: the particle's x-weights (x/y-halo tiles take them from
+  // the piece records; xw is null then)
+  float4* xw4 = xw ? reinterpret_cast<float4*>(xw + (size_t)i * xw_len) : nullptr;
   if (!ok) {
     geo_t[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     geo_c[i] = make_int4(0, 0, 0, 0);
-    for (int k = 0; k < xw_len / 4; ++k) xw4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; xw4 && k < xw_len / 4; ++k) xw4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
   uint32_t pack = ERPP_GEO_VALID;
@@ -167,7 +168,7 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
   }
   geo_c[i] = make_int4(c[0], c[1], c[2], (int)pack);
   const float d0 = (float)off[0] - t[0];
-  for (int k = 0; k < xw_len / 4; ++k) {
+  for (int k = 0; xw4 && k < xw_len / 4; ++k) {
     float v[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -226,14 +227,15 @@ __global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict_
     return pos;
   };
   if (kp.design == 4) {
-    // record: {p, x0 | y0 << 7 | z0 << 13 | lz << 15 | qa << 18 | lx << 22 |
-    //          ly << 27, d0y bits, d0z bits}: x0, y0 the staged x/y index of
-    // the piece's first node, z0 its first plane in the tile, lz the planes in
-    // the tile, [qa, qa + lx) the piece's positions in the particle's
-    // x-window, ly the y-window length, d0 distances (grid units) of the first
-    // y node / first plane
+    // record: {d0x bits, x0 | y0 << 7 | z0 << 13 | lz << 15 | qa << 18 |
+    //          lx << 22 | ly << 27, d0y bits, d0z bits}: x0, y0 the staged x/y
+    // index of the piece's first node, z0 its first plane in the tile, lz the
+    // planes in the tile, [qa, qa + lx) the piece's positions in the
+    // particle's x-window, ly the y-window length, d0 distances (grid units)
+    // of the window's first x node, first y node and the piece's first plane
     const int ty = c[1] / kp.T[1];
     const int y0 = jlo[1] - (ty * kp.T[1] - kp.yhlo);
+    const float d0x = (float)(jlo[0] - c[0]) - gt.x;
     const float d0y = (float)(jlo[1] - c[1]) - gt.y;
     const uint32_t fixed = ((uint32_t)y0 << 7) | ((uint32_t)nw[1] << 27);
     for_each_piece4(kp, c, jlo, nw, [&](int tile, int qa, int lx, int x0, int jz, int ez, int z0) {
@@ -243,7 +245,8 @@ __global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict_
                           ((uint32_t)lx << 22);
       const int64_t pos = place(tile);
       if (pos < cap)
-        entries[pos] = make_int4((int)i, (int)pk, __float_as_int(d0y), __float_as_int(d0z));
+        entries[pos] = make_int4(__float_as_int(d0x), (int)pk, __float_as_int(d0y),
+                                 __float_as_int(d0z));
       else
         erpp_set_err(err, ERPP_ERRBIT_BOUNDS);
     });
@@ -370,7 +373,8 @@ cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bo
     int blocks = (int)((n + 255) / 256);
     ++ctx->launches;
     k_bin_count<<<blocks, 256, 0, st>>>(kp, n, x[0], x[1], x[2], ctx->geo_t, ctx->geo_c,
-                                        ctx->xw, ctx->xw_len, zero_acc ? ctx->up_acc : nullptr,
+                                        kp.design == 4 ? nullptr : ctx->xw, ctx->xw_len,
+                                        zero_acc ? ctx->up_acc : nullptr,
                                         ctx->cap, ctx->tile_cnt, ctx->piece_slot, ms, ctx->err);
   }
   const int nchunks = (nbins + kScanChunk - 1) / kScanChunk;

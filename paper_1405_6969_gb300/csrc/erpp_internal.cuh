@@ -23,6 +23,8 @@
 //                     piece_slot[k][n] holds the place of particle i's k-th
 //                     piece once the binning is done
 //   fscat[i]  float4  -(1/rho_f) D_i norm / dV, max|component|
+//   fs_piece  float4  x/y-halo tiles: the force word of the piece's particle,
+//                     at the place of the piece's record
 //   halo      float   per tile, the scatter's x-halo columns (left hlo,
 //                     right hhi), [tile][3][T_z][T_y][hlo + hhi]
 // Grids are [3][nz][ny][nx] (x fastest).  Tiles: x-width W = 64 (last one
@@ -87,6 +89,8 @@ struct erpp_kparams {
   double inv_dx[3];  // N / L
   double L[3];
   double cp[3];      // r_c / dx
+  int cp_int[3];     // floor(cp)
+  float cp_frac[3];  // cp - floor(cp), rounded to FP32
   double dx[3];
   double dV;
   double rho_f, nu, eps_R, dt, mu;
@@ -130,12 +134,13 @@ struct erpp_ctx {
   int64_t cap;            // particle capacity of the per-particle arrays
   float4* geo_t;
   int4* geo_c;
-  float* xw;              // [cap][xw_len] x-weights per particle
+  float* xw;              // [cap][xw_len] x-weights per particle (x-halo tiles)
   int xw_len;
   float* up_acc;          // [3][cap] gathered velocity (x-halo tiles cut in y and z)
   float4* up_part;        // [entries_cap] x/y-halo tiles: each piece's gathered sums,
                           // at its place in the piece records
   float4* fscat;
+  float4* fs_piece;       // [entries_cap] x/y-halo tiles: each piece's force word
   double* up64;           // FP64 mode or other weights: gathered velocity [3][cap]
   int32_t* w_key;         // other weights: sort key, place and order of each particle [cap]
   int32_t* w_slot;
@@ -203,6 +208,9 @@ cudaError_t launch_gather_f32(erpp_ctx* ctx, const float* u, int64_t n, cudaStre
 cudaError_t launch_scatter_f32(erpp_ctx* ctx, float* S, cudaStream_t st);  // + x-halo merge
 cudaError_t launch_gather_f32_4(erpp_ctx* ctx, const float* u, cudaStream_t st);
 size_t smem_bytes4(const erpp_kparams& kp, int copies, bool gather);
+// Batch width of the x/y-halo tile kernels: 8 for x-windows of at most 7
+// nodes, else 16 (256 or 128 pieces per batch).
+int xw4(const erpp_kparams& kp);
 cudaError_t launch_scatter_f32_4(erpp_ctx* ctx, float* S, cudaStream_t st);  // + halo merge
 cudaError_t launch_finalize_up(erpp_ctx* ctx, int64_t n, const double* const x[3],
                                double* const up[3], cudaStream_t st);
@@ -270,6 +278,64 @@ __device__ __forceinline__ void erpp_axis_window(double x, double inv_dx, double
   *s = sv;
   *jlo = ceil(__dadd_rn(sv, -cp));
   *jhi = floor(__dadd_rn(sv, cp));
+}
+
+// The window of one axis as the binning uses it: s = x N/L (FP64, one
+// rounding), the home cell ci = floor(s), jlo = ceil(RN(s - cp)),
+// jhi = floor(RN(s + cp)) and t = RN_f32(s - ci), which are the values of
+// the FP64 form above (each rounding done once).  Only the product is taken
+// in FP64: the FP64 pipe is narrow, so the rest is integer and FP32 work.
+// With s = ci + f and cp = ck + cf (integer and fractional parts), s - cp =
+// (ci - ck) + (f - cf) and s + cp = (ci + ck) + (f + cf); f is read exactly
+// from the bits of s, and the FP32 estimates of g = f - cf and h = f + cf
+// (error below 2e-7) decide the ceiling and floor wherever they are farther
+// than 1e-5 from the points where the rounding of the sum could move the
+// result (g near -1 or 0, h near 1 or 2).  Elsewhere, and for s below 2^-126
+// in fraction, the FP64 form runs.
+struct erpp_axis_win {
+  int ci, lo, hi;
+  float t;
+};
+__device__ __forceinline__ erpp_axis_win erpp_axis_window_lean(double x, double inv_dx, double cp,
+                                                               int ck, float cf) {
+  erpp_axis_win w;
+  const double s = __dmul_rn(x, inv_dx);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+  const int ef = (int)((b >> 52) & 0x7ffu);
+  bool lean = ef != 0 && (b >> 63) == 0ull;
+  if (lean) {
+    // s = m 2^-sh, m with its implicit bit
+    const int sh = 1075 - ef;
+    const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+    const int ci = sh < 64 ? (int)(m >> sh) : 0;
+    const unsigned long long fb = sh < 64 ? (m & ((1ull << sh) - 1ull)) : m;  // f = fb 2^-sh
+    float t = 0.f;
+    if (fb != 0ull) {
+      const int lz = __clzll((long long)fb);
+      const int E = (63 - lz) - sh + 127;  // biased FP32 exponent of f
+      const unsigned long long mm = fb << lz;
+      const unsigned int hi24 = (unsigned int)(mm >> 40);
+      const unsigned long long rem = mm & ((1ull << 40) - 1ull);
+      const unsigned int up =
+          (rem > (1ull << 39) || (rem == (1ull << 39) && (hi24 & 1u))) ? 1u : 0u;
+      lean = E >= 1;
+      t = __uint_as_float(((unsigned int)max(E, 0) << 23) + (hi24 - (1u << 23)) + up);
+    }
+    const float g = t - cf, h = t + cf;
+    lean = lean && fabsf(g) > 1e-5f && g > -1.f + 1e-5f && fabsf(h - 1.f) > 1e-5f &&
+           h < 2.f - 1e-5f;
+    w.ci = ci;
+    w.lo = ci - ck + (g > 0.f ? 1 : 0);
+    w.hi = ci + ck + (h > 1.f ? 1 : 0);
+    w.t = t;
+  }
+  if (!lean) {
+    w.ci = __double2int_rd(s);
+    w.lo = __double2int_ru(__dadd_rn(s, -cp));
+    w.hi = __double2int_rd(__dadd_rn(s, cp));
+    w.t = __double2float_rn(__dadd_rn(s, -(double)w.ci));
+  }
+  return w;
 }
 
 __device__ __forceinline__ int erpp_geo_off(uint32_t pack, int a) {

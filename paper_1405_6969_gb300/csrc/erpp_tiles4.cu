@@ -94,18 +94,20 @@ struct Batch {
   static constexpr int kUnits = kPB * kMaxTz;
 };
 
-// Piece record (from the binning): p, packed geometry, d0y, d0z.  The piece
-// covers positions [qa, qa + lx) of the particle's x-window (qa > 0 or a
-// shorter lx only when the window is cut at x-tile boundaries).
+// Piece record (from the binning): d0x, packed geometry, d0y, d0z, where
+// d0a is the distance (grid units) from the particle to the first node of
+// its window along axis a.  The piece covers positions [qa, qa + lx) of the
+// particle's x-window (qa > 0 or a shorter lx only when the window is cut at
+// x-tile boundaries).
 struct Piece4 {
-  int p;
+  float d0x;
   int x0, y0, z0, lz, qa, lx, ly;
   float d0y, d0z;
 };
 
 __device__ __forceinline__ Piece4 unpack4(int4 r) {
   Piece4 pc;
-  pc.p = r.x;
+  pc.d0x = __int_as_float(r.x);
   const uint32_t v = (uint32_t)r.y;
   pc.x0 = (int)(v & 127u);
   pc.y0 = (int)((v >> 7) & 63u);
@@ -119,29 +121,16 @@ __device__ __forceinline__ Piece4 unpack4(int4 r) {
   return pc;
 }
 
-// The x-weights of a unit: the piece's x-weight record (XW floats in shared
-// memory, float4 aligned) shifted down by qa (a barrel shift of selects), so
-// that ex[q] weights slot q of the piece; slots from lx on get 0.
-template <int XM, int XW>
-__device__ __forceinline__ void load_ex(const float* xrow, int qa, int lx, float (&ex)[XM]) {
-  float v[XW];
-  const float4* xs = reinterpret_cast<const float4*>(xrow);
+// The x-weights of a unit: 2^(-beta_x d^2) at its slots q (window position
+// qa + q, distance d0x + qa + q), 0 past the piece's lx slots.  The binning's
+// normalisation takes the same values with the same arithmetic.
+template <int XM>
+__device__ __forceinline__ void make_ex(const Piece4& pc, float bx, float (&ex)[XM]) {
 #pragma unroll
-  for (int j = 0; j < XW / 4; ++j) {
-    const float4 t = xs[j];
-    v[4 * j] = t.x;
-    v[4 * j + 1] = t.y;
-    v[4 * j + 2] = t.z;
-    v[4 * j + 3] = t.w;
+  for (int q = 0; q < XM; ++q) {
+    const float d = pc.d0x + (float)(pc.qa + q);
+    ex[q] = q < pc.lx ? exp2f(-bx * d * d) : 0.f;
   }
-#pragma unroll
-  for (int b = 1; b < XW; b <<= 1) {
-    const bool sh = (qa & b) != 0;
-#pragma unroll
-    for (int q = 0; q < XW; ++q) v[q] = sh ? (q + b < XW ? v[q + b] : 0.f) : v[q];
-  }
-#pragma unroll
-  for (int q = 0; q < XM; ++q) ex[q] = (q < XW && q < lx) ? v[q] : 0.f;
 }
 
 // ---- asynchronous global -> shared copies (cp.async) ----
@@ -362,13 +351,12 @@ __device__ __forceinline__ void row_red_split(unsigned a0, unsigned a1, unsigned
 }
 
 // Dynamic shared memory of one block: the staged field (copies * plane
-// floats), then the batch's records, x-weights, force words (scatter), unit
-// words, schedule and piece accumulators (gather).
+// floats), then the batch's records, force words (scatter), unit words,
+// schedule and piece accumulators (gather).
 template <int XW>
 struct Carve {
   float* field;
   int4* rec;
-  float* xwb;
   float4* fsb;
   uint32_t* unit;
   uint16_t* sched;
@@ -384,7 +372,6 @@ __host__ __device__ inline size_t carve_bytes(int plane, int copies, bool gather
   constexpr int PB = Batch<XW>::kPB, NU = Batch<XW>::kUnits;
   size_t b = ((size_t)copies * plane + kFieldPad) * 4;
   b += (size_t)PB * 16;          // rec
-  b += (size_t)PB * XW * 4;      // xwb
   if (!gather) b += (size_t)PB * 16;  // fsb
   b += (size_t)NU * 4;           // unit
   b += (size_t)NU * 2;           // sched
@@ -402,8 +389,6 @@ __device__ inline Carve<XW> carve(unsigned char* base, int plane, int copies, bo
   o += ((size_t)copies * plane + kFieldPad) * 4;
   c.rec = reinterpret_cast<int4*>(base + o);
   o += (size_t)PB * 16;
-  c.xwb = reinterpret_cast<float*>(base + o);
-  o += (size_t)PB * XW * 4;
   c.fsb = reinterpret_cast<float4*>(base + o);
   if (!gather) o += (size_t)PB * 16;
   c.unit = reinterpret_cast<uint32_t*>(base + o);
@@ -607,21 +592,19 @@ __device__ __forceinline__ int batch_size(int total, int PB) {
 
 // A batch holds at most one piece per thread (PB <= threads per block):
 // thread k loads record k of the batch (issued early, so that its latency
-// overlaps other work), then stages it and, through the particle index, its
-// x-weights and force word into shared memory (asynchronous copies).
+// overlaps other work) and stages it; the scatter also stages the piece's
+// force word, which the advance stores at the place of the record, so that a
+// batch's records and forces are two contiguous ranges.
 __device__ __forceinline__ int4 load_rec(const int4* __restrict__ entries, int b0, int np) {
   return threadIdx.x < np ? __ldg(&entries[b0 + threadIdx.x]) : make_int4(0, 0, 0, 0);
 }
 template <int XW, bool FORCES>
-__device__ void stage_batch(const Carve<XW>& cv, int4 r, int np, const float* __restrict__ xw,
-                            const float4* __restrict__ fscat) {
+__device__ void stage_batch(const Carve<XW>& cv, int4 r, int np, int b0,
+                            const float4* __restrict__ fs_piece) {
   const int k = threadIdx.x;
   if (k < np) {
     cv.rec[k] = r;
-    const float* src = xw + (size_t)r.x * XW;
-#pragma unroll
-    for (int j = 0; j < XW / 4; ++j) cp_async16(cv.xwb + k * XW + 4 * j, src + 4 * j);
-    if (FORCES) cp_async16(cv.fsb + k, fscat + r.x);
+    if (FORCES) cp_async16(cv.fsb + k, fs_piece + b0 + k);
   }
 }
 
@@ -633,13 +616,13 @@ struct UnitRows {
   float d0y, ezz;
 };
 
-// XM: longest x-window; LMIN: shortest (slots q >= LMIN are tested); XW:
-// x-weights stored per particle.
+// XM: longest x-window; LMIN: shortest (slots q >= LMIN are tested); XW: 8
+// for windows of at most 7 nodes, else 16 (sets the pieces per batch).
 template <int XM, int LMIN, int XW, int NT>
 __global__ void __launch_bounds__(NT, 2) k_gather4(
     erpp_kparams kp, const float* __restrict__ u, const __grid_constant__ CUtensorMap tmap,
     int use_tma, const int32_t* __restrict__ start, const int4* __restrict__ entries,
-    int64_t ecap, const float* __restrict__ xw, float4* __restrict__ up_part, uint32_t* err) {
+    int64_t ecap, float4* __restrict__ up_part, uint32_t* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SchedState ss;
   __shared__ __align__(8) uint64_t tma_bar;
@@ -700,13 +683,13 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
   bool staged = false;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int plane = kp.plane, px = kp.px, pxy = kp.pxy;
-  const float by = kp.beta[1], bz = kp.beta[2];
+  const float bx = kp.beta[0], by = kp.beta[1], bz = kp.beta[2];
   const unsigned fbase = shared_addr(cv.field);
   for (int b0 = e0; b0 < e1; b0 += bs) {
     const int np = min(bs, e1 - b0);
-    stage_batch<XW, false>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, xw, nullptr);
+    stage_batch<XW, false>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, b0, nullptr);
     const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
-    cp_async_wait_all();                            // field (first batch), x-weights
+    cp_async_wait_all();                            // field (first batch)
     // One thread waits (bounded) for the staged field; the block learns the
     // outcome at the barrier and either goes on or returns as a whole.
     int timed_out = 0;
@@ -742,7 +725,7 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
         const int z = (int)((w >> 10) & 15u);
         uz = z;
         const Piece4 pc = unpack4(cv.rec[k]);
-        load_ex<XM, XW>(cv.xwb + k * XW, pc.qa, pc.lx, ex);
+        make_ex<XM>(pc, bx, ex);
         ur.base = (pc.z0 + z) * pxy + pc.y0 * px + pc.x0;
         ur.ly = pc.ly;
         ur.lx = pc.lx;
@@ -838,8 +821,7 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
                                                 const Carve<XW>& cv, SchedState& ss, float* red,
                                                 const int32_t* __restrict__ start,
                                                 const int4* __restrict__ entries, int64_t ecap,
-                                                const float* __restrict__ xw,
-                                                const float4* __restrict__ fscat) {
+                                                const float4* __restrict__ fs_piece) {
   constexpr int NW = NT / 32;
   constexpr int PB = Batch<XW>::kPB;
   float* smem = cv.field;
@@ -909,14 +891,13 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
     };
     if (fixedp && !single) {
       const int cnt = (e1 - e0 - (int)threadIdx.x + NT - 1) / NT;
-      set_scale([&](int j) { return __ldg(&fscat[__ldg(&entries[e0 + threadIdx.x + j * NT].x)]).w; },
-                max(cnt, 0));
+      set_scale([&](int j) { return __ldg(&fs_piece[e0 + threadIdx.x + j * NT]).w; }, max(cnt, 0));
     }
-    const float by = kp.beta[1], bz = kp.beta[2];
+    const float bx = kp.beta[0], by = kp.beta[1], bz = kp.beta[2];
     const unsigned fbase = shared_addr(smem);
     for (int b0 = e0; b0 < e1; b0 += bs) {
       const int np = min(bs, e1 - b0);
-      stage_batch<XW, true>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, xw, fscat);
+      stage_batch<XW, true>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, b0, fs_piece);
       const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
       cp_async_wait_all();
       __syncthreads();
@@ -941,7 +922,7 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
           const int k = (int)(w & 1023u);
           const int z = (int)((w >> 10) & 15u);
           const Piece4 pc = unpack4(cv.rec[k]);
-          load_ex<XM, XW>(cv.xwb + k * XW, pc.qa, pc.lx, ex);
+          make_ex<XM>(pc, bx, ex);
           ur.base = (pc.z0 + z) * pxy + pc.y0 * px + pc.x0;
           ur.ly = pc.ly;
           ur.lx = pc.lx;
@@ -1030,7 +1011,7 @@ template <int XM, int LMIN, int XW, int MODE, int NT, bool CL>
 __global__ void __launch_bounds__(NT, 2) k_scatter4(
     erpp_kparams kp, float* __restrict__ S, float* __restrict__ halo,
     const int32_t* __restrict__ start, const int4* __restrict__ entries, int64_t ecap,
-    const float* __restrict__ xw, const float4* __restrict__ fscat) {
+    const float4* __restrict__ fs_piece) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SchedState ss;
   constexpr int NW = NT / 32;
@@ -1041,7 +1022,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
   const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, MODE == 1 ? 6 : 3, false);
   float* smem = cv.field;
   const TileAcc ta =
-      scatter_tile<XM, LMIN, XW, MODE, NT>(kp, tile, cv, ss, red, start, entries, ecap, xw, fscat);
+      scatter_tile<XM, LMIN, XW, MODE, NT>(kp, tile, cv, ss, red, start, entries, ecap, fs_piece);
   const bool any = ta.any, fixedp = ta.fixedp;
   const float inv_scale = ta.inv_scale;
   int b[3], ext[3], tt[3];
@@ -1375,7 +1356,7 @@ cudaError_t gather4_nt(erpp_ctx* ctx, const float* u, cudaStream_t st) {
   const int use_tma = field_tensor_map(kp, u, &map) ? 1 : 0;
   ++ctx->launches;
   k_gather4<XM, LMIN, XW, NT><<<kp.ntiles, NT, sm, st>>>(kp, u, map, use_tma, ctx->tile_start,
-                                                         ctx->entries, ctx->entries_cap, ctx->xw,
+                                                         ctx->entries, ctx->entries_cap,
                                                          ctx->up_part, ctx->err);
   return cudaGetLastError();
 }
@@ -1399,7 +1380,7 @@ cudaError_t scatter4_mode(erpp_ctx* ctx, float* S, cudaStream_t st) {
   if (!CL) {
     ++ctx->launches;
     kern<<<kp.ntiles, NT, sm, st>>>(kp, S, ctx->halo, ctx->tile_start, ctx->entries,
-                                    ctx->entries_cap, ctx->xw, ctx->fscat);
+                                    ctx->entries_cap, ctx->fs_piece);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg;
@@ -1424,8 +1405,8 @@ cudaError_t scatter4_mode(erpp_ctx* ctx, float* S, cudaStream_t st) {
   if (ctx->cluster_probe != 1) return cudaErrorNotSupported;
   ++ctx->launches;
   return cudaLaunchKernelEx(&cfg, kern, kp, S, ctx->halo, (const int32_t*)ctx->tile_start,
-                            (const int4*)ctx->entries, ctx->entries_cap, (const float*)ctx->xw,
-                            (const float4*)ctx->fscat);
+                            (const int4*)ctx->entries, ctx->entries_cap,
+                            (const float4*)ctx->fs_piece);
 }
 
 template <int XM, int LMIN, int XW, bool CL>
@@ -1483,10 +1464,18 @@ int variant4(const erpp_kparams& kp) {
   return 4;
 }
 
-// Dynamic shared memory of the design-4 kernels (host side of the carve).
+// Batch width of the design-4 kernels: 8 for the variants of windows of at
+// most 7 nodes (0, 1, 5), else 16.
+int xw4(const erpp_kparams& kp) {
+  const int v = variant4(kp);
+  return (v == 0 || v == 1 || v == 5) ? 8 : 16;
+}
+
+// Dynamic shared memory of the design-4 kernels (host side of the carve),
+// for the batch width the launched variant uses.
 size_t smem_bytes4(const erpp_kparams& kp, int copies, bool gather) {
-  return kp.xxs <= 8 ? carve_bytes<8>(kp.plane, copies, gather)
-                     : carve_bytes<16>(kp.plane, copies, gather);
+  return xw4(kp) == 8 ? carve_bytes<8>(kp.plane, copies, gather)
+                      : carve_bytes<16>(kp.plane, copies, gather);
 }
 
 cudaError_t launch_gather_f32_4(erpp_ctx* ctx, const float* u, cudaStream_t st) {

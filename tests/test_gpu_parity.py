@@ -99,6 +99,27 @@ def _setup(w, npart):
     return grid, st
 
 
+def _near_window_ends(p, w):
+    """Positions whose x N/L lies within a few units in the last place of
+    j + c' or j - c' (a window end changes there) or of a node j (the home
+    cell and the fractional position change), on each axis; -0.0 too."""
+    L = np.array(w.L, dtype=np.float64)
+    n = np.array(w.n, dtype=np.float64)
+    sig = np.sqrt(2.0 * p["nu"] * p["eps_R"])
+    cp = p["cutoff"] * sig * n / L
+    cols = []
+    for j in (3, 5, 11):
+        for centre in (j + cp, j - cp, np.full(3, float(j))):
+            x0 = np.mod(centre, n) * (L / n)
+            for k in range(-3, 4):
+                x = x0.copy()
+                for _ in range(abs(k)):
+                    x = np.nextafter(x, np.inf if k > 0 else 0.0)
+                cols.append(np.clip(x, 0.0, np.nextafter(L, 0)))
+    cols.append(np.array([-0.0, -0.0, -0.0]))
+    return np.stack(cols, axis=1)
+
+
 @pytest.mark.parametrize("name,w,npart", CASES, ids=[c[0] for c in CASES])
 def test_windows_bit_exact(erpp, oracle_lib, name, w, npart):
     """Integer stencil membership is identical to the oracle's."""
@@ -112,6 +133,7 @@ def test_windows_bit_exact(erpp, oracle_lib, name, w, npart):
         (np.arange(12) % n + 0.5) * (L / n),
         np.nextafter(L, 0) * np.ones((3, 4)),
         np.zeros((3, 2)),
+        _near_window_ends(p, w),
     ], axis=1)
     x = np.concatenate([st.x, special], axis=1)
     ctx = erpp.Context(p, precision="fp32")
