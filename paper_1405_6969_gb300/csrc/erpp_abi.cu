@@ -48,9 +48,9 @@ void free_scratch(erpp_ctx* c) {
   cudaFree(c->xw);
   cudaFree(c->up_acc);
   cudaFree(c->up_part);
-  cudaFree(c->fs_piece);
+  cudaFree(c->d0x);
   c->up_part = nullptr;
-  c->fs_piece = nullptr;
+  c->d0x = nullptr;
   cudaFree(c->fscat);
   cudaFree(c->entries);
   cudaFree(c->piece_slot);
@@ -108,15 +108,15 @@ erpp_status ensure_capacity(erpp_ctx* c, int64_t n) {
   if (!c->fp64 && e == cudaSuccess) {
     int64_t ecap = cap * (int64_t)c->maxseg[0] * c->maxseg[1] * c->maxseg[2];
     e = cudaMalloc(&c->geo_t, sizeof(float4) * (size_t)cap);
-    if (e == cudaSuccess) e = cudaMalloc(&c->xw, sizeof(float) * (size_t)c->xw_len * (size_t)cap);
+    if (e == cudaSuccess && c->kp.design != 4)
+      e = cudaMalloc(&c->xw, sizeof(float) * (size_t)c->xw_len * (size_t)cap);
+    if (e == cudaSuccess && c->kp.design == 4) e = cudaMalloc(&c->d0x, sizeof(float) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->geo_c, sizeof(int4) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->up_acc, sizeof(float) * 3 * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->fscat, sizeof(float4) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->entries, sizeof(int4) * (size_t)ecap);
     if (e == cudaSuccess && c->kp.design == 4)
       e = cudaMalloc(&c->up_part, sizeof(float4) * (size_t)ecap);
-    if (e == cudaSuccess && c->kp.design == 4)
-      e = cudaMalloc(&c->fs_piece, sizeof(float4) * (size_t)ecap);
     if (e == cudaSuccess) e = cudaMalloc(&c->piece_slot, sizeof(int32_t) * (size_t)ecap);
     c->entries_cap = ecap;
   }

@@ -103,9 +103,10 @@ __device__ __forceinline__ void for_each_piece4(const erpp_kparams& kp, const in
 __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict__ x0,
                             const double* __restrict__ x1, const double* __restrict__ x2,
                             float4* __restrict__ geo_t, int4* __restrict__ geo_c,
-                            float* __restrict__ xw, int xw_len, float* __restrict__ up_acc,
-                            int64_t acc_stride, int32_t* __restrict__ tile_cnt,
-                            int32_t* __restrict__ slot, int ms, uint32_t* err) {
+                            float* __restrict__ xw, int xw_len, float* __restrict__ d0x,
+                            float* __restrict__ up_acc, int64_t acc_stride,
+                            int32_t* __restrict__ tile_cnt, int32_t* __restrict__ slot, int ms,
+                            uint32_t* err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double xv[3] = {x0[i], x1[i], x2[i]};
@@ -151,10 +152,12 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
   } else {
     erpp_set_err(err, ERPP_ERRBIT_RANGE);
   }
-  // x-halo tiles: the particle's x-weights (x/y-halo tiles take them from
-  // the piece records; xw is null then)
+  // x-halo tiles: the particle's x-weights; x/y-halo tiles: the distance of
+  // its x-window's first node, from which the tile kernels form the weights
+  // (one of xw, d0x is null)
   float4* xw4 = xw ? reinterpret_cast<float4*>(xw + (size_t)i * xw_len) : nullptr;
   if (!ok) {
+    if (d0x) d0x[i] = 0.f;
     geo_t[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     geo_c[i] = make_int4(0, 0, 0, 0);
     for (int k = 0; xw4 && k < xw_len / 4; ++k) xw4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -168,6 +171,7 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
   }
   geo_c[i] = make_int4(c[0], c[1], c[2], (int)pack);
   const float d0 = (float)off[0] - t[0];
+  if (d0x) d0x[i] = d0;
   for (int k = 0; xw4 && k < xw_len / 4; ++k) {
     float v[4];
 #pragma unroll
@@ -227,15 +231,14 @@ __global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict_
     return pos;
   };
   if (kp.design == 4) {
-    // record: {d0x bits, x0 | y0 << 7 | z0 << 13 | lz << 15 | qa << 18 |
-    //          lx << 22 | ly << 27, d0y bits, d0z bits}: x0, y0 the staged x/y
-    // index of the piece's first node, z0 its first plane in the tile, lz the
-    // planes in the tile, [qa, qa + lx) the piece's positions in the
-    // particle's x-window, ly the y-window length, d0 distances (grid units)
-    // of the window's first x node, first y node and the piece's first plane
+    // record: {p, x0 | y0 << 7 | z0 << 13 | lz << 15 | qa << 18 | lx << 22 |
+    //          ly << 27, d0y bits, d0z bits}: x0, y0 the staged x/y index of
+    // the piece's first node, z0 its first plane in the tile, lz the planes in
+    // the tile, [qa, qa + lx) the piece's positions in the particle's
+    // x-window, ly the y-window length, d0 distances (grid units) of the first
+    // y node / first plane
     const int ty = c[1] / kp.T[1];
     const int y0 = jlo[1] - (ty * kp.T[1] - kp.yhlo);
-    const float d0x = (float)(jlo[0] - c[0]) - gt.x;
     const float d0y = (float)(jlo[1] - c[1]) - gt.y;
     const uint32_t fixed = ((uint32_t)y0 << 7) | ((uint32_t)nw[1] << 27);
     for_each_piece4(kp, c, jlo, nw, [&](int tile, int qa, int lx, int x0, int jz, int ez, int z0) {
@@ -245,8 +248,7 @@ __global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict_
                           ((uint32_t)lx << 22);
       const int64_t pos = place(tile);
       if (pos < cap)
-        entries[pos] = make_int4(__float_as_int(d0x), (int)pk, __float_as_int(d0y),
-                                 __float_as_int(d0z));
+        entries[pos] = make_int4((int)i, (int)pk, __float_as_int(d0y), __float_as_int(d0z));
       else
         erpp_set_err(err, ERPP_ERRBIT_BOUNDS);
     });
@@ -374,6 +376,7 @@ cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bo
     ++ctx->launches;
     k_bin_count<<<blocks, 256, 0, st>>>(kp, n, x[0], x[1], x[2], ctx->geo_t, ctx->geo_c,
                                         kp.design == 4 ? nullptr : ctx->xw, ctx->xw_len,
+                                        kp.design == 4 ? ctx->d0x : nullptr,
                                         zero_acc ? ctx->up_acc : nullptr,
                                         ctx->cap, ctx->tile_cnt, ctx->piece_slot, ms, ctx->err);
   }

@@ -23,8 +23,8 @@
 //                     piece_slot[k][n] holds the place of particle i's k-th
 //                     piece once the binning is done
 //   fscat[i]  float4  -(1/rho_f) D_i norm / dV, max|component|
-//   fs_piece  float4  x/y-halo tiles: the force word of the piece's particle,
-//                     at the place of the piece's record
+//   d0x[i]    float   x/y-halo tiles: distance (grid units) from particle i
+//                     to the first node of its x-window
 //   halo      float   per tile, the scatter's x-halo columns (left hlo,
 //                     right hhi), [tile][3][T_z][T_y][hlo + hhi]
 // Grids are [3][nz][ny][nx] (x fastest).  Tiles: x-width W = 64 (last one
@@ -135,12 +135,12 @@ struct erpp_ctx {
   float4* geo_t;
   int4* geo_c;
   float* xw;              // [cap][xw_len] x-weights per particle (x-halo tiles)
+  float* d0x;             // [cap] x/y-halo tiles: x-distance of the window's first node
   int xw_len;
   float* up_acc;          // [3][cap] gathered velocity (x-halo tiles cut in y and z)
   float4* up_part;        // [entries_cap] x/y-halo tiles: each piece's gathered sums,
                           // at its place in the piece records
   float4* fscat;
-  float4* fs_piece;       // [entries_cap] x/y-halo tiles: each piece's force word
   double* up64;           // FP64 mode or other weights: gathered velocity [3][cap]
   int32_t* w_key;         // other weights: sort key, place and order of each particle [cap]
   int32_t* w_slot;

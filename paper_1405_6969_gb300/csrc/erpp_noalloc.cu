@@ -127,6 +127,9 @@ extern "C" erpp_status erpp_interpolate_noalloc(const erpp_params* params, const
   c.up_acc = reinterpret_cast<float*>(base + kOffAcc);
   c.entries = reinterpret_cast<int4*>(base + kOffEntries);
   c.xw = reinterpret_cast<float*>(base + kOffXw);
+  // the x/y-halo tiles keep one x-distance per particle where the x-halo
+  // tiles keep their x-weights (a context uses one of the two)
+  c.d0x = reinterpret_cast<float*>(base + kOffXw);
   c.tile_cnt = reinterpret_cast<int32_t*>(base + kOffCnt);
   c.tile_start = reinterpret_cast<int32_t*>(base + kOffStart);
   c.piece_slot = reinterpret_cast<int32_t*>(base + kOffSlot);

@@ -276,20 +276,6 @@ __global__ void __launch_bounds__(256) k_advance_full(erpp_kparams kp, int64_t n
   }
 }
 
-// Stores particle i's scatter word: at fscat[i] (x-halo tiles), or at the
-// place of each of its piece records (x/y-halo tiles, fs_piece non-null), so
-// that the scatter stages a batch's forces as one contiguous range.
-__device__ __forceinline__ void store_force(float4 f, int64_t i, const float4* __restrict__ geo_t,
-                                            const erpp_acc& acc, float4* __restrict__ fscat,
-                                            float4* __restrict__ fs_piece) {
-  if (!fs_piece) {
-    fscat[i] = f;
-    return;
-  }
-  const int np = __float_as_int(geo_t[i].w);
-  for (int k = 0; k < np; ++k) fs_piece[acc.piece_slot[(int64_t)k * acc.n + i]] = f;
-}
-
 // Removal + drag + Euler (Sec. 2.5, Eqs. particle_motion, force_stokes_drag).
 // FROM_ACC: the gathered velocity comes from the tile gather's accumulator
 // (scaled here by the kernel normalisation); otherwise from caller arrays.
@@ -301,8 +287,7 @@ __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, Par
                                                  UpPtrs U, erpp_acc acc,
                                                  const float4* __restrict__ geo_t,
                                                  const int4* __restrict__ geo_c,
-                                                 float4* __restrict__ fscat,
-                                                 float4* __restrict__ fs_piece, int first_step) {
+                                                 float4* __restrict__ fscat, int first_step) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double x[3], v[3];
@@ -398,8 +383,7 @@ __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, Par
   if (fscat) {
     const float s = -norm * kp.inv_rho_dV;
     const float f0 = s * Dnf[0], f1 = s * Dnf[1], f2 = s * Dnf[2];
-    store_force(make_float4(f0, f1, f2, fmaxf(fabsf(f0), fmaxf(fabsf(f1), fabsf(f2)))), i, geo_t,
-                acc, fscat, fs_piece);
+    fscat[i] = make_float4(f0, f1, f2, fmaxf(fabsf(f0), fmaxf(fabsf(f1), fabsf(f2))));
   }
 }
 
@@ -431,14 +415,12 @@ erpp_acc acc_of(const erpp_ctx* ctx, int64_t n) {
 __global__ void k_prep_fscat(erpp_kparams kp, int64_t n, const double* __restrict__ D0,
                              const double* __restrict__ D1, const double* __restrict__ D2,
                              const float4* __restrict__ geo_t, const int4* __restrict__ geo_c,
-                             float scale, erpp_acc acc, float4* __restrict__ fscat,
-                             float4* __restrict__ fs_piece) {
+                             float scale, float4* __restrict__ fscat) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float s = erpp_norm(kp, geo_t[i], geo_c[i]) * scale;
   const float f0 = s * (float)D0[i], f1 = s * (float)D1[i], f2 = s * (float)D2[i];
-  store_force(make_float4(f0, f1, f2, fmaxf(fabsf(f0), fmaxf(fabsf(f1), fabsf(f2)))), i, geo_t,
-              acc, fscat, fs_piece);
+  fscat[i] = make_float4(f0, f1, f2, fmaxf(fabsf(f0), fmaxf(fabsf(f1), fabsf(f2))));
 }
 
 __global__ void k_windows(erpp_kparams kp, int64_t n, const double* __restrict__ x0,
@@ -578,18 +560,17 @@ cudaError_t launch_advance(erpp_ctx* ctx, const erpp_particles* P, const double*
   for (int a = 0; a < 3; ++a) U.up[a] = up ? up[a] : nullptr;
   int blocks = (int)((n + 255) / 256);
   float4* fs = write_fscat ? ctx->fscat : nullptr;
-  float4* fsp = (write_fscat && ctx->kp.design == 4) ? ctx->fs_piece : nullptr;
   const bool f32 = !ctx->fp64;
   ++ctx->launches;
   if (from_acc) {
     k_advance<true, true><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, acc_of(ctx, n), ctx->geo_t,
-                                                  ctx->geo_c, fs, fsp, first_step);
+                                                  ctx->geo_c, fs, first_step);
   } else if (f32) {
     k_advance<false, true><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, erpp_acc{}, nullptr,
-                                                   nullptr, nullptr, nullptr, first_step);
+                                                   nullptr, nullptr, first_step);
   } else {
     k_advance<false, false><<<blocks, 256, 0, st>>>(ctx->kp, n, q, U, erpp_acc{}, nullptr,
-                                                    nullptr, nullptr, nullptr, first_step);
+                                                    nullptr, nullptr, first_step);
   }
   return cudaGetLastError();
 }
@@ -652,8 +633,7 @@ cudaError_t launch_prep_fscat(erpp_ctx* ctx, int64_t n, const double* const D[3]
   if (n <= 0) return cudaSuccess;
   int blocks = (int)((n + 255) / 256);
   k_prep_fscat<<<blocks, 256, 0, st>>>(ctx->kp, n, D[0], D[1], D[2], ctx->geo_t, ctx->geo_c,
-                                       scale, acc_of(ctx, n), ctx->fscat,
-                                       ctx->kp.design == 4 ? ctx->fs_piece : nullptr);
+                                       scale, ctx->fscat);
   return cudaGetLastError();
 }
 

@@ -94,20 +94,20 @@ struct Batch {
   static constexpr int kUnits = kPB * kMaxTz;
 };
 
-// Piece record (from the binning): d0x, packed geometry, d0y, d0z, where
-// d0a is the distance (grid units) from the particle to the first node of
-// its window along axis a.  The piece covers positions [qa, qa + lx) of the
+// Piece record (from the binning): p, packed geometry, d0y, d0z (distances,
+// in grid units, from the particle to the first node of its y-window and to
+// the piece's first plane).  The piece covers positions [qa, qa + lx) of the
 // particle's x-window (qa > 0 or a shorter lx only when the window is cut at
 // x-tile boundaries).
 struct Piece4 {
-  float d0x;
+  int p;
   int x0, y0, z0, lz, qa, lx, ly;
   float d0y, d0z;
 };
 
 __device__ __forceinline__ Piece4 unpack4(int4 r) {
   Piece4 pc;
-  pc.d0x = __int_as_float(r.x);
+  pc.p = r.x;
   const uint32_t v = (uint32_t)r.y;
   pc.x0 = (int)(v & 127u);
   pc.y0 = (int)((v >> 7) & 63u);
@@ -122,13 +122,14 @@ __device__ __forceinline__ Piece4 unpack4(int4 r) {
 }
 
 // The x-weights of a unit: 2^(-beta_x d^2) at its slots q (window position
-// qa + q, distance d0x + qa + q), 0 past the piece's lx slots.  The binning's
-// normalisation takes the same values with the same arithmetic.
+// qa + q, distance d0x + qa + q with d0x that of the window's first node),
+// 0 past the piece's lx slots.  The binning's normalisation takes the same
+// values with the same arithmetic.
 template <int XM>
-__device__ __forceinline__ void make_ex(const Piece4& pc, float bx, float (&ex)[XM]) {
+__device__ __forceinline__ void make_ex(const Piece4& pc, float d0x, float bx, float (&ex)[XM]) {
 #pragma unroll
   for (int q = 0; q < XM; ++q) {
-    const float d = pc.d0x + (float)(pc.qa + q);
+    const float d = d0x + (float)(pc.qa + q);
     ex[q] = q < pc.lx ? exp2f(-bx * d * d) : 0.f;
   }
 }
@@ -351,13 +352,14 @@ __device__ __forceinline__ void row_red_split(unsigned a0, unsigned a1, unsigned
 }
 
 // Dynamic shared memory of one block: the staged field (copies * plane
-// floats), then the batch's records, force words (scatter), unit words,
-// schedule and piece accumulators (gather).
+// floats), then the batch's records, force words (scatter), x-distances,
+// unit words, schedule and piece accumulators (gather).
 template <int XW>
 struct Carve {
   float* field;
   int4* rec;
   float4* fsb;
+  float* dxb;
   uint32_t* unit;
   uint16_t* sched;
   float* pacc;
@@ -373,6 +375,7 @@ __host__ __device__ inline size_t carve_bytes(int plane, int copies, bool gather
   size_t b = ((size_t)copies * plane + kFieldPad) * 4;
   b += (size_t)PB * 16;          // rec
   if (!gather) b += (size_t)PB * 16;  // fsb
+  b += (size_t)PB * 4;           // dxb
   b += (size_t)NU * 4;           // unit
   b += (size_t)NU * 2;           // sched
   b = (b + 15) & ~(size_t)15;
@@ -391,6 +394,8 @@ __device__ inline Carve<XW> carve(unsigned char* base, int plane, int copies, bo
   o += (size_t)PB * 16;
   c.fsb = reinterpret_cast<float4*>(base + o);
   if (!gather) o += (size_t)PB * 16;
+  c.dxb = reinterpret_cast<float*>(base + o);
+  o += (size_t)PB * 4;
   c.unit = reinterpret_cast<uint32_t*>(base + o);
   o += (size_t)NU * 4;
   c.sched = reinterpret_cast<uint16_t*>(base + o);
@@ -592,19 +597,19 @@ __device__ __forceinline__ int batch_size(int total, int PB) {
 
 // A batch holds at most one piece per thread (PB <= threads per block):
 // thread k loads record k of the batch (issued early, so that its latency
-// overlaps other work) and stages it; the scatter also stages the piece's
-// force word, which the advance stores at the place of the record, so that a
-// batch's records and forces are two contiguous ranges.
+// overlaps other work), then stages it and, through the particle index, the
+// particle's x-distance and (scatter) force word (asynchronous copies).
 __device__ __forceinline__ int4 load_rec(const int4* __restrict__ entries, int b0, int np) {
   return threadIdx.x < np ? __ldg(&entries[b0 + threadIdx.x]) : make_int4(0, 0, 0, 0);
 }
 template <int XW, bool FORCES>
-__device__ void stage_batch(const Carve<XW>& cv, int4 r, int np, int b0,
-                            const float4* __restrict__ fs_piece) {
+__device__ void stage_batch(const Carve<XW>& cv, int4 r, int np, const float* __restrict__ d0x,
+                            const float4* __restrict__ fscat) {
   const int k = threadIdx.x;
   if (k < np) {
     cv.rec[k] = r;
-    if (FORCES) cp_async16(cv.fsb + k, fs_piece + b0 + k);
+    cp_async4(cv.dxb + k, d0x + r.x);
+    if (FORCES) cp_async16(cv.fsb + k, fscat + r.x);
   }
 }
 
@@ -622,7 +627,7 @@ template <int XM, int LMIN, int XW, int NT>
 __global__ void __launch_bounds__(NT, 2) k_gather4(
     erpp_kparams kp, const float* __restrict__ u, const __grid_constant__ CUtensorMap tmap,
     int use_tma, const int32_t* __restrict__ start, const int4* __restrict__ entries,
-    int64_t ecap, float4* __restrict__ up_part, uint32_t* err) {
+    int64_t ecap, const float* __restrict__ d0x, float4* __restrict__ up_part, uint32_t* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SchedState ss;
   __shared__ __align__(8) uint64_t tma_bar;
@@ -687,9 +692,9 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
   const unsigned fbase = shared_addr(cv.field);
   for (int b0 = e0; b0 < e1; b0 += bs) {
     const int np = min(bs, e1 - b0);
-    stage_batch<XW, false>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, b0, nullptr);
+    stage_batch<XW, false>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, d0x, nullptr);
     const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
-    cp_async_wait_all();                            // field (first batch)
+    cp_async_wait_all();                            // field (first batch), x-distances
     // One thread waits (bounded) for the staged field; the block learns the
     // outcome at the barrier and either goes on or returns as a whole.
     int timed_out = 0;
@@ -725,7 +730,7 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
         const int z = (int)((w >> 10) & 15u);
         uz = z;
         const Piece4 pc = unpack4(cv.rec[k]);
-        make_ex<XM>(pc, bx, ex);
+        make_ex<XM>(pc, cv.dxb[k], bx, ex);
         ur.base = (pc.z0 + z) * pxy + pc.y0 * px + pc.x0;
         ur.ly = pc.ly;
         ur.lx = pc.lx;
@@ -821,7 +826,8 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
                                                 const Carve<XW>& cv, SchedState& ss, float* red,
                                                 const int32_t* __restrict__ start,
                                                 const int4* __restrict__ entries, int64_t ecap,
-                                                const float4* __restrict__ fs_piece) {
+                                                const float* __restrict__ d0x,
+                                                const float4* __restrict__ fscat) {
   constexpr int NW = NT / 32;
   constexpr int PB = Batch<XW>::kPB;
   float* smem = cv.field;
@@ -891,13 +897,14 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
     };
     if (fixedp && !single) {
       const int cnt = (e1 - e0 - (int)threadIdx.x + NT - 1) / NT;
-      set_scale([&](int j) { return __ldg(&fs_piece[e0 + threadIdx.x + j * NT]).w; }, max(cnt, 0));
+      set_scale([&](int j) { return __ldg(&fscat[__ldg(&entries[e0 + threadIdx.x + j * NT].x)]).w; },
+                max(cnt, 0));
     }
     const float bx = kp.beta[0], by = kp.beta[1], bz = kp.beta[2];
     const unsigned fbase = shared_addr(smem);
     for (int b0 = e0; b0 < e1; b0 += bs) {
       const int np = min(bs, e1 - b0);
-      stage_batch<XW, true>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, b0, fs_piece);
+      stage_batch<XW, true>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, d0x, fscat);
       const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
       cp_async_wait_all();
       __syncthreads();
@@ -922,7 +929,7 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
           const int k = (int)(w & 1023u);
           const int z = (int)((w >> 10) & 15u);
           const Piece4 pc = unpack4(cv.rec[k]);
-          make_ex<XM>(pc, bx, ex);
+          make_ex<XM>(pc, cv.dxb[k], bx, ex);
           ur.base = (pc.z0 + z) * pxy + pc.y0 * px + pc.x0;
           ur.ly = pc.ly;
           ur.lx = pc.lx;
@@ -1011,7 +1018,7 @@ template <int XM, int LMIN, int XW, int MODE, int NT, bool CL>
 __global__ void __launch_bounds__(NT, 2) k_scatter4(
     erpp_kparams kp, float* __restrict__ S, float* __restrict__ halo,
     const int32_t* __restrict__ start, const int4* __restrict__ entries, int64_t ecap,
-    const float4* __restrict__ fs_piece) {
+    const float* __restrict__ d0x, const float4* __restrict__ fscat) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SchedState ss;
   constexpr int NW = NT / 32;
@@ -1022,7 +1029,8 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
   const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, MODE == 1 ? 6 : 3, false);
   float* smem = cv.field;
   const TileAcc ta =
-      scatter_tile<XM, LMIN, XW, MODE, NT>(kp, tile, cv, ss, red, start, entries, ecap, fs_piece);
+      scatter_tile<XM, LMIN, XW, MODE, NT>(kp, tile, cv, ss, red, start, entries, ecap, d0x,
+                                           fscat);
   const bool any = ta.any, fixedp = ta.fixedp;
   const float inv_scale = ta.inv_scale;
   int b[3], ext[3], tt[3];
@@ -1357,7 +1365,7 @@ cudaError_t gather4_nt(erpp_ctx* ctx, const float* u, cudaStream_t st) {
   ++ctx->launches;
   k_gather4<XM, LMIN, XW, NT><<<kp.ntiles, NT, sm, st>>>(kp, u, map, use_tma, ctx->tile_start,
                                                          ctx->entries, ctx->entries_cap,
-                                                         ctx->up_part, ctx->err);
+                                                         ctx->d0x, ctx->up_part, ctx->err);
   return cudaGetLastError();
 }
 
@@ -1380,7 +1388,7 @@ cudaError_t scatter4_mode(erpp_ctx* ctx, float* S, cudaStream_t st) {
   if (!CL) {
     ++ctx->launches;
     kern<<<kp.ntiles, NT, sm, st>>>(kp, S, ctx->halo, ctx->tile_start, ctx->entries,
-                                    ctx->entries_cap, ctx->fs_piece);
+                                    ctx->entries_cap, ctx->d0x, ctx->fscat);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg;
@@ -1406,7 +1414,7 @@ cudaError_t scatter4_mode(erpp_ctx* ctx, float* S, cudaStream_t st) {
   ++ctx->launches;
   return cudaLaunchKernelEx(&cfg, kern, kp, S, ctx->halo, (const int32_t*)ctx->tile_start,
                             (const int4*)ctx->entries, ctx->entries_cap,
-                            (const float4*)ctx->fs_piece);
+                            (const float*)ctx->d0x, (const float4*)ctx->fscat);
 }
 
 template <int XM, int LMIN, int XW, bool CL>
