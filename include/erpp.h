@@ -63,10 +63,13 @@ enum {
   ERPP_FP64 = 1u << 1,         /* double grids; plain FP64 kernels           */
   ERPP_NORMALIZE = 1u << 2,    /* unit discrete mass per axis (recommended)  */
   ERPP_SELF_REMOVAL = 1u << 3, /* subtract the closed-form self disturbance  */
-  ERPP_KAHAN = 1u << 4,        /* FP32 only: compensated scatter: the FP32
-                                  kernel values summed per tile without any
-                                  rounding (64-bit fixed point); twice the
-                                  shared memory of the default form          */
+  ERPP_KAHAN = 1u << 4,        /* FP32 only: compensated scatter: each
+                                  contribution's 64-bit fixed-point product
+                                  summed per tile as a high and a low 32-bit
+                                  word (about 46 bits below the tile's force
+                                  bound, order independent), converted to
+                                  FP32 once per tile; twice the shared memory
+                                  of the default form                        */
   ERPP_PIC = 1u << 5,          /* classical particle-in-cell coupling instead
                                   of the regularised kernel (see below)      */
   ERPP_POINT_GATHER = 1u << 6, /* point-value gather (see below); the source

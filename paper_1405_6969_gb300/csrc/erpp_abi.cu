@@ -49,8 +49,12 @@ void free_scratch(erpp_ctx* c) {
   cudaFree(c->up_acc);
   cudaFree(c->up_part);
   cudaFree(c->d0x);
+  cudaFree(c->lapc);
+  cudaFree(c->lap_part);
   c->up_part = nullptr;
   c->d0x = nullptr;
+  c->lapc = nullptr;
+  c->lap_part = nullptr;
   cudaFree(c->fscat);
   cudaFree(c->entries);
   cudaFree(c->piece_slot);
@@ -111,12 +115,16 @@ erpp_status ensure_capacity(erpp_ctx* c, int64_t n) {
     if (e == cudaSuccess && c->kp.design != 4)
       e = cudaMalloc(&c->xw, sizeof(float) * (size_t)c->xw_len * (size_t)cap);
     if (e == cudaSuccess && c->kp.design == 4) e = cudaMalloc(&c->d0x, sizeof(float) * (size_t)cap);
+    if (e == cudaSuccess && c->kp.design == 4 && c->kp.full_force)
+      e = cudaMalloc(&c->lapc, 2 * sizeof(float4) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->geo_c, sizeof(int4) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->up_acc, sizeof(float) * 3 * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->fscat, sizeof(float4) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc(&c->entries, sizeof(int4) * (size_t)ecap);
     if (e == cudaSuccess && c->kp.design == 4)
       e = cudaMalloc(&c->up_part, sizeof(float4) * (size_t)ecap);
+    if (e == cudaSuccess && c->kp.design == 4 && c->kp.full_force)
+      e = cudaMalloc(&c->lap_part, sizeof(float4) * (size_t)ecap);
     if (e == cudaSuccess) e = cudaMalloc(&c->piece_slot, sizeof(int32_t) * (size_t)ecap);
     c->entries_cap = ecap;
   }
@@ -293,7 +301,10 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
     kp.wrap_hi_f[a] = (float)((1.0 - 1e-4) * L[a]);
   }
   const double log2e = 1.4426950408889634;
-  for (int a = 0; a < 3; ++a) kp.beta[a] = (float)(log2e * kp.dx[a] * kp.dx[a] / (2.0 * sig2));
+  for (int a = 0; a < 3; ++a) {
+    kp.beta[a] = (float)(log2e * kp.dx[a] * kp.dx[a] / (2.0 * sig2));
+    kp.lap_k[a] = (float)(kp.dx[a] * kp.dx[a] / (sig2 * sig2));
+  }
   kp.inv_rho_dV = (float)(1.0 / (p->rho_f * kp.dV));
   kp.normalize = (p->flags & ERPP_NORMALIZE) ? 1 : 0;
   kp.self_removal = (p->flags & ERPP_SELF_REMOVAL) ? 1 : 0;
@@ -693,7 +704,10 @@ erpp_status step_lagged(erpp_ctx* c, const void* u, const erpp_particles* P, voi
 }
 
 // The step with the general force (ERPP_FULL_FORCE): gather of the velocity and
-// its Laplacian, the general-force advance, the source of D^n at x^n.
+// its Laplacian, the general-force advance, the source of D^n at x^n.  FP32 on
+// x/y-halo tiles: one binning of x^n serves the tile gather of both and the
+// source (the advance leaves x^n in x_prev); otherwise the warp-per-particle
+// gather, and the source binned on its own.
 erpp_status step_full_force(erpp_ctx* c, const void* u, const erpp_particles* P, void* S,
                             int first_step, cudaStream_t st, cudaEvent_t after_advance) {
   const int64_t n = P->n;
@@ -707,10 +721,23 @@ erpp_status step_full_force(erpp_ctx* c, const void* u, const erpp_particles* P,
   double* up[3] = {c->up64, c->up64 + c->cap, c->up64 + 2 * c->cap};
   const double* const upc[3] = {up[0], up[1], up[2]};
   c->launches = 0;
-  cudaError_t e = erpp::launch_gather_faxen(c, u, n, xin, up, st);
+  const bool tiles = !c->fp64 && c->kp.design == 4 && c->kp.weights == ERPP_W_GAUSS;
+  cudaError_t e = cudaSuccess;
+  if (tiles) {
+    e = erpp::bin_particles(c, n, xin, true, st);
+    if (e == cudaSuccess) e = erpp::launch_gather_lap_f32_4(c, (const float*)u, st);
+    if (e == cudaSuccess) e = erpp::launch_finalize_full(c, n, xin, up, c->ff_lap, c->cap, st);
+  } else {
+    e = erpp::launch_gather_faxen(c, u, n, xin, up, st);
+  }
   if (e == cudaSuccess) e = erpp::launch_advance_full(c, P, upc, first_step, st);
   if (e == cudaSuccess && after_advance) e = cudaEventRecord(after_advance, st);
-  if (e == cudaSuccess) e = erpp::scatter_source(c, n, xprev, Dv, S, st);
+  if (e == cudaSuccess && tiles) {
+    e = erpp::launch_prep_fscat(c, n, Dv, -c->kp.inv_rho_dV, st);
+    if (e == cudaSuccess) e = erpp::launch_scatter_f32(c, (float*)S, st);
+  } else if (e == cudaSuccess) {
+    e = erpp::scatter_source(c, n, xprev, Dv, S, st);
+  }
   c->last_step_launches = c->launches;
   return set_cuda_err(e);
 }

@@ -104,7 +104,8 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
                             const double* __restrict__ x1, const double* __restrict__ x2,
                             float4* __restrict__ geo_t, int4* __restrict__ geo_c,
                             float* __restrict__ xw, int xw_len, float* __restrict__ d0x,
-                            float* __restrict__ up_acc, int64_t acc_stride,
+                            float4* __restrict__ lapc, float* __restrict__ up_acc,
+                            int64_t acc_stride,
                             int32_t* __restrict__ tile_cnt, int32_t* __restrict__ slot, int ms,
                             uint32_t* err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -158,6 +159,10 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
   float4* xw4 = xw ? reinterpret_cast<float4*>(xw + (size_t)i * xw_len) : nullptr;
   if (!ok) {
     if (d0x) d0x[i] = 0.f;
+    if (lapc) {
+      lapc[2 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      lapc[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     geo_t[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     geo_c[i] = make_int4(0, 0, 0, 0);
     for (int k = 0; xw4 && k < xw_len / 4; ++k) xw4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -172,6 +177,13 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
   geo_c[i] = make_int4(c[0], c[1], c[2], (int)pack);
   const float d0 = (float)off[0] - t[0];
   if (d0x) d0x[i] = d0;
+  if (lapc) {
+    // the general force: the window's weight moments for the Laplacian
+    float4 m[2];
+    erpp_lap_moments(kp, t, off, nw, m);
+    lapc[2 * i] = m[0];
+    lapc[2 * i + 1] = m[1];
+  }
   for (int k = 0; xw4 && k < xw_len / 4; ++k) {
     float v[4];
 #pragma unroll
@@ -377,6 +389,7 @@ cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bo
     k_bin_count<<<blocks, 256, 0, st>>>(kp, n, x[0], x[1], x[2], ctx->geo_t, ctx->geo_c,
                                         kp.design == 4 ? nullptr : ctx->xw, ctx->xw_len,
                                         kp.design == 4 ? ctx->d0x : nullptr,
+                                        kp.design == 4 && kp.full_force ? ctx->lapc : nullptr,
                                         zero_acc ? ctx->up_acc : nullptr,
                                         ctx->cap, ctx->tile_cnt, ctx->piece_slot, ms, ctx->err);
   }

@@ -91,6 +91,8 @@ struct erpp_kparams {
   double cp[3];      // r_c / dx
   int cp_int[3];     // floor(cp)
   float cp_frac[3];  // cp - floor(cp), rounded to FP32
+  float lap_k[3];    // dx_a^2 / sigma_R^4: scale of the weights' second
+                     // derivatives in the particle position (general force)
   double dx[3];
   double dV;
   double rho_f, nu, eps_R, dt, mu;
@@ -136,6 +138,10 @@ struct erpp_ctx {
   int4* geo_c;
   float* xw;              // [cap][xw_len] x-weights per particle (x-halo tiles)
   float* d0x;             // [cap] x/y-halo tiles: x-distance of the window's first node
+  float4* lapc;           // [2 cap] general force, x/y-halo tiles: per particle the mean
+                          // and variance of its window offsets under the weights,
+                          // (mu_x, V_x, mu_y, V_y), (mu_z, V_z, 0, 0)
+  float4* lap_part;       // [entries_cap] general force: each piece's Laplacian sums
   int xw_len;
   float* up_acc;          // [3][cap] gathered velocity (x-halo tiles cut in y and z)
   float4* up_part;        // [entries_cap] x/y-halo tiles: each piece's gathered sums,
@@ -207,6 +213,13 @@ cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bo
 cudaError_t launch_gather_f32(erpp_ctx* ctx, const float* u, int64_t n, cudaStream_t st);
 cudaError_t launch_scatter_f32(erpp_ctx* ctx, float* S, cudaStream_t st);  // + x-halo merge
 cudaError_t launch_gather_f32_4(erpp_ctx* ctx, const float* u, cudaStream_t st);
+// General force on x/y-halo tiles: the gather of the velocity and of its
+// Laplacian (per-piece sums in up_part and lap_part), and their per-particle
+// totals: up = norm * sum + shear y (x component), lap = norm * sum.
+cudaError_t launch_gather_lap_f32_4(erpp_ctx* ctx, const float* u, cudaStream_t st);
+cudaError_t launch_finalize_full(erpp_ctx* ctx, int64_t n, const double* const x[3],
+                                 double* const up[3], double* lap, int64_t lap_stride,
+                                 cudaStream_t st);
 size_t smem_bytes4(const erpp_kparams& kp, int copies, bool gather);
 // Batch width of the x/y-halo tile kernels: 8 for x-windows of at most 7
 // nodes, else 16 (256 or 128 pieces per batch).
@@ -371,6 +384,41 @@ __device__ __forceinline__ float erpp_norm(const erpp_kparams& kp, float4 gt, in
     prod *= sum;
   }
   return 1.f / prod;
+}
+
+// Per axis, the mean mu and variance V of the offsets u = node - particle
+// (grid units) of the particle's window under its weights e(u) =
+// 2^(-beta u^2).  The second derivative in the particle position of the
+// normalised weight e / sum e is then e / sum e * lap_k ((u - mu)^2 - V)
+// (differentiate the quotient twice: the normalising sum contributes the
+// mean and variance terms); for the raw Gaussian, mu = 0 and V = sigma_R^2
+// in grid units.  out: (mu_x, V_x, mu_y, V_y), (mu_z, V_z, 0, 0).
+__device__ __forceinline__ void erpp_lap_moments(const erpp_kparams& kp, const float t[3],
+                                                 const int off[3], const int nw[3],
+                                                 float4 out[2]) {
+  float m[3], v[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (!kp.normalize) {
+      m[a] = 0.f;
+      v[a] = 1.4426950408889634f / (2.f * kp.beta[a]);
+      continue;
+    }
+    const float d0 = (float)off[a] - t[a];
+    float s = 0.f, s1 = 0.f, s2 = 0.f;
+    for (int k = 0; k < nw[a]; ++k) {
+      const float d = d0 + (float)k;
+      const float e = exp2f(-kp.beta[a] * d * d);
+      s += e;
+      s1 = fmaf(e, d, s1);
+      s2 = fmaf(e * d, d, s2);
+    }
+    const float inv = 1.f / s;
+    m[a] = s1 * inv;
+    v[a] = fmaf(-m[a], m[a], s2 * inv);
+  }
+  out[0] = make_float4(m[0], v[0], m[1], v[1]);
+  out[1] = make_float4(m[2], v[2], 0.f, 0.f);
 }
 
 // The gathered sums of particle i (before normalisation): x/y-halo tiles add

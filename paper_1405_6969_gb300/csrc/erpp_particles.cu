@@ -402,6 +402,36 @@ __global__ void k_finalize_up(erpp_kparams kp, int64_t n, erpp_acc acc,
   up2[i] = (double)(g[2] * norm);
 }
 
+// The general force on x/y-halo tiles: the gathered velocity (norm * sum +
+// shear y in x) and its Laplacian (norm * sum of the second-derivative
+// weights), each particle's pieces added in piece order.
+__global__ void k_finalize_full(erpp_kparams kp, int64_t n, erpp_acc acc,
+                                const float4* __restrict__ lap_part,
+                                const float4* __restrict__ geo_t, const int4* __restrict__ geo_c,
+                                const double* __restrict__ y, double* up0, double* up1,
+                                double* up2, double* __restrict__ lap, int64_t lap_stride) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 gt = geo_t[i];
+  const float norm = erpp_norm(kp, gt, geo_c[i]);
+  float g[3];
+  erpp_gathered(kp, acc, gt, i, g);
+  const int np = __float_as_int(gt.w);
+  float l0 = 0.f, l1 = 0.f, l2 = 0.f;
+  for (int k = 0; k < np; ++k) {
+    const float4 v = lap_part[acc.piece_slot[(int64_t)k * acc.n + i]];
+    l0 += v.x;
+    l1 += v.y;
+    l2 += v.z;
+  }
+  up0[i] = (double)(g[0] * norm) + kp.shear_rate * y[i];
+  up1[i] = (double)(g[1] * norm);
+  up2[i] = (double)(g[2] * norm);
+  lap[i] = (double)(l0 * norm);
+  lap[lap_stride + i] = (double)(l1 * norm);
+  lap[2 * lap_stride + i] = (double)(l2 * norm);
+}
+
 erpp_acc acc_of(const erpp_ctx* ctx, int64_t n) {
   erpp_acc a;
   a.up_acc = ctx->up_acc;
@@ -623,8 +653,20 @@ cudaError_t launch_finalize_up(erpp_ctx* ctx, int64_t n, const double* const x[3
                                double* const up[3], cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int blocks = (int)((n + 255) / 256);
+  ++ctx->launches;
   k_finalize_up<<<blocks, 256, 0, st>>>(ctx->kp, n, acc_of(ctx, n), ctx->geo_t, ctx->geo_c,
                                         x[1], up[0], up[1], up[2]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_full(erpp_ctx* ctx, int64_t n, const double* const x[3],
+                                 double* const up[3], double* lap, int64_t lap_stride,
+                                 cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (int)((n + 255) / 256);
+  ++ctx->launches;
+  k_finalize_full<<<blocks, 256, 0, st>>>(ctx->kp, n, acc_of(ctx, n), ctx->lap_part, ctx->geo_t,
+                                          ctx->geo_c, x[1], up[0], up[1], up[2], lap, lap_stride);
   return cudaGetLastError();
 }
 
@@ -632,6 +674,7 @@ cudaError_t launch_prep_fscat(erpp_ctx* ctx, int64_t n, const double* const D[3]
                               cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int blocks = (int)((n + 255) / 256);
+  ++ctx->launches;
   k_prep_fscat<<<blocks, 256, 0, st>>>(ctx->kp, n, D[0], D[1], D[2], ctx->geo_t, ctx->geo_c,
                                        scale, ctx->fscat);
   return cudaGetLastError();

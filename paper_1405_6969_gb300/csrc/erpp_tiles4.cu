@@ -294,6 +294,25 @@ __device__ __forceinline__ void row_dot(unsigned a0, unsigned a1, unsigned a2, c
   }
 }
 
+// row_dot with a second set of x-weights on the same loaded values: x_c +=
+// e_x(q) u_c(q) and y_c += e2_x(q) u_c(q) (the general force's gather of the
+// velocity and of its Laplacian).
+template <int Q, int XM>
+__device__ __forceinline__ void row_dot2(unsigned a0, unsigned a1, unsigned a2,
+                                         const float (&ex)[XM], const float (&e2)[XM], float& x0,
+                                         float& x1, float& x2, float& y0, float& y1, float& y2) {
+  if constexpr (Q < XM) {
+    const float u0 = lds_f32<4 * Q>(a0), u1 = lds_f32<4 * Q>(a1), u2 = lds_f32<4 * Q>(a2);
+    x0 = fmaf(ex[Q], u0, x0);
+    x1 = fmaf(ex[Q], u1, x1);
+    x2 = fmaf(ex[Q], u2, x2);
+    y0 = fmaf(e2[Q], u0, y0);
+    y1 = fmaf(e2[Q], u1, y1);
+    y2 = fmaf(e2[Q], u2, y2);
+    row_dot2<Q + 1, XM>(a0, a1, a2, ex, e2, x0, x1, x2, y0, y1, y2);
+  }
+}
+
 template <int Q, int XM, int LMIN>
 __device__ __forceinline__ void row_red_fixed(unsigned a0, unsigned a1, unsigned a2,
                                               const int (&G0)[XM], const int (&G1)[XM],
@@ -353,13 +372,15 @@ __device__ __forceinline__ void row_red_split(unsigned a0, unsigned a1, unsigned
 
 // Dynamic shared memory of one block: the staged field (copies * plane
 // floats), then the batch's records, force words (scatter), x-distances,
-// unit words, schedule and piece accumulators (gather).
+// Laplacian moments (general-force gather), unit words, schedule and piece
+// accumulators (gather: value sums, and Laplacian sums with lap).
 template <int XW>
 struct Carve {
   float* field;
   int4* rec;
   float4* fsb;
   float* dxb;
+  float4* lcb;
   uint32_t* unit;
   uint16_t* sched;
   float* pacc;
@@ -370,21 +391,25 @@ struct Carve {
 constexpr int kFieldPad = 16;
 
 template <int XW>
-__host__ __device__ inline size_t carve_bytes(int plane, int copies, bool gather) {
+__host__ __device__ inline size_t carve_bytes(int plane, int copies, bool gather,
+                                              bool lap = false) {
   constexpr int PB = Batch<XW>::kPB, NU = Batch<XW>::kUnits;
   size_t b = ((size_t)copies * plane + kFieldPad) * 4;
   b += (size_t)PB * 16;          // rec
   if (!gather) b += (size_t)PB * 16;  // fsb
   b += (size_t)PB * 4;           // dxb
+  b = (b + 15) & ~(size_t)15;
+  if (lap) b += (size_t)PB * 32;  // lcb
   b += (size_t)NU * 4;           // unit
   b += (size_t)NU * 2;           // sched
   b = (b + 15) & ~(size_t)15;
-  if (gather) b += (size_t)3 * kMaxTz * PB * 4;  // pacc
+  if (gather) b += (size_t)(lap ? 6 : 3) * kMaxTz * PB * 4;  // pacc
   return b;
 }
 
 template <int XW>
-__device__ inline Carve<XW> carve(unsigned char* base, int plane, int copies, bool gather) {
+__device__ inline Carve<XW> carve(unsigned char* base, int plane, int copies, bool gather,
+                                  bool lap = false) {
   constexpr int PB = Batch<XW>::kPB, NU = Batch<XW>::kUnits;
   Carve<XW> c;
   size_t o = 0;
@@ -396,6 +421,9 @@ __device__ inline Carve<XW> carve(unsigned char* base, int plane, int copies, bo
   if (!gather) o += (size_t)PB * 16;
   c.dxb = reinterpret_cast<float*>(base + o);
   o += (size_t)PB * 4;
+  o = (o + 15) & ~(size_t)15;
+  c.lcb = reinterpret_cast<float4*>(base + o);
+  if (lap) o += (size_t)PB * 32;
   c.unit = reinterpret_cast<uint32_t*>(base + o);
   o += (size_t)NU * 4;
   c.sched = reinterpret_cast<uint16_t*>(base + o);
@@ -602,14 +630,19 @@ __device__ __forceinline__ int batch_size(int total, int PB) {
 __device__ __forceinline__ int4 load_rec(const int4* __restrict__ entries, int b0, int np) {
   return threadIdx.x < np ? __ldg(&entries[b0 + threadIdx.x]) : make_int4(0, 0, 0, 0);
 }
-template <int XW, bool FORCES>
+template <int XW, bool FORCES, bool LAP = false>
 __device__ void stage_batch(const Carve<XW>& cv, int4 r, int np, const float* __restrict__ d0x,
-                            const float4* __restrict__ fscat) {
+                            const float4* __restrict__ fscat,
+                            const float4* __restrict__ lapc = nullptr) {
   const int k = threadIdx.x;
   if (k < np) {
     cv.rec[k] = r;
     cp_async4(cv.dxb + k, d0x + r.x);
     if (FORCES) cp_async16(cv.fsb + k, fscat + r.x);
+    if (LAP) {
+      cp_async16(cv.lcb + 2 * k, lapc + 2 * (size_t)r.x);
+      cp_async16(cv.lcb + 2 * k + 1, lapc + 2 * (size_t)r.x + 1);
+    }
   }
 }
 
@@ -623,11 +656,15 @@ struct UnitRows {
 
 // XM: longest x-window; LMIN: shortest (slots q >= LMIN are tested); XW: 8
 // for windows of at most 7 nodes, else 16 (sets the pieces per batch).
-template <int XM, int LMIN, int XW, int NT>
+// LAP: also the Laplacian of the gathered velocity (general force, Eq.
+// force_particle): per row, the same loaded values against the x-weights'
+// second-derivative factors, and the row's and plane's own factors.
+template <int XM, int LMIN, int XW, int NT, bool LAP>
 __global__ void __launch_bounds__(NT, 2) k_gather4(
     erpp_kparams kp, const float* __restrict__ u, const __grid_constant__ CUtensorMap tmap,
     int use_tma, const int32_t* __restrict__ start, const int4* __restrict__ entries,
-    int64_t ecap, const float* __restrict__ d0x, float4* __restrict__ up_part, uint32_t* err) {
+    int64_t ecap, const float* __restrict__ d0x, const float4* __restrict__ lapc,
+    float4* __restrict__ up_part, float4* __restrict__ lap_part, uint32_t* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SchedState ss;
   __shared__ __align__(8) uint64_t tma_bar;
@@ -638,7 +675,7 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
   const int e0 = start[tile];
   const int e1 = (int)min((int64_t)start[tile + 1], ecap);
   if (e0 >= e1) return;
-  const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, 3, true);
+  const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, 3, true, LAP);
   int b[3], ext[3], tt[3];
   tile_origin4(kp, tile, b, ext, tt);
   // one TMA box when the staged rows need no periodic wrap
@@ -692,7 +729,8 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
   const unsigned fbase = shared_addr(cv.field);
   for (int b0 = e0; b0 < e1; b0 += bs) {
     const int np = min(bs, e1 - b0);
-    stage_batch<XW, false>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, d0x, nullptr);
+    stage_batch<XW, false, LAP>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, d0x,
+                                nullptr, lapc);
     const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
     cp_async_wait_all();                            // field (first batch), x-distances
     // One thread waits (bounded) for the staged field; the block learns the
@@ -721,16 +759,21 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
       const bool active = ui != kEmpty;
       UnitRows ur = {0, 0, 0, 0, 0.f, 0.f};
       int k = 0, uz = 0;
-      float ex[XM];
+      float ex[XM], e2[LAP ? XM : 1];
+      // LAP: the y-window's mean and variance and the plane's factor
+      float my = 0.f, vy = 0.f, pz = 0.f;
 #pragma unroll
       for (int q = 0; q < XM; ++q) ex[q] = 0.f;
+#pragma unroll
+      for (int q = 0; q < (LAP ? XM : 1); ++q) e2[q] = 0.f;
       if (active) {
         const uint32_t w = cv.unit[ui];
         k = (int)(w & 1023u);
         const int z = (int)((w >> 10) & 15u);
         uz = z;
         const Piece4 pc = unpack4(cv.rec[k]);
-        make_ex<XM>(pc, cv.dxb[k], bx, ex);
+        const float dx0 = cv.dxb[k];
+        make_ex<XM>(pc, dx0, bx, ex);
         ur.base = (pc.z0 + z) * pxy + pc.y0 * px + pc.x0;
         ur.ly = pc.ly;
         ur.lx = pc.lx;
@@ -738,6 +781,18 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
         ur.d0y = pc.d0y;
         const float dz = pc.d0z + (float)z;
         ur.ezz = bz * dz * dz;
+        if constexpr (LAP) {
+          const float4 c0 = cv.lcb[2 * k], c1 = cv.lcb[2 * k + 1];
+#pragma unroll
+          for (int q = 0; q < XM; ++q) {
+            const float du = dx0 + (float)(pc.qa + q) - c0.x;
+            e2[q] = ex[q] * (kp.lap_k[0] * fmaf(du, du, -c0.y));
+          }
+          my = c0.z;
+          vy = c0.w;
+          const float dzz = dz - c1.x;
+          pz = kp.lap_k[2] * fmaf(dzz, dzz, -c1.y);
+        }
       }
       const int rows = __reduce_max_sync(0xffffffffu, (unsigned)ur.ly);
       // Straight-line rows: rows past the unit's own length get weight 0,
@@ -746,6 +801,7 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
       // summed in row order and the first row's term is added at the end, so
       // that the unit's sum does not depend on where its walk started.
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, r0 = 0.f, r1 = 0.f, r2 = 0.f;
+      float l0 = 0.f, l1 = 0.f, l2 = 0.f, q0 = 0.f, q1 = 0.f, q2 = 0.f;  // LAP
       const unsigned pl4 = 4u * (unsigned)plane, px4 = 4u * (unsigned)px;
       const unsigned abase = fbase + 4u * (unsigned)(active ? ur.base : lane);
       const unsigned aend = abase + px4 * (unsigned)ur.ly;
@@ -757,15 +813,35 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
         const bool in = t < ur.ly;
         const float wr = in ? e : 0.f;
         float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-        row_dot<0, XM>(ar, ar + pl4, ar + 2 * pl4, ex, x0, x1, x2);
+        float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+        if constexpr (LAP)
+          row_dot2<0, XM>(ar, ar + pl4, ar + 2 * pl4, ex, e2, x0, x1, x2, y0, y1, y2);
+        else
+          row_dot<0, XM>(ar, ar + pl4, ar + 2 * pl4, ex, x0, x1, x2);
+        // LAP: the row's Laplacian term, (P_y + P_z) x_c + y_c
+        float pr = 0.f;
+        if (LAP) {
+          const float ddy = dy - my;
+          pr = fmaf(kp.lap_k[1], fmaf(ddy, ddy, -vy), pz);
+        }
         if (in && ar == abase) {
           r0 = wr * x0;
           r1 = wr * x1;
           r2 = wr * x2;
+          if (LAP) {
+            q0 = wr * fmaf(pr, x0, y0);
+            q1 = wr * fmaf(pr, x1, y1);
+            q2 = wr * fmaf(pr, x2, y2);
+          }
         } else {
           a0 = fmaf(wr, x0, a0);
           a1 = fmaf(wr, x1, a1);
           a2 = fmaf(wr, x2, a2);
+          if (LAP) {
+            l0 = fmaf(wr, fmaf(pr, x0, y0), l0);
+            l1 = fmaf(wr, fmaf(pr, x1, y1), l1);
+            l2 = fmaf(wr, fmaf(pr, x2, y2), l2);
+          }
         }
         ar += px4;
         dy += 1.f;
@@ -779,6 +855,11 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
         pa[0] = a0 + r0;
         pa[kMaxTz * PB] = a1 + r1;
         pa[2 * kMaxTz * PB] = a2 + r2;
+        if (LAP) {
+          pa[3 * kMaxTz * PB] = l0 + q0;
+          pa[4 * kMaxTz * PB] = l1 + q1;
+          pa[5 * kMaxTz * PB] = l2 + q2;
+        }
       }
     }
     __syncthreads();
@@ -794,6 +875,15 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
         s2 += cv.pacc[(2 * kMaxTz + z) * PB + k];
       }
       up_part[b0 + k] = make_float4(s0, s1, s2, 0.f);
+      if (LAP) {
+        float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+        for (int z = 0; z < lz; ++z) {
+          t0 += cv.pacc[(3 * kMaxTz + z) * PB + k];
+          t1 += cv.pacc[(4 * kMaxTz + z) * PB + k];
+          t2 += cv.pacc[(5 * kMaxTz + z) * PB + k];
+        }
+        lap_part[b0 + k] = make_float4(t0, t1, t2, 0.f);
+      }
     }
     __syncthreads();
   }
@@ -1352,27 +1442,33 @@ bool field_tensor_map(const erpp_kparams& kp, const float* u, CUtensorMap* map) 
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int XM, int LMIN, int XW, int NT>
+template <int XM, int LMIN, int XW, int NT, bool LAP>
 cudaError_t gather4_nt(erpp_ctx* ctx, const float* u, cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;
-  const size_t sm = carve_bytes<XW>(kp.plane, 3, true);
-  cudaError_t e = cudaFuncSetAttribute(k_gather4<XM, LMIN, XW, NT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (LAP && (!ctx->lapc || !ctx->lap_part)) return cudaErrorInvalidValue;
+  const size_t sm = carve_bytes<XW>(kp.plane, 3, true, LAP);
+  auto kern = k_gather4<XM, LMIN, XW, NT, LAP>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   CUtensorMap map;
   memset(&map, 0, sizeof(map));
   const int use_tma = field_tensor_map(kp, u, &map) ? 1 : 0;
   ++ctx->launches;
-  k_gather4<XM, LMIN, XW, NT><<<kp.ntiles, NT, sm, st>>>(kp, u, map, use_tma, ctx->tile_start,
-                                                         ctx->entries, ctx->entries_cap,
-                                                         ctx->d0x, ctx->up_part, ctx->err);
+  kern<<<kp.ntiles, NT, sm, st>>>(kp, u, map, use_tma, ctx->tile_start, ctx->entries,
+                                  ctx->entries_cap, ctx->d0x, ctx->lapc, ctx->up_part,
+                                  ctx->lap_part, ctx->err);
   return cudaGetLastError();
 }
 
-template <int XM, int LMIN, int XW>
+// LAP (the general force's gather) always runs 256-thread blocks.
+template <int XM, int LMIN, int XW, bool LAP = false>
 cudaError_t gather4(erpp_ctx* ctx, const float* u, cudaStream_t st) {
-  return ctx->kp.nthreads == 512 ? gather4_nt<XM, LMIN, XW, 512>(ctx, u, st)
-                                 : gather4_nt<XM, LMIN, XW, 256>(ctx, u, st);
+  if constexpr (LAP) {
+    return gather4_nt<XM, LMIN, XW, 256, true>(ctx, u, st);
+  } else {
+    return ctx->kp.nthreads == 512 ? gather4_nt<XM, LMIN, XW, 512, false>(ctx, u, st)
+                                   : gather4_nt<XM, LMIN, XW, 256, false>(ctx, u, st);
+  }
 }
 
 // Launches k_scatter4; CL: as thread-block clusters of the nt[0] x-tiles of a
@@ -1480,22 +1576,33 @@ int xw4(const erpp_kparams& kp) {
 }
 
 // Dynamic shared memory of the design-4 kernels (host side of the carve),
-// for the batch width the launched variant uses.
+// for the batch width the launched variant uses; a general-force context's
+// gather also stages the Laplacian moments and sums.
 size_t smem_bytes4(const erpp_kparams& kp, int copies, bool gather) {
-  return xw4(kp) == 8 ? carve_bytes<8>(kp.plane, copies, gather)
-                      : carve_bytes<16>(kp.plane, copies, gather);
+  const bool lap = gather && kp.full_force;
+  return xw4(kp) == 8 ? carve_bytes<8>(kp.plane, copies, gather, lap)
+                      : carve_bytes<16>(kp.plane, copies, gather, lap);
+}
+
+template <bool LAP>
+cudaError_t gather4_variant(erpp_ctx* ctx, const float* u, cudaStream_t st) {
+  switch (variant4(ctx->kp)) {
+    case 0: return gather4<7, 6, 8, LAP>(ctx, u, st);
+    case 1: return gather4<7, 5, 8, LAP>(ctx, u, st);
+    case 2: return gather4<10, 9, 16, LAP>(ctx, u, st);
+    case 3: return gather4<10, 8, 16, LAP>(ctx, u, st);
+    case 5: return gather4<7, 1, 8, LAP>(ctx, u, st);
+    case 6: return gather4<10, 1, 16, LAP>(ctx, u, st);
+    default: return gather4<16, 1, 16, LAP>(ctx, u, st);
+  }
 }
 
 cudaError_t launch_gather_f32_4(erpp_ctx* ctx, const float* u, cudaStream_t st) {
-  switch (variant4(ctx->kp)) {
-    case 0: return gather4<7, 6, 8>(ctx, u, st);
-    case 1: return gather4<7, 5, 8>(ctx, u, st);
-    case 2: return gather4<10, 9, 16>(ctx, u, st);
-    case 3: return gather4<10, 8, 16>(ctx, u, st);
-    case 5: return gather4<7, 1, 8>(ctx, u, st);
-    case 6: return gather4<10, 1, 16>(ctx, u, st);
-    default: return gather4<16, 1, 16>(ctx, u, st);
-  }
+  return gather4_variant<false>(ctx, u, st);
+}
+
+cudaError_t launch_gather_lap_f32_4(erpp_ctx* ctx, const float* u, cudaStream_t st) {
+  return gather4_variant<true>(ctx, u, st);
 }
 
 cudaError_t launch_scatter_f32_4(erpp_ctx* ctx, float* S, cudaStream_t st) {

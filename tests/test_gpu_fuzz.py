@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 
 import erpp_inputs as I
+from test_gpu_full_force import _fp32_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -112,7 +113,8 @@ def test_fuzz_options(erpp, oracle_lib, kind, seed):
     their oracle steps: PIC and point-value weights, the source delayed by
     L = 2 steps (dt = eps_R / 2 with nu = 1 and particles of radius 0.05, so
     that the step stays short and stable), the general force (rho_p / rho_f =
-    2, radius 0.05)."""
+    2, radius 0.05; in FP32 within the bound that the one-step differences of
+    u~ set on the gather's rounding, as in the general-force parity tests)."""
     import torch
     from oracle import full_force as FF
     from oracle import lagged as LG
@@ -135,7 +137,7 @@ def test_fuzz_options(erpp, oracle_lib, kind, seed):
     opts = {"pic": dict(weights="pic"), "point": dict(weights="point"),
             "lag": dict(lag=True), "full": dict(full_force=True)}[kind]
     for precision in ("fp32", "fp64"):
-        tol = (5e-5 if kind == "full" else 1e-5) if precision == "fp32" else 1e-11
+        tol = 1e-5 if precision == "fp32" else 1e-11
         dtype = torch.float32 if precision == "fp32" else torch.float64
         ctx = erpp.Context(p, precision=precision, **opts)
         ps = erpp.ParticleState.from_numpy(st)
@@ -151,6 +153,8 @@ def test_fuzz_options(erpp, oracle_lib, kind, seed):
                 S_ref = LG.step(p, grid, ref, hist, first_step=first)
             else:
                 S_ref = FF.step(p, grid, ref, hist, first_step=first)
+                if precision == "fp32" and not first:
+                    tol = _fp32_bound(p, st, hist.ut, ref.D)
             got = S.cpu().numpy()
             if np.abs(S_ref).max() == 0.0:
                 assert float(np.abs(got).max()) == 0.0, (precision, k)
