@@ -296,9 +296,10 @@ erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c) {
   for (int a = 0; a < 3; ++a) {
     kp.grav_f[a] = (float)p->gravity[a];
     kp.halfL_f[a] = (float)(0.5 * L[a]);
-    // a float position at least 1e-4 L inside the box is certainly inside it
-    kp.wrap_lo_f[a] = (float)(1e-4 * L[a]);
-    kp.wrap_hi_f[a] = (float)((1.0 - 1e-4) * L[a]);
+    // a position at least 1e-4 L inside the box needs no periodic wrap
+    const double wlo = 1e-4 * L[a], whi = (1.0 - 1e-4) * L[a];
+    memcpy(&kp.wrap_lo_bits[a], &wlo, sizeof(double));
+    memcpy(&kp.wrap_hi_bits[a], &whi, sizeof(double));
   }
   const double log2e = 1.4426950408889634;
   for (int a = 0; a < 3; ++a) {

@@ -320,12 +320,14 @@ __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, Par
       const double d = x[a] - P.xs[a][i];
       // the exact minimum-image test only where the float difference is
       // near half the box
-      r[a] = fabsf((float)d) > 0.99f * kp.halfL_f[a] ? min_image(d, kp.L[a]) : d;
+      r[a] = fabsf(erpp_d2f(d)) > 0.99f * kp.halfL_f[a] ? min_image(d, kp.L[a]) : d;
       D[a] = P.Ds[a][i];
     }
     if (F32) {
-      float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
-      float Df[3] = {(float)D[0], (float)D[1], (float)D[2]};
+      // conversions by integer operations (erpp_d2f): same values, off the
+      // FP64 pipe that bounds this kernel
+      float rf[3] = {erpp_d2f(r[0]), erpp_d2f(r[1]), erpp_d2f(r[2])};
+      float Df[3] = {erpp_d2f(D[0]), erpp_d2f(D[1]), erpp_d2f(D[2])};
       self_velocity_f32(kp, rf, Df, vsf);
     } else {
       self_velocity_f64(kp, r, D, vs);
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, Par
   double Dn[3];
   float Dnf[3];
   if (F32) {
-    const float af = (float)a_p, rf = (float)rho;
+    const float af = erpp_d2f(a_p), rf = erpp_d2f(rho);
     const float k_drag = kp.drag_f * af;
     const float inv_m = 1.f / ((float)(4.0 / 3.0 * pi) * af * af * af * rf);
     const float buoy = 1.f - kp.rho_f_f / rf;
@@ -347,20 +349,22 @@ __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, Par
       // caller's FP64 velocity (shear included): subtract in FP64
       double ut;
       if (FROM_ACC) {
-        ut = (double)(upf[a] - vsf[a]);
+        ut = erpp_f2d(upf[a] - vsf[a]);
         if (a == 0) ut += kp.shear_rate * x[1];
       } else {
-        ut = up[a] - (double)vsf[a];
+        ut = up[a] - erpp_f2d(vsf[a]);
       }
-      const float slip = (float)(ut - v[a]);
+      const float slip = erpp_d2f(ut - v[a]);
       const float Df = k_drag * slip;
       const float dv = kp.dt_f * (Df * inv_m + buoy * kp.grav_f[a]);
       Dnf[a] = Df;
-      Dn[a] = (double)Df;
-      P.v[a][i] = v[a] + (double)dv;
+      Dn[a] = erpp_f2d(Df);
+      P.v[a][i] = v[a] + erpp_f2d(dv);
       double xn = x[a] + kp.dt * v[a];
-      const float xf = (float)xn;
-      if (!(xf > kp.wrap_lo_f[a] && xf < kp.wrap_hi_f[a])) xn = wrap_coord(xn, kp.L[a]);
+      // inside [1e-4 L, (1 - 1e-4) L] no wrap is needed (an integer compare
+      // of the bit patterns; negative values and NaN fall outside)
+      const int64_t xb = __double_as_longlong(xn);
+      if (!(xb > kp.wrap_lo_bits[a] && xb < kp.wrap_hi_bits[a])) xn = wrap_coord(xn, kp.L[a]);
       P.x[a][i] = xn;
       P.xp[a][i] = x[a];
       P.D[a][i] = Dn[a];

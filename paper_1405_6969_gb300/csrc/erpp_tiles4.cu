@@ -91,7 +91,6 @@ constexpr uint16_t kEmpty = 0xffffu;
 template <int XW>
 struct Batch {
   static constexpr int kPB = XW <= 8 ? 256 : 128;
-  static constexpr int kUnits = kPB * kMaxTz;
 };
 
 // Piece record (from the binning): p, packed geometry, d0y, d0z (distances,
@@ -390,10 +389,14 @@ struct Carve {
 // slots may reach past the last staged row.
 constexpr int kFieldPad = 16;
 
+// The unit words, the schedule and the gather's piece accumulators are sized
+// for the tile's tz planes (a piece has at most tz units); the schedule holds
+// whole rounds of up to 512 threads.
 template <int XW>
-__host__ __device__ inline size_t carve_bytes(int plane, int copies, bool gather,
+__host__ __device__ inline size_t carve_bytes(int plane, int tz, int copies, bool gather,
                                               bool lap = false) {
-  constexpr int PB = Batch<XW>::kPB, NU = Batch<XW>::kUnits;
+  constexpr int PB = Batch<XW>::kPB;
+  const int NU = PB * tz, NS = (NU + 511) & ~511;
   size_t b = ((size_t)copies * plane + kFieldPad) * 4;
   b += (size_t)PB * 16;          // rec
   if (!gather) b += (size_t)PB * 16;  // fsb
@@ -401,16 +404,17 @@ __host__ __device__ inline size_t carve_bytes(int plane, int copies, bool gather
   b = (b + 15) & ~(size_t)15;
   if (lap) b += (size_t)PB * 32;  // lcb
   b += (size_t)NU * 4;           // unit
-  b += (size_t)NU * 2;           // sched
+  b += (size_t)NS * 2;           // sched
   b = (b + 15) & ~(size_t)15;
-  if (gather) b += (size_t)(lap ? 6 : 3) * kMaxTz * PB * 4;  // pacc
+  if (gather) b += (size_t)(lap ? 6 : 3) * tz * PB * 4;  // pacc
   return b;
 }
 
 template <int XW>
-__device__ inline Carve<XW> carve(unsigned char* base, int plane, int copies, bool gather,
+__device__ inline Carve<XW> carve(unsigned char* base, int plane, int tz, int copies, bool gather,
                                   bool lap = false) {
-  constexpr int PB = Batch<XW>::kPB, NU = Batch<XW>::kUnits;
+  constexpr int PB = Batch<XW>::kPB;
+  const int NU = PB * tz, NS = (NU + 511) & ~511;
   Carve<XW> c;
   size_t o = 0;
   c.field = reinterpret_cast<float*>(base);
@@ -427,7 +431,7 @@ __device__ inline Carve<XW> carve(unsigned char* base, int plane, int copies, bo
   c.unit = reinterpret_cast<uint32_t*>(base + o);
   o += (size_t)NU * 4;
   c.sched = reinterpret_cast<uint16_t*>(base + o);
-  o += (size_t)NU * 2;
+  o += (size_t)NS * 2;
   o = (o + 15) & ~(size_t)15;
   c.pacc = reinterpret_cast<float*>(base + o);
   return c;
@@ -660,7 +664,7 @@ struct UnitRows {
 // force_particle): per row, the same loaded values against the x-weights'
 // second-derivative factors, and the row's and plane's own factors.
 template <int XM, int LMIN, int XW, int NT, bool LAP>
-__global__ void __launch_bounds__(NT, 2) k_gather4(
+__global__ void __launch_bounds__(NT, LAP ? 2 : 768 / NT) k_gather4(
     erpp_kparams kp, const float* __restrict__ u, const __grid_constant__ CUtensorMap tmap,
     int use_tma, const int32_t* __restrict__ start, const int4* __restrict__ entries,
     int64_t ecap, const float* __restrict__ d0x, const float4* __restrict__ lapc,
@@ -675,7 +679,8 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
   const int e0 = start[tile];
   const int e1 = (int)min((int64_t)start[tile + 1], ecap);
   if (e0 >= e1) return;
-  const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, 3, true, LAP);
+  const int tzs = kp.T[2];  // planes per tile: units per piece, at most
+  const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, tzs, 3, true, LAP);
   int b[3], ext[3], tt[3];
   tile_origin4(kp, tile, b, ext, tt);
   // one TMA box when the staged rows need no periodic wrap
@@ -853,12 +858,12 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
         // the unit's own slot (piece k, plane uz): no two units share one
         float* pa = cv.pacc + uz * PB + k;
         pa[0] = a0 + r0;
-        pa[kMaxTz * PB] = a1 + r1;
-        pa[2 * kMaxTz * PB] = a2 + r2;
+        pa[tzs * PB] = a1 + r1;
+        pa[2 * tzs * PB] = a2 + r2;
         if (LAP) {
-          pa[3 * kMaxTz * PB] = l0 + q0;
-          pa[4 * kMaxTz * PB] = l1 + q1;
-          pa[5 * kMaxTz * PB] = l2 + q2;
+          pa[3 * tzs * PB] = l0 + q0;
+          pa[4 * tzs * PB] = l1 + q1;
+          pa[5 * tzs * PB] = l2 + q2;
         }
       }
     }
@@ -871,16 +876,16 @@ __global__ void __launch_bounds__(NT, 2) k_gather4(
       float s0 = 0.f, s1 = 0.f, s2 = 0.f;
       for (int z = 0; z < lz; ++z) {
         s0 += cv.pacc[z * PB + k];
-        s1 += cv.pacc[(kMaxTz + z) * PB + k];
-        s2 += cv.pacc[(2 * kMaxTz + z) * PB + k];
+        s1 += cv.pacc[(tzs + z) * PB + k];
+        s2 += cv.pacc[(2 * tzs + z) * PB + k];
       }
       up_part[b0 + k] = make_float4(s0, s1, s2, 0.f);
       if (LAP) {
         float t0 = 0.f, t1 = 0.f, t2 = 0.f;
         for (int z = 0; z < lz; ++z) {
-          t0 += cv.pacc[(3 * kMaxTz + z) * PB + k];
-          t1 += cv.pacc[(4 * kMaxTz + z) * PB + k];
-          t2 += cv.pacc[(5 * kMaxTz + z) * PB + k];
+          t0 += cv.pacc[(3 * tzs + z) * PB + k];
+          t1 += cv.pacc[(4 * tzs + z) * PB + k];
+          t2 += cv.pacc[(5 * tzs + z) * PB + k];
         }
         lap_part[b0 + k] = make_float4(t0, t1, t2, 0.f);
       }
@@ -1105,7 +1110,7 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
 }
 
 template <int XM, int LMIN, int XW, int MODE, int NT, bool CL>
-__global__ void __launch_bounds__(NT, 2) k_scatter4(
+__global__ void __launch_bounds__(NT, MODE == 0 ? 1024 / NT : 2) k_scatter4(
     erpp_kparams kp, float* __restrict__ S, float* __restrict__ halo,
     const int32_t* __restrict__ start, const int4* __restrict__ entries, int64_t ecap,
     const float* __restrict__ d0x, const float4* __restrict__ fscat) {
@@ -1116,7 +1121,7 @@ __global__ void __launch_bounds__(NT, 2) k_scatter4(
   constexpr int PB = Batch<XW>::kPB;
   static_assert(PB <= NT, "a batch holds at most one piece per thread");
   const int tile = blockIdx.x;
-  const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, MODE == 1 ? 6 : 3, false);
+  const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, kp.T[2], MODE == 1 ? 6 : 3, false);
   float* smem = cv.field;
   const TileAcc ta =
       scatter_tile<XM, LMIN, XW, MODE, NT>(kp, tile, cv, ss, red, start, entries, ecap, d0x,
@@ -1446,7 +1451,7 @@ template <int XM, int LMIN, int XW, int NT, bool LAP>
 cudaError_t gather4_nt(erpp_ctx* ctx, const float* u, cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;
   if (LAP && (!ctx->lapc || !ctx->lap_part)) return cudaErrorInvalidValue;
-  const size_t sm = carve_bytes<XW>(kp.plane, 3, true, LAP);
+  const size_t sm = carve_bytes<XW>(kp.plane, kp.T[2], 3, true, LAP);
   auto kern = k_gather4<XM, LMIN, XW, NT, LAP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -1477,7 +1482,7 @@ cudaError_t gather4(erpp_ctx* ctx, const float* u, cudaStream_t st) {
 template <int XM, int LMIN, int XW, int MODE, int NT, bool CL>
 cudaError_t scatter4_mode(erpp_ctx* ctx, float* S, cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;
-  const size_t sm = carve_bytes<XW>(kp.plane, MODE == 1 ? 6 : 3, false);
+  const size_t sm = carve_bytes<XW>(kp.plane, kp.T[2], MODE == 1 ? 6 : 3, false);
   auto kern = k_scatter4<XM, LMIN, XW, MODE, NT, CL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -1580,8 +1585,9 @@ int xw4(const erpp_kparams& kp) {
 // gather also stages the Laplacian moments and sums.
 size_t smem_bytes4(const erpp_kparams& kp, int copies, bool gather) {
   const bool lap = gather && kp.full_force;
-  return xw4(kp) == 8 ? carve_bytes<8>(kp.plane, copies, gather, lap)
-                      : carve_bytes<16>(kp.plane, copies, gather, lap);
+  const int tz = kp.plane / kp.pxy;
+  return xw4(kp) == 8 ? carve_bytes<8>(kp.plane, tz, copies, gather, lap)
+                      : carve_bytes<16>(kp.plane, tz, copies, gather, lap);
 }
 
 template <bool LAP>
