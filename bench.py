@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--tiling", default=None,
                     help="fixed tile shape TYxTZ[xTHREADS] (for example 32x2x256) instead of "
                          "the autotuner")
+    ap.add_argument("--scatter-mode", default=None, choices=["merge", "cluster", "xclip"],
+                    help="with --tiling: how tile halos reach their neighbours (default merge)")
     ap.add_argument("--no-loop", action="store_true",
                     help="skip the closed-loop (coupling + fluid stand-in) timing")
     ap.add_argument("--no-variants", action="store_true",
@@ -176,10 +178,10 @@ def algorithmic_bytes(w, n_p):
             "step": 24 * w.n_nodes + 208 * n_p}
 
 
-def captured_traffic(w, kernel, tiling):
+def captured_traffic(w, kernel, tiling, mode):
     """DRAM bytes (read + write) per launch of the dominant phase from the ncu
     capture summarised in profiles/, when it was taken on this workload, tile
-    shape and kernel source; else None."""
+    shape, halo mode and kernel source; else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "erpp_step_shear512_traffic.json")
     try:
@@ -190,9 +192,9 @@ def captured_traffic(w, kernel, tiling):
     except (OSError, ValueError, KeyError):
         return None
     if (d.get("workload") != w.name or kernel != "scatter" or sha != d.get("source_sha256")
-            or list(tiling[2:5]) != list(d.get("tiling", []))):
+            or list(tiling[2:5]) != list(d.get("tiling", [])) or mode not in d.get("modes", {})):
         return None
-    return d["traffic_bytes"]
+    return d["modes"][mode]["traffic_bytes"]
 
 
 def run_reference(args, ws, rank):
@@ -441,6 +443,8 @@ def workload_record(w, args, peak, kahan=False, steps=100, made=None):
     if args.tiling:
         t = [int(v) for v in args.tiling.lower().split("x")] + [0]
         ctx.set_tiling(t[0], t[1], t[2])
+        if args.scatter_mode:
+            ctx.set_scatter_mode(args.scatter_mode)
     elif not args.no_autotune:
         from paper_1405_6969_gb300 import autotune
         autotune.tune(ctx, u, ps, S=S, use_cache=False)
@@ -534,7 +538,10 @@ def main():
     if args.tiling:
         t = [int(v) for v in args.tiling.lower().split("x")] + [0]
         ctx.set_tiling(t[0], t[1], t[2])
-        tiling = {"tile": tuple(t[:3]), "tiling": ctx.tiling(), "ms": None, "cached": False}
+        if args.scatter_mode:
+            ctx.set_scatter_mode(args.scatter_mode)
+        tiling = {"tile": tuple(t[:3]), "mode": ctx.scatter_mode(), "tiling": ctx.tiling(),
+                  "ms": None, "cached": False}
     elif args.lag:
         # the first round(eps_R/dt) delayed steps have no source to time: keep
         # the tile shape the autotuner picks for this workload without delay
@@ -603,7 +610,7 @@ def main():
         achieved = alg[dom] / (per[dom] * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                     "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": captured_traffic(w, dom, ctx.tiling()),
+                    "traffic": captured_traffic(w, dom, ctx.tiling(), ctx.scatter_mode()),
                     "peak_kind": peak_kind}
     step_gbs = alg["step"] / (ms_per_step * 1e-3) / 1e9
 
