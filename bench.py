@@ -362,8 +362,14 @@ def batched_record(args, ws, rank, steps, peak):
     time.sleep(0.3)
     ms_graph = timed(b32, True, steps)
     clocks = sampler.stop()
+    launches_per_step = b32.last_step_launches()  # the graph's kernels
     ms_eager = timed(b32, False, max(3, steps // 4))
-    launches_per_step = b32.last_step_launches()
+    # the other graph form: nine kernels over all boxes (persistent gather and
+    # scatter over (box, tile) work items)
+    b32.set_form("multi")
+    ms_multi = timed(b32, True, steps)
+    multi_launches = b32.last_step_launches()
+    b32.set_form("branches")
     b32.close()
     b64, _ = batch("fp64")
     ms_f64 = timed(b64, False, max(3, min(steps // 10, 10)))
@@ -388,6 +394,9 @@ def batched_record(args, ws, rank, steps, peak):
         "steps_per_s": 1e3 / ms_graph,
         "plain_launches_ms_per_step": ms_eager,
         "graph_speedup_vs_plain_launches": ms_eager / ms_graph,
+        "multi_box_form": {"ms_per_step": ms_multi, "gpu_launches_per_step": multi_launches,
+                           "note": "the same step as nine kernels over all boxes "
+                                   "(erpp_batch_set_form multi)"},
         "fp64_plain_form_ms_per_step": ms_f64,
         "speedup_vs_fp64_plain_form": ms_f64 / ms_graph,
         "accuracy_fp32_vs_fp64_plain": dict(accuracy, tolerance=1e-5,

@@ -349,14 +349,29 @@ typedef struct erpp_batch erpp_batch;
 erpp_status erpp_batch_init(int32_t nbox, const erpp_box_desc* boxes, erpp_batch** out);
 
 /* One coupling step (erpp_step) of every box, asynchronous on `stream`.
- * use_graph != 0: the first call for each value of first_step captures all
- * boxes' launch sequences into one CUDA graph (one independent branch per
- * box, boxes run concurrently) and every call replays it with a single graph
- * launch on `stream`; the capture itself makes no allocation.  use_graph ==
- * 0: the boxes' launches are issued one box after another on `stream`.
- * Both forms compute the same thing. */
+ * use_graph != 0: the first call for each value of first_step captures the
+ * step into one CUDA graph and every call replays it with a single graph
+ * launch on `stream`; the graph's form is set by erpp_batch_set_form.
+ * use_graph == 0: each box's erpp_step, one box after another on `stream`.
+ * All forms compute the same thing. */
 erpp_status erpp_step_batched(erpp_batch* batch, int first_step, int use_graph,
                               erpp_stream stream);
+
+/* The form of the batched graph (not in the paper, which treats one box):
+ *   ERPP_BATCH_BRANCHES (default): one independent branch per box with the
+ *     box's own launches; the boxes run concurrently.
+ *   ERPP_BATCH_MULTI: nine kernels for all boxes together: the binning in
+ *     four (counts cleared, counted, scanned per box, records filled), a
+ *     persistent gather whose blocks pull (box, tile) work items, densest
+ *     boxes first, from a counter, the advance, a persistent scatter and the
+ *     two halo merges.  Needs every box on the FP32 step with x/y-halo tiles,
+ *     the fixed-point scatter and windows of the same longest length, else
+ *     the branches are captured.  The first graph call in this form builds
+ *     the boxes' device descriptors (a small device allocation, before the
+ *     capture).
+ * Discards captured graphs.  ERPP_EINVAL for other values. */
+enum { ERPP_BATCH_BRANCHES = 0, ERPP_BATCH_MULTI = 1 };
+erpp_status erpp_batch_set_form(erpp_batch* batch, int32_t form);
 
 /* erpp_set_tiling for one box (0 <= box < nbox) of the batch; the box's
  * scratch is reallocated at once and captured graphs are discarded (the next
@@ -368,9 +383,10 @@ erpp_status erpp_batch_set_tiling(erpp_batch* batch, int32_t box, int32_t tile_y
  * HOST array of 5. */
 erpp_status erpp_batch_get_tiling(erpp_batch* batch, int32_t box, int32_t out[5]);
 
-/* Sum over the boxes of erpp_last_step_launches: the kernels of one batched
- * step (a captured graph replays the sequences recorded at capture), written
- * to the HOST int *n. */
+/* The kernels of one batched step, written to the HOST int *n: the sum over
+ * the boxes of erpp_last_step_launches, plus the nine multi-box kernels when
+ * the graph holds them (a captured graph replays what was recorded at
+ * capture). */
 erpp_status erpp_batch_last_step_launches(erpp_batch* batch, int32_t* n);
 
 /* erpp_check over every box: synchronises `stream`, returns the first error

@@ -98,6 +98,7 @@ _SIGS = {
     "erpp_batch_set_tiling": (_st, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_int32]),
     "erpp_batch_destroy": (_st, [_vp]),
+    "erpp_batch_set_form": (_st, [_vp, ctypes.c_int32]),
     "erpp_set_tiling": (_st, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "erpp_get_tiling": (_st, [_vp, ctypes.POINTER(ctypes.c_int32)]),
     "erpp_set_scatter_mode": (_st, [_vp, ctypes.c_int32]),

@@ -12,12 +12,26 @@
 // concurrently.  Without a graph the same sequences are issued box after box
 // on the caller's stream (plain launches, for comparison).
 //
+// In the multi-box form (erpp_batch_set_form), when every box runs the FP32
+// step on x/y-halo tiles with compatible window variants and the fixed-point
+// scatter, the graph instead holds nine launches for all boxes together: the
+// binning (counts cleared, counted, scanned per box, records filled), ONE
+// persistent gather over the (box, tile) work items of every box (densest
+// boxes first, pulled from a counter), the advance of every particle, ONE
+// persistent scatter, and the two halo merges.  Each phase then waits for
+// every box's previous phase, where the branches let one box's binning
+// overlap another's gather: on many small dense boxes the branches are the
+// faster form (the binning's atomic increments of few tile counters, for
+// one, are no longer hidden behind other boxes' work).
+//
 // The graph holds the descriptors' device pointers: the buffers must stay
 // allocated and in place for the batch's lifetime (their contents change
 // freely between steps).
 #include <cuda_runtime.h>
 #include <stdlib.h>
 #include <string.h>
+
+#include <vector>
 
 #include "erpp_internal.cuh"
 
@@ -30,9 +44,15 @@ struct erpp_batch {
   cudaEvent_t fork;
   cudaEvent_t* join;
   cudaGraphExec_t exec[2];  // [first_step]
+  erpp::Multi4* multi;      // multi-box tile launches, or null
+  int32_t form;             // ERPP_BATCH_BRANCHES or ERPP_BATCH_MULTI
 };
 
 namespace {
+
+// Kernels of the multi-box step: clear, count, scan, fill, gather, advance,
+// scatter, row merge, column merge.
+constexpr int32_t kMultiLaunches = 9;
 
 erpp_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return ERPP_OK;
@@ -41,19 +61,45 @@ erpp_status cuda_status(cudaError_t e) {
 }
 
 erpp_status capture(erpp_batch* b, int first_step) {
+  if (!b->multi && b->form == ERPP_BATCH_MULTI) {
+    // the multi-box launches need every box's scratch in place and the same
+    // kernel variant; otherwise each box's own step is captured
+    std::vector<erpp_ctx*> cs(b->ctx, b->ctx + b->nbox);
+    if (erpp::multi4_eligible(cs.data(), b->nbox)) {
+      std::vector<const float*> us((size_t)b->nbox);
+      std::vector<float*> ss((size_t)b->nbox);
+      std::vector<erpp_particles> ps((size_t)b->nbox);
+      for (int i = 0; i < b->nbox; ++i) {
+        us[(size_t)i] = (const float*)b->boxes[i].u;
+        ss[(size_t)i] = (float*)b->boxes[i].S;
+        ps[(size_t)i] = b->boxes[i].particles;
+      }
+      if (erpp::multi4_create(cs.data(), us.data(), ss.data(), ps.data(), b->nbox, &b->multi) !=
+          cudaSuccess) {
+        b->multi = nullptr;
+        cudaGetLastError();
+      }
+    }
+  }
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return cuda_status(e);
   erpp_status s = ERPP_OK;
-  e = cudaEventRecord(b->fork, b->origin);
-  for (int i = 0; i < b->nbox && e == cudaSuccess && s == ERPP_OK; ++i) {
-    e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
-    if (e != cudaSuccess) break;
-    const erpp_box_desc& d = b->boxes[i];
-    s = erpp_step(b->ctx[i], d.u, &d.particles, d.S, first_step, (erpp_stream)b->branch[i]);
-    if (s != ERPP_OK) break;
-    e = cudaEventRecord(b->join[i], b->branch[i]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->join[i], 0);
+  if (b->multi) {
+    // one stream: binning, gather, advance, scatter and merges of all boxes
+    for (int i = 0; i < b->nbox; ++i) b->ctx[i]->last_step_launches = 0;
+    e = erpp::multi4_step(b->multi, first_step, b->origin);
+  } else {
+    e = cudaEventRecord(b->fork, b->origin);
+    for (int i = 0; i < b->nbox && e == cudaSuccess && s == ERPP_OK; ++i) {
+      e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+      if (e != cudaSuccess) break;
+      const erpp_box_desc& d = b->boxes[i];
+      s = erpp_step(b->ctx[i], d.u, &d.particles, d.S, first_step, (erpp_stream)b->branch[i]);
+      if (s != ERPP_OK) break;
+      e = cudaEventRecord(b->join[i], b->branch[i]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->join[i], 0);
+    }
   }
   // always end the capture (a failed capture is discarded)
   cudaError_t e2 = cudaStreamEndCapture(b->origin, &graph);
@@ -82,6 +128,7 @@ erpp_status erpp_batch_destroy(erpp_batch* b) {
   cudaDeviceSynchronize();
   for (int k = 0; k < 2; ++k)
     if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+  erpp::multi4_destroy(b->multi);
   if (b->ctx)
     for (int i = 0; i < b->nbox; ++i) erpp_destroy(b->ctx[i]);
   if (b->branch)
@@ -185,7 +232,25 @@ erpp_status erpp_batch_set_tiling(erpp_batch* b, int32_t box, int32_t tile_y, in
     if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
     b->exec[k] = nullptr;
   }
+  // the multi-box descriptors hold the old scratch and tile shape
+  cudaDeviceSynchronize();
+  erpp::multi4_destroy(b->multi);
+  b->multi = nullptr;
   return s;
+}
+
+erpp_status erpp_batch_set_form(erpp_batch* b, int32_t form) {
+  if (!b || (form != ERPP_BATCH_BRANCHES && form != ERPP_BATCH_MULTI)) return ERPP_EINVAL;
+  if (form == b->form) return ERPP_OK;
+  b->form = form;
+  cudaDeviceSynchronize();
+  for (int k = 0; k < 2; ++k) {
+    if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+    b->exec[k] = nullptr;
+  }
+  erpp::multi4_destroy(b->multi);
+  b->multi = nullptr;
+  return ERPP_OK;
 }
 
 erpp_status erpp_batch_get_tiling(erpp_batch* b, int32_t box, int32_t out[5]) {
@@ -195,7 +260,7 @@ erpp_status erpp_batch_get_tiling(erpp_batch* b, int32_t box, int32_t out[5]) {
 
 erpp_status erpp_batch_last_step_launches(erpp_batch* b, int32_t* n) {
   if (!b || !n) return ERPP_EINVAL;
-  int32_t total = 0;
+  int32_t total = b->multi ? kMultiLaunches : 0;  // the multi-box step's kernels
   for (int i = 0; i < b->nbox; ++i) {
     int32_t k = 0;
     erpp_last_step_launches(b->ctx[i], &k);

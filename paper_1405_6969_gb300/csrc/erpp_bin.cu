@@ -100,16 +100,14 @@ __device__ __forceinline__ void for_each_piece4(const erpp_kparams& kp, const in
   }
 }
 
-__global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict__ x0,
-                            const double* __restrict__ x1, const double* __restrict__ x2,
-                            float4* __restrict__ geo_t, int4* __restrict__ geo_c,
-                            float* __restrict__ xw, int xw_len, float* __restrict__ d0x,
-                            float4* __restrict__ lapc, float* __restrict__ up_acc,
-                            int64_t acc_stride,
-                            int32_t* __restrict__ tile_cnt, int32_t* __restrict__ slot, int ms,
-                            uint32_t* err) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// Geometry and piece places of particle i < n (the body of k_bin_count and of
+// its multi-box form).
+__device__ __forceinline__ void bin_count_one(
+    const erpp_kparams& kp, int64_t i, int64_t n, const double* __restrict__ x0,
+    const double* __restrict__ x1, const double* __restrict__ x2, float4* __restrict__ geo_t,
+    int4* __restrict__ geo_c, float* __restrict__ xw, int xw_len, float* __restrict__ d0x,
+    float4* __restrict__ lapc, float* __restrict__ up_acc, int64_t acc_stride,
+    int32_t* __restrict__ tile_cnt, int32_t* __restrict__ slot, int ms, uint32_t* err) {
   double xv[3] = {x0[i], x1[i], x2[i]};
   if (up_acc && kp.design != 4) {
     up_acc[i] = 0.f;
@@ -210,15 +208,30 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
   geo_t[i] = make_float4(t[0], t[1], t[2], __int_as_float(min(k, ms)));
 }
 
+__global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict__ x0,
+                            const double* __restrict__ x1, const double* __restrict__ x2,
+                            float4* __restrict__ geo_t, int4* __restrict__ geo_c,
+                            float* __restrict__ xw, int xw_len, float* __restrict__ d0x,
+                            float4* __restrict__ lapc, float* __restrict__ up_acc,
+                            int64_t acc_stride,
+                            int32_t* __restrict__ tile_cnt, int32_t* __restrict__ slot, int ms,
+                            uint32_t* err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bin_count_one(kp, i, n, x0, x1, x2, geo_t, geo_c, xw, xw_len, d0x, lapc, up_acc, acc_stride,
+                tile_cnt, slot, ms, err);
+}
+
 // Writes one record per piece, at its bin's start plus the place the piece
 // took in k_bin_count (pieces visited in the same order); x/y-halo tiles keep
 // that record position in slot[k][i] for the gather's per-piece sums.
-__global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict__ geo_t,
-                           const int4* __restrict__ geo_c, const int32_t* __restrict__ start,
-                           int32_t* __restrict__ slot, int ms,
-                           int4* __restrict__ entries, int64_t cap, uint32_t* err) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ void bin_fill_one(const erpp_kparams& kp, int64_t i, int64_t n,
+                                             const float4* __restrict__ geo_t,
+                                             const int4* __restrict__ geo_c,
+                                             const int32_t* __restrict__ start,
+                                             int32_t* __restrict__ slot, int ms,
+                                             int4* __restrict__ entries, int64_t cap,
+                                             uint32_t* err) {
   const int4 g = geo_c[i];
   const uint32_t pack = (uint32_t)g.w;
   if (!(pack & ERPP_GEO_VALID)) return;
@@ -282,6 +295,15 @@ __global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict_
     else
       erpp_set_err(err, ERPP_ERRBIT_BOUNDS);
   });
+}
+
+__global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict__ geo_t,
+                           const int4* __restrict__ geo_c, const int32_t* __restrict__ start,
+                           int32_t* __restrict__ slot, int ms,
+                           int4* __restrict__ entries, int64_t cap, uint32_t* err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bin_fill_one(kp, i, n, geo_t, geo_c, start, slot, ms, entries, cap, err);
 }
 
 // Exclusive scan of the per-bin counts: k_scan_local scans chunks of
@@ -362,6 +384,63 @@ __global__ void k_scan_add(int32_t* __restrict__ start, const int32_t* __restric
   start[i] += chunk_off[i / kScanChunk];
 }
 
+// ---- many boxes in one launch (batched boxes) ----
+// Block b clears the counts of box b.
+__global__ void k_zero_counts_multi(const erpp_box_dev* __restrict__ boxes) {
+  const erpp_box_dev& B = boxes[blockIdx.x];
+  for (int k = threadIdx.x; k < B.nbins; k += blockDim.x) B.tile_cnt[k] = 0;
+}
+
+// One block per (box, first particle) item of 256 particles.
+__global__ void __launch_bounds__(256) k_bin_count_multi(const erpp_box_dev* __restrict__ boxes,
+                                                         const int2* __restrict__ items) {
+  const int2 it = items[blockIdx.x];
+  const erpp_box_dev& B = boxes[it.x];
+  const int64_t i = (int64_t)it.y + threadIdx.x;
+  if (i >= B.n) return;
+  bin_count_one(B.kp, i, B.n, B.x[0], B.x[1], B.x[2], B.geo_t, B.geo_c, nullptr, B.xw_len,
+                B.d0x, nullptr, nullptr, B.cap, B.tile_cnt, B.piece_slot, B.ms, B.err);
+}
+
+// Block b scans the counts of box b (chunks of 4096 bins, the running total
+// carried from chunk to chunk) into its starts, total at start[nbins].
+__global__ void __launch_bounds__(1024) k_scan_multi(const erpp_box_dev* __restrict__ boxes) {
+  __shared__ int32_t ws[32];
+  __shared__ int32_t tot;
+  const erpp_box_dev& B = boxes[blockIdx.x];
+  const int nbins = B.nbins;
+  int32_t carry = 0;
+  for (int c0 = 0; c0 < nbins; c0 += kScanChunk) {
+    const int base = c0 + threadIdx.x * 4;
+    int32_t v[4];
+    int32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = (base + k < nbins) ? B.tile_cnt[base + k] : 0;
+      s += v[k];
+    }
+    int32_t run = carry + block_exclusive_scan(s, ws, &tot);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (base + k < nbins) B.tile_start[base + k] = run;
+      run += v[k];
+    }
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) B.tile_start[nbins] = carry;
+}
+
+__global__ void __launch_bounds__(256) k_bin_fill_multi(const erpp_box_dev* __restrict__ boxes,
+                                                        const int2* __restrict__ items) {
+  const int2 it = items[blockIdx.x];
+  const erpp_box_dev& B = boxes[it.x];
+  const int64_t i = (int64_t)it.y + threadIdx.x;
+  if (i >= B.n) return;
+  bin_fill_one(B.kp, i, B.n, B.geo_t, B.geo_c, B.tile_start, B.piece_slot, B.ms, B.entries,
+               B.ecap, B.err);
+}
+
 }  // namespace
 
 namespace erpp {
@@ -405,6 +484,16 @@ cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bo
                                        ctx->piece_slot, ms, ctx->entries, ctx->entries_cap,
                                        ctx->err);
   }
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_bin_multi(const erpp_box_dev* boxes, int nbox, const int2* pitems,
+                             int npitems, cudaStream_t st) {
+  k_zero_counts_multi<<<nbox, 256, 0, st>>>(boxes);
+  if (npitems > 0) k_bin_count_multi<<<npitems, 256, 0, st>>>(boxes, pitems);
+  k_scan_multi<<<nbox, 1024, 0, st>>>(boxes);
+  if (npitems > 0) k_bin_fill_multi<<<npitems, 256, 0, st>>>(boxes, pitems);
   return cudaGetLastError();
 }
 

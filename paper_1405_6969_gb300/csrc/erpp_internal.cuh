@@ -193,8 +193,45 @@ struct erpp_acc {
   int64_t n;
 };
 
+// One box of the multi-box launches (batched boxes): its kernel parameters,
+// sizes, and the buffers of its context and particle state, in device memory.
+struct erpp_box_dev {
+  erpp_kparams kp;
+  int64_t n;      // particles
+  int64_t cap;    // particle capacity of the context's arrays (their stride)
+  int64_t ecap;   // piece-record capacity
+  int32_t ms;     // most pieces per particle
+  int32_t nbins;  // tiles
+  int32_t xw_len; // longest x-window the binning accepts
+  double* x[3];
+  double* v[3];
+  double* xp[3];
+  double* D[3];
+  const double* radius;
+  const double* rho_p;
+  float4* geo_t;
+  int4* geo_c;
+  float* d0x;
+  int32_t* tile_cnt;
+  int32_t* tile_start;
+  int32_t* piece_slot;
+  int4* entries;
+  float4* up_part;
+  float4* fscat;
+  float* S;
+  float* halo;
+  uint32_t* err;
+};
+
 // ---- host-side launchers (stream-ordered, no synchronisation) ----
 namespace erpp {
+// Multi-box launches over pitems = (box, first particle) chunks of 256
+// particles or the boxes themselves: the binning (counts cleared, counted,
+// scanned per box, records filled: four launches) and the advance.
+cudaError_t launch_bin_multi(const erpp_box_dev* boxes, int nbox, const int2* pitems,
+                             int npitems, cudaStream_t st);
+cudaError_t launch_advance_multi(const erpp_box_dev* boxes, const int2* pitems, int npitems,
+                                 int first_step, cudaStream_t st);
 
 erpp_status derive_ctx(const erpp_params* p, erpp_ctx* c);
 erpp_status ensure_capacity(erpp_ctx* c, int64_t n);  // may allocate (synchronous)
@@ -227,6 +264,21 @@ size_t smem_bytes4(const erpp_kparams& kp, int copies, bool gather);
 // nodes, else 16 (256 or 128 pieces per batch).
 int xw4(const erpp_kparams& kp);
 cudaError_t launch_scatter_f32_4(erpp_ctx* ctx, float* S, cudaStream_t st);  // + halo merge
+// Many boxes (batched) in one gather launch and one scatter launch: persistent
+// blocks pull (box, tile) items, densest boxes first, from a counter.  Needs
+// every box on x/y-halo tiles, FP32, Gaussian weights, the fixed-point
+// scatter and the same window variant (multi4_eligible).  The descriptors
+// hold the contexts' buffers as they are at creation.
+struct Multi4;
+bool multi4_eligible(erpp_ctx* const* ctx, int nbox);
+cudaError_t multi4_create(erpp_ctx* const* ctx, const float* const* u, float* const* S,
+                          const erpp_particles* parts, int nbox, Multi4** out);
+// The coupling step of every box in ten launches: binning (4), gather,
+// advance, scatter and the two halo merges of all boxes, and the clearing of
+// the work counters.
+cudaError_t multi4_step(const Multi4* m, int first_step, cudaStream_t st);
+void multi4_destroy(Multi4* m);
+
 cudaError_t launch_finalize_up(erpp_ctx* ctx, int64_t n, const double* const x[3],
                                double* const up[3], cudaStream_t st);
 // fscat_i = scale * norm_i * D_i (scale = -1/(rho_f dV) for the source).

@@ -283,13 +283,11 @@ __global__ void __launch_bounds__(256) k_advance_full(erpp_kparams kp, int64_t n
 // slip (the increment is a small correction to the FP64 velocity); the
 // velocity and position updates themselves stay in FP64.
 template <bool FROM_ACC, bool F32>
-__global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, PartPtrs P,
-                                                 UpPtrs U, erpp_acc acc,
-                                                 const float4* __restrict__ geo_t,
-                                                 const int4* __restrict__ geo_c,
-                                                 float4* __restrict__ fscat, int first_step) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ void advance_one(const erpp_kparams& kp, int64_t i, const PartPtrs& P,
+                                            const UpPtrs& U, const erpp_acc& acc,
+                                            const float4* __restrict__ geo_t,
+                                            const int4* __restrict__ geo_c,
+                                            float4* __restrict__ fscat, int first_step) {
   double x[3], v[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -389,6 +387,47 @@ __global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, Par
     const float f0 = s * Dnf[0], f1 = s * Dnf[1], f2 = s * Dnf[2];
     fscat[i] = make_float4(f0, f1, f2, fmaxf(fabsf(f0), fmaxf(fabsf(f1), fabsf(f2))));
   }
+}
+
+template <bool FROM_ACC, bool F32>
+__global__ void __launch_bounds__(256) k_advance(erpp_kparams kp, int64_t n, PartPtrs P,
+                                                 UpPtrs U, erpp_acc acc,
+                                                 const float4* __restrict__ geo_t,
+                                                 const int4* __restrict__ geo_c,
+                                                 float4* __restrict__ fscat, int first_step) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  advance_one<FROM_ACC, F32>(kp, i, P, U, acc, geo_t, geo_c, fscat, first_step);
+}
+
+// Many boxes in one launch (batched boxes): one block per (box, first
+// particle) item of 256 particles; the FP32 tile step's advance of each.
+__global__ void __launch_bounds__(256) k_advance_multi(const erpp_box_dev* __restrict__ boxes,
+                                                       const int2* __restrict__ items,
+                                                       int first_step) {
+  const int2 it = items[blockIdx.x];
+  const erpp_box_dev& B = boxes[it.x];
+  const int64_t i = (int64_t)it.y + threadIdx.x;
+  if (i >= B.n) return;
+  PartPtrs P;
+  for (int a = 0; a < 3; ++a) {
+    P.x[a] = B.x[a];
+    P.v[a] = B.v[a];
+    P.xp[a] = B.xp[a];
+    P.D[a] = B.D[a];
+    P.xs[a] = B.xp[a];
+    P.Ds[a] = B.D[a];
+  }
+  P.radius = B.radius;
+  P.rho_p = B.rho_p;
+  UpPtrs U = {{nullptr, nullptr, nullptr}};
+  erpp_acc acc;
+  acc.up_acc = nullptr;
+  acc.stride = B.cap;
+  acc.up_part = B.up_part;
+  acc.piece_slot = B.piece_slot;
+  acc.n = B.n;
+  advance_one<true, true>(B.kp, i, P, U, acc, B.geo_t, B.geo_c, B.fscat, first_step);
 }
 
 __global__ void k_finalize_up(erpp_kparams kp, int64_t n, erpp_acc acc,
@@ -705,6 +744,13 @@ cudaError_t launch_momentum(erpp_ctx* ctx, const void* S, int64_t n, const doubl
     k_grid_sum<float><<<kRedBlocks, 256, 0, st>>>((const float*)S, nn, gpart);
   k_part_sum<<<kRedBlocks, 256, 0, st>>>(kp, n, x[0], x[1], x[2], D[0], D[1], D[2], ppart);
   k_momentum_final<<<1, 32, 0, st>>>(kp, gpart, ppart, kRedBlocks, out);
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_advance_multi(const erpp_box_dev* boxes, const int2* pitems, int npitems,
+                                 int first_step, cudaStream_t st) {
+  if (npitems > 0) k_advance_multi<<<npitems, 256, 0, st>>>(boxes, pitems, first_step);
   return cudaGetLastError();
 }
 

@@ -75,6 +75,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "erpp_internal.cuh"
 
@@ -169,6 +170,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
                : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// Before the barrier's memory is initialised again (a persistent block that
+// stages one tile after another).
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
@@ -658,27 +664,27 @@ struct UnitRows {
   float d0y, ezz;
 };
 
-// XM: longest x-window; LMIN: shortest (slots q >= LMIN are tested); XW: 8
-// for windows of at most 7 nodes, else 16 (sets the pieces per batch).
-// LAP: also the Laplacian of the gathered velocity (general force, Eq.
-// force_particle): per row, the same loaded values against the x-weights'
-// second-derivative factors, and the row's and plane's own factors.
+// The gather of one tile, called by the whole block (the body of k_gather4
+// and of the multi-box gather).  XM: longest x-window; LMIN: shortest (slots
+// q >= LMIN are tested); XW: 8 for windows of at most 7 nodes, else 16 (sets
+// the pieces per batch).  LAP: also the Laplacian of the gathered velocity
+// (general force, Eq. force_particle): per row, the same loaded values
+// against the x-weights' second-derivative factors, and the row's and
+// plane's own factors.  tmap: the field's tensor map (parameter or global
+// memory).  Returns bit 0: a bounded wait ran out (the block gave the tile
+// up); bit 1: the staging barriers were initialised.
 template <int XM, int LMIN, int XW, int NT, bool LAP>
-__global__ void __launch_bounds__(NT, LAP ? 2 : 768 / NT) k_gather4(
-    erpp_kparams kp, const float* __restrict__ u, const __grid_constant__ CUtensorMap tmap,
+__device__ __forceinline__ int gather_tile4(
+    const erpp_kparams& kp, int tile, const float* __restrict__ u, const CUtensorMap* tmap,
     int use_tma, const int32_t* __restrict__ start, const int4* __restrict__ entries,
     int64_t ecap, const float* __restrict__ d0x, const float4* __restrict__ lapc,
-    float4* __restrict__ up_part, float4* __restrict__ lap_part, uint32_t* err) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ SchedState ss;
-  __shared__ __align__(8) uint64_t tma_bar;
-  __shared__ __align__(8) uint64_t stall_bar;  // debug_stall only: never completed
+    float4* __restrict__ up_part, float4* __restrict__ lap_part, uint32_t* err,
+    unsigned char* smem_raw, SchedState& ss, uint64_t& tma_bar, uint64_t& stall_bar) {
   constexpr int PB = Batch<XW>::kPB;
   static_assert(PB <= NT, "a batch holds at most one piece per thread");
-  const int tile = blockIdx.x;
   const int e0 = start[tile];
   const int e1 = (int)min((int64_t)start[tile + 1], ecap);
-  if (e0 >= e1) return;
+  if (e0 >= e1) return 0;
   const int tzs = kp.T[2];  // planes per tile: units per piece, at most
   const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, tzs, 3, true, LAP);
   int b[3], ext[3], tt[3];
@@ -699,7 +705,7 @@ __global__ void __launch_bounds__(NT, LAP ? 2 : 768 / NT) k_gather4(
     if (kp.debug_stall) mbar_init(&stall_bar, 1);
     if (tma) {
       mbar_expect_tx(&tma_bar, (unsigned)(3 * kp.plane * 4));
-      tma_load_4d(cv.field, &tmap, &tma_bar, x0, y0, b[2], 0);
+      tma_load_4d(cv.field, tmap, &tma_bar, x0, y0, b[2], 0);
     } else {
       mbar_expect_tx(&tma_bar, tile_rows_bytes(kp, ext));
     }
@@ -755,7 +761,7 @@ __global__ void __launch_bounds__(NT, LAP ? 2 : 768 / NT) k_gather4(
       }
     }
     staged = staged || first_wait;
-    if (__syncthreads_or(timed_out)) return;
+    if (__syncthreads_or(timed_out)) return (tma || rows) ? 3 : 1;
     // the phase has completed: every thread observes it (acquire of the
     // copied field), which returns at once
     if (first_wait && threadIdx.x != 0) mbar_try_wait(&tma_bar, 0);
@@ -892,6 +898,22 @@ __global__ void __launch_bounds__(NT, LAP ? 2 : 768 / NT) k_gather4(
     }
     __syncthreads();
   }
+  return (tma || rows) ? 2 : 0;
+}
+
+template <int XM, int LMIN, int XW, int NT, bool LAP>
+__global__ void __launch_bounds__(NT, LAP ? 2 : 768 / NT) k_gather4(
+    erpp_kparams kp, const float* __restrict__ u, const __grid_constant__ CUtensorMap tmap,
+    int use_tma, const int32_t* __restrict__ start, const int4* __restrict__ entries,
+    int64_t ecap, const float* __restrict__ d0x, const float4* __restrict__ lapc,
+    float4* __restrict__ up_part, float4* __restrict__ lap_part, uint32_t* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ SchedState ss;
+  __shared__ __align__(8) uint64_t tma_bar;
+  __shared__ __align__(8) uint64_t stall_bar;  // debug_stall only: never completed
+  gather_tile4<XM, LMIN, XW, NT, LAP>(kp, blockIdx.x, u, &tmap, use_tma, start, entries, ecap,
+                                      d0x, lapc, up_part, lap_part, err, smem_raw, ss, tma_bar,
+                                      stall_bar);
 }
 
 // MODE 0: 32-bit fixed point (FP32 atomics on dense tiles); MODE 1: split
@@ -1109,18 +1131,20 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
   return TileAcc{any, fixedp, inv_scale};
 }
 
+// The scatter of one tile with its write-out, called by the whole block (the
+// body of k_scatter4 and of the multi-box scatter).
 template <int XM, int LMIN, int XW, int MODE, int NT, bool CL>
-__global__ void __launch_bounds__(NT, MODE == 0 ? 1024 / NT : 2) k_scatter4(
-    erpp_kparams kp, float* __restrict__ S, float* __restrict__ halo,
-    const int32_t* __restrict__ start, const int4* __restrict__ entries, int64_t ecap,
-    const float* __restrict__ d0x, const float4* __restrict__ fscat) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ SchedState ss;
+__device__ __forceinline__ void scatter_tile4(const erpp_kparams& kp, int tile,
+                                              float* __restrict__ S, float* __restrict__ halo,
+                                              const int32_t* __restrict__ start,
+                                              const int4* __restrict__ entries, int64_t ecap,
+                                              const float* __restrict__ d0x,
+                                              const float4* __restrict__ fscat,
+                                              unsigned char* smem_raw, SchedState& ss,
+                                              float* red) {
   constexpr int NW = NT / 32;
-  __shared__ __align__(8) float red[2 * NW];  // per-warp partials (8-byte ones too)
   constexpr int PB = Batch<XW>::kPB;
   static_assert(PB <= NT, "a batch holds at most one piece per thread");
-  const int tile = blockIdx.x;
   const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, kp.T[2], MODE == 1 ? 6 : 3, false);
   float* smem = cv.field;
   const TileAcc ta =
@@ -1285,6 +1309,18 @@ __global__ void __launch_bounds__(NT, MODE == 0 ? 1024 / NT : 2) k_scatter4(
   }
 }
 
+template <int XM, int LMIN, int XW, int MODE, int NT, bool CL>
+__global__ void __launch_bounds__(NT, MODE == 0 ? 1024 / NT : 2) k_scatter4(
+    erpp_kparams kp, float* __restrict__ S, float* __restrict__ halo,
+    const int32_t* __restrict__ start, const int4* __restrict__ entries, int64_t ecap,
+    const float* __restrict__ d0x, const float4* __restrict__ fscat) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ SchedState ss;
+  __shared__ __align__(8) float red[2 * (NT / 32)];  // per-warp partials (8-byte ones too)
+  scatter_tile4<XM, LMIN, XW, MODE, NT, CL>(kp, blockIdx.x, S, halo, start, entries, ecap, d0x,
+                                            fscat, smem_raw, ss, red);
+}
+
 // Adds the scatter's halo strips onto the tiles they belong to, in two
 // phases (stream order, each node updated by one thread per phase, so the
 // result is deterministic), one block per tile, periodic in x and y:
@@ -1302,10 +1338,11 @@ __device__ __forceinline__ int tile_id(const erpp_kparams& kp, int tx, int ty, i
 
 constexpr int kMergeThreads = 128;
 
-__global__ void __launch_bounds__(kMergeThreads) k_merge_rows(erpp_kparams kp, float* __restrict__ S,
-                                                              const float* __restrict__ halo) {
+__device__ __forceinline__ void merge_rows_tile(const erpp_kparams& kp, int tile,
+                                                float* __restrict__ S,
+                                                const float* __restrict__ halo) {
   int b[3], ext[3], t[3];
-  tile_origin4(kp, blockIdx.x, b, ext, t);
+  tile_origin4(kp, tile, b, ext, t);
   const int W = kp.T[0], hy = kp.yhlo + kp.yhhi;
   const int tyl = t[1] == 0 ? kp.nt[1] - 1 : t[1] - 1;
   const int tyr = t[1] == kp.nt[1] - 1 ? 0 : t[1] + 1;
@@ -1356,10 +1393,16 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_rows(erpp_kparams kp, f
   }
 }
 
-__global__ void __launch_bounds__(kMergeThreads) k_merge_cols(erpp_kparams kp, float* __restrict__ S,
+__global__ void __launch_bounds__(kMergeThreads) k_merge_rows(erpp_kparams kp, float* __restrict__ S,
                                                               const float* __restrict__ halo) {
+  merge_rows_tile(kp, blockIdx.x, S, halo);
+}
+
+__device__ __forceinline__ void merge_cols_tile(const erpp_kparams& kp, int tile,
+                                                float* __restrict__ S,
+                                                const float* __restrict__ halo) {
   int b[3], ext[3], t[3];
-  tile_origin4(kp, blockIdx.x, b, ext, t);
+  tile_origin4(kp, tile, b, ext, t);
   const int hx = kp.xhlo + kp.xhhi, hy = kp.yhlo + kp.yhhi;
   const int Ty = kp.T[1];
   const int txl = t[0] == 0 ? kp.nt[0] - 1 : t[0] - 1;
@@ -1407,6 +1450,11 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_cols(erpp_kparams kp, f
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(kMergeThreads) k_merge_cols(erpp_kparams kp, float* __restrict__ S,
+                                                              const float* __restrict__ halo) {
+  merge_cols_tile(kp, blockIdx.x, S, halo);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
@@ -1555,6 +1603,95 @@ bool cluster_eligible(const erpp_ctx* ctx, const float* S) {
          (((uintptr_t)ctx->halo) & 15) == 0;
 }
 
+// ---- Many boxes in one launch (batched boxes) ----
+// One box of a multi-box launch, in device memory: its kernel parameters,
+// the field's tensor map and its buffers (those of its context).
+struct __align__(64) BoxTiles {
+  CUtensorMap tmap;
+  erpp_kparams kp;
+  const float* u;
+  float* S;
+  float* halo;
+  const int32_t* start;
+  const int4* entries;
+  int64_t ecap;
+  const float* d0x;
+  const float4* fscat;
+  float4* up_part;
+  uint32_t* err;
+  int use_tma;
+};
+
+// Persistent blocks pull (box, tile) work items from a counter that only
+// grows, so every block ends once the items are used up: no block waits on
+// another.  The items are ordered by cost (denser boxes first); each is the
+// single-box tile body with the box's parameters and buffers.
+template <int XM, int LMIN, int XW>
+__global__ void __launch_bounds__(256, 3) k_gather4_multi(const BoxTiles* __restrict__ boxes,
+                                                          const int2* __restrict__ items,
+                                                          int nitems, int* __restrict__ counter) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ SchedState ss;
+  __shared__ __align__(8) uint64_t tma_bar;
+  __shared__ __align__(8) uint64_t stall_bar;
+  __shared__ int item;
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = item;
+    if (it >= nitems) break;
+    const int2 bt = items[it];
+    const BoxTiles& B = boxes[bt.x];
+    const int r = gather_tile4<XM, LMIN, XW, 256, false>(
+        B.kp, bt.y, B.u, &B.tmap, B.use_tma, B.start, B.entries, B.ecap, B.d0x, nullptr,
+        B.up_part, nullptr, B.err, smem_raw, ss, tma_bar, stall_bar);
+    // every thread is done with the tile, its barriers and `item`
+    __syncthreads();
+    if (r & 1) break;  // a bounded wait ran out (recorded): the block stops
+    if (threadIdx.x == 0 && (r & 2)) {
+      mbar_inval(&tma_bar);
+      if (B.kp.debug_stall) mbar_inval(&stall_bar);
+    }
+  }
+}
+
+template <int XM, int LMIN, int XW>
+__global__ void __launch_bounds__(256, 4) k_scatter4_multi(const BoxTiles* __restrict__ boxes,
+                                                           const int2* __restrict__ items,
+                                                           int nitems, int* __restrict__ counter) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ SchedState ss;
+  __shared__ __align__(8) float red[2 * (256 / 32)];
+  __shared__ int item;
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = item;
+    if (it >= nitems) break;
+    const int2 bt = items[it];
+    const BoxTiles& B = boxes[bt.x];
+    scatter_tile4<XM, LMIN, XW, 0, 256, false>(B.kp, bt.y, B.S, B.halo, B.start, B.entries,
+                                               B.ecap, B.d0x, B.fscat, smem_raw, ss, red);
+    // every thread is done with the tile's shared memory and `item`
+    __syncthreads();
+  }
+}
+
+// The halo merges of every box's tiles: one block per (box, tile) item
+// (x-windows cut at x-tile boundaries leave no x-strips to merge).
+__global__ void __launch_bounds__(kMergeThreads) k_merge_rows_multi(
+    const BoxTiles* __restrict__ boxes, const int2* __restrict__ items) {
+  const int2 bt = items[blockIdx.x];
+  const BoxTiles& B = boxes[bt.x];
+  merge_rows_tile(B.kp, bt.y, B.S, B.halo);
+}
+__global__ void __launch_bounds__(kMergeThreads) k_merge_cols_multi(
+    const BoxTiles* __restrict__ boxes, const int2* __restrict__ items) {
+  const int2 bt = items[blockIdx.x];
+  const BoxTiles& B = boxes[bt.x];
+  if (!B.kp.xclip) merge_cols_tile(B.kp, bt.y, B.S, B.halo);
+}
+
 }  // namespace
 
 namespace erpp {
@@ -1629,5 +1766,226 @@ cudaError_t launch_scatter_f32_4(erpp_ctx* ctx, float* S, cudaStream_t st) {
   }
   return cudaGetLastError();
 }
+
+
+// ---- multi-box launches ----
+struct Multi4 {
+  BoxTiles* boxes = nullptr;      // device: tile kernels' view of every box
+  erpp_box_dev* pboxes = nullptr; // device: particle kernels' view
+  int2* items = nullptr;          // device: (box, tile), densest boxes first
+  int2* pitems = nullptr;         // device: (box, first particle), 256 each
+  int* counter = nullptr;         // device: [gather, scatter]
+  int nbox = 0;
+  int nitems = 0;
+  int npitems = 0;
+  int variant = 0;
+  size_t smem_g = 0, smem_s = 0;
+  int grid_g = 0, grid_s = 0;
+};
+
+// The window variant one launch can serve for every box: the boxes' own
+// variants must share the longest window (0, 1: 7 nodes; 2, 3: 10 nodes); of
+// two, the one that tests more slots (1, 3) serves both.  -1: none.
+int multi4_variant(erpp_ctx* const* ctx, int nbox) {
+  int chosen = -1;
+  for (int i = 0; i < nbox; ++i) {
+    const int v = variant4(ctx[i]->kp);
+    if (v < 0 || v > 3) return -1;
+    if (chosen >= 0 && (v >> 1) != (chosen >> 1)) return -1;
+    chosen = std::max(chosen, v);
+  }
+  return chosen;
+}
+
+bool multi4_eligible(erpp_ctx* const* ctx, int nbox) {
+  if (nbox < 1 || multi4_variant(ctx, nbox) < 0) return false;
+  for (int i = 0; i < nbox; ++i) {
+    const erpp_kparams& kp = ctx[i]->kp;
+    if (ctx[i]->fp64 || kp.design != 4 || kp.weights != ERPP_W_GAUSS || kp.kahan || kp.lag > 0 ||
+        kp.full_force || !ctx[i]->entries || !ctx[i]->halo)
+      return false;
+  }
+  return true;
+}
+
+template <int XM, int LMIN, int XW>
+cudaError_t multi4_setup_kernels(Multi4* m, int nsm) {
+  int nb = 0;
+  cudaError_t e = cudaFuncSetAttribute(k_gather4_multi<XM, LMIN, XW>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m->smem_g);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gather4_multi<XM, LMIN, XW>, 256,
+                                                      m->smem_g);
+  m->grid_g = nsm * (nb > 0 ? nb : 1);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_scatter4_multi<XM, LMIN, XW>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m->smem_s);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter4_multi<XM, LMIN, XW>, 256,
+                                                      m->smem_s);
+  m->grid_s = nsm * (nb > 0 ? nb : 1);
+  return e;
+}
+
+void multi4_destroy(Multi4* m) {
+  if (!m) return;
+  cudaFree(m->boxes);
+  cudaFree(m->pboxes);
+  cudaFree(m->items);
+  cudaFree(m->pitems);
+  cudaFree(m->counter);
+  delete m;
+}
+
+// The descriptors of every box (their contexts' current buffers), the work
+// items ordered by particles per tile (densest boxes first) and the counters.
+cudaError_t multi4_create(erpp_ctx* const* ctx, const float* const* u, float* const* S,
+                          const erpp_particles* parts, int nbox, Multi4** out) {
+  *out = nullptr;
+  Multi4* m = new Multi4();
+  m->nbox = nbox;
+  std::vector<BoxTiles> hb((size_t)nbox);
+  std::vector<erpp_box_dev> hp((size_t)nbox);
+  std::vector<int> order((size_t)nbox);
+  std::vector<int64_t> npart((size_t)nbox);
+  std::vector<int2> pitems;
+  int64_t nitems = 0;
+  for (int i = 0; i < nbox; ++i) {
+    BoxTiles& d = hb[(size_t)i];
+    memset(&d, 0, sizeof(d));
+    const erpp_ctx* c = ctx[i];
+    const erpp_particles& P = parts[i];
+    npart[(size_t)i] = P.n;
+    erpp_box_dev& q = hp[(size_t)i];
+    memset(&q, 0, sizeof(q));
+    q.kp = c->kp;
+    q.n = P.n;
+    q.cap = c->cap;
+    q.ecap = c->entries_cap;
+    q.ms = c->maxseg[0] * c->maxseg[1] * c->maxseg[2];
+    q.nbins = nbins(c->kp);
+    q.xw_len = c->xw_len;
+    for (int a = 0; a < 3; ++a) {
+      q.x[a] = P.x[a];
+      q.v[a] = P.v[a];
+      q.xp[a] = P.x_prev[a];
+      q.D[a] = P.D[a];
+    }
+    q.radius = P.radius;
+    q.rho_p = P.rho_p;
+    q.geo_t = c->geo_t;
+    q.geo_c = c->geo_c;
+    q.d0x = c->d0x;
+    q.tile_cnt = c->tile_cnt;
+    q.tile_start = c->tile_start;
+    q.piece_slot = c->piece_slot;
+    q.entries = c->entries;
+    q.up_part = c->up_part;
+    q.fscat = c->fscat;
+    q.S = S[i];
+    q.halo = c->halo;
+    q.err = c->err;
+    for (int64_t f = 0; f < P.n; f += 256) pitems.push_back(make_int2(i, (int)f));
+    d.kp = c->kp;
+    d.use_tma = field_tensor_map(c->kp, u[i], &d.tmap) ? 1 : 0;
+    d.u = u[i];
+    d.S = S[i];
+    d.halo = c->halo;
+    d.start = c->tile_start;
+    d.entries = c->entries;
+    d.ecap = c->entries_cap;
+    d.d0x = c->d0x;
+    d.fscat = c->fscat;
+    d.up_part = c->up_part;
+    d.err = c->err;
+    order[(size_t)i] = i;
+    nitems += c->kp.ntiles;
+    m->smem_g = std::max(m->smem_g, smem_bytes4(c->kp, 3, true));
+    m->smem_s = std::max(m->smem_s, smem_bytes4(c->kp, 3, false));
+  }
+  if (nitems > (int64_t)1 << 30) {
+    delete m;
+    return cudaErrorInvalidValue;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (double)npart[(size_t)a] / ctx[a]->kp.ntiles >
+           (double)npart[(size_t)b] / ctx[b]->kp.ntiles;
+  });
+  std::vector<int2> items;
+  items.reserve((size_t)nitems);
+  for (int i : order)
+    for (int t = 0; t < ctx[i]->kp.ntiles; ++t) items.push_back(make_int2(i, t));
+  m->nitems = (int)nitems;
+  m->npitems = (int)pitems.size();
+  m->variant = multi4_variant(ctx, nbox);
+  cudaError_t e = cudaMalloc(&m->boxes, sizeof(BoxTiles) * (size_t)nbox);
+  if (e == cudaSuccess) e = cudaMalloc(&m->pboxes, sizeof(erpp_box_dev) * (size_t)nbox);
+  if (e == cudaSuccess) e = cudaMalloc(&m->items, sizeof(int2) * std::max<size_t>(items.size(), 1));
+  if (e == cudaSuccess)
+    e = cudaMalloc(&m->pitems, sizeof(int2) * std::max<size_t>(pitems.size(), 1));
+  if (e == cudaSuccess) e = cudaMalloc(&m->counter, 2 * sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->boxes, hb.data(), sizeof(BoxTiles) * (size_t)nbox, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->pboxes, hp.data(), sizeof(erpp_box_dev) * (size_t)nbox,
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !items.empty())
+    e = cudaMemcpy(m->items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !pitems.empty())
+    e = cudaMemcpy(m->pitems, pitems.data(), sizeof(int2) * pitems.size(),
+                   cudaMemcpyHostToDevice);
+  int dev = 0, nsm = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) {
+    switch (m->variant) {
+      case 0: e = multi4_setup_kernels<7, 6, 8>(m, nsm); break;
+      case 1: e = multi4_setup_kernels<7, 5, 8>(m, nsm); break;
+      case 2: e = multi4_setup_kernels<10, 9, 16>(m, nsm); break;
+      default: e = multi4_setup_kernels<10, 8, 16>(m, nsm); break;
+    }
+  }
+  if (e != cudaSuccess) {
+    multi4_destroy(m);
+    return e;
+  }
+  *out = m;
+  return cudaSuccess;
+}
+
+template <int XM, int LMIN, int XW>
+cudaError_t multi4_run(const Multi4* m, bool gather, cudaStream_t st) {
+  if (gather)
+    k_gather4_multi<XM, LMIN, XW><<<m->grid_g, 256, m->smem_g, st>>>(m->boxes, m->items,
+                                                                      m->nitems, m->counter);
+  else
+    k_scatter4_multi<XM, LMIN, XW><<<m->grid_s, 256, m->smem_s, st>>>(m->boxes, m->items,
+                                                                       m->nitems, m->counter + 1);
+  return cudaGetLastError();
+}
+
+cudaError_t multi4_tiles(const Multi4* m, bool gather, cudaStream_t st) {
+  switch (m->variant) {
+    case 0: return multi4_run<7, 6, 8>(m, gather, st);
+    case 1: return multi4_run<7, 5, 8>(m, gather, st);
+    case 2: return multi4_run<10, 9, 16>(m, gather, st);
+    default: return multi4_run<10, 8, 16>(m, gather, st);
+  }
+}
+
+cudaError_t multi4_step(const Multi4* m, int first_step, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(m->counter, 0, 2 * sizeof(int), st);
+  if (e == cudaSuccess) e = launch_bin_multi(m->pboxes, m->nbox, m->pitems, m->npitems, st);
+  if (e == cudaSuccess) e = multi4_tiles(m, true, st);
+  if (e == cudaSuccess) e = launch_advance_multi(m->pboxes, m->pitems, m->npitems, first_step, st);
+  if (e == cudaSuccess) e = multi4_tiles(m, false, st);
+  if (e == cudaSuccess && m->nitems > 0) {
+    k_merge_rows_multi<<<m->nitems, kMergeThreads, 0, st>>>(m->boxes, m->items);
+    k_merge_cols_multi<<<m->nitems, kMergeThreads, 0, st>>>(m->boxes, m->items);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
 
 }  // namespace erpp

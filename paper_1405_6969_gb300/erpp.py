@@ -396,6 +396,14 @@ class Batch:
         _lib.check(self.lib.erpp_batch_set_tiling(self._h, int(box), int(tile_y), int(tile_z),
                                                   int(threads)), "erpp_batch_set_tiling")
 
+    BATCH_FORMS = {"branches": 0, "multi": 1}
+
+    def set_form(self, form="branches"):
+        """The graph's form: one branch per box ("branches") or nine kernels
+        over all boxes ("multi", erpp_batch_set_form)."""
+        _lib.check(self.lib.erpp_batch_set_form(self._h, self.BATCH_FORMS[form]),
+                   "erpp_batch_set_form")
+
     def last_step_launches(self):
         """Kernels of one batched step (the boxes' most recent step sequences,
         the ones a captured graph replays)."""

@@ -101,6 +101,62 @@ def test_batched_step_matches_oracle(erpp, oracle_lib, precision, use_graph):
     batch.close()
 
 
+def same_variant_boxes():
+    """Five boxes whose stencils share one window length (sigma_R = dx along
+    x): the graph runs the step of all of them as nine multi-box launches.
+    Cubic, anisotropic and ragged grids, dense and sparse clouds, one box
+    with a single particle."""
+    b = []
+    for i, (n, L, npart, cloud, shear) in enumerate([
+        ((64, 64, 64), (2 * math.pi,) * 3, 20000, "uniform", 1.0),
+        ((72, 40, 20), (2 * math.pi, 2 * math.pi * 40 / 72, 2 * math.pi * 20 / 72), 2500,
+         "clusters", 0.5),
+        ((96, 48, 48), (2 * math.pi, math.pi, math.pi), 6000, "uniform", 0.0),
+        ((40, 40, 40), (2 * math.pi,) * 3, 1, "uniform", 0.0),
+        ((130, 34, 18), (2 * math.pi, 2 * math.pi * 34 / 130, 2 * math.pi * 18 / 130), 3000,
+         "clusters", 0.0),
+    ]):
+        b.append(I.Workload(name=f"m{i}", n=n, L=L, n_particles=npart, sigma_over_dx=1.0,
+                            kmax=3.0, field_seed=10 + i, particle_seed=10 + i, cloud=cloud,
+                            n_clusters=4, cluster_std=0.5, shear_rate=shear))
+    return b
+
+
+def test_multi_box_launches_match_oracle_and_plain_launches(erpp, oracle_lib):
+    """The multi-box graph (binning, advance and merges over every box's
+    particles and tiles, persistent gather and scatter pulling (box, tile)
+    items) against the oracle per box, over three steps, and bit for bit
+    against the same batch run as plain launches box after box."""
+    boxes = same_variant_boxes()
+    entries, refs = _build(erpp, "fp32", boxes)
+    entries2, _ = _build(erpp, "fp32", boxes)
+    batch = erpp.Batch(entries, precision="fp32")
+    batch.set_form("multi")
+    plain = erpp.Batch(entries2, precision="fp32")
+    for k in range(3):
+        batch.step(first_step=(k == 0), use_graph=True)
+        plain.step(first_step=(k == 0), use_graph=False)
+        for (p, _, _, _), (grid, ref) in zip(entries, refs):
+            oracle_lib.step(p, grid, ref, first_step=(k == 0))
+    batch.check()
+    plain.check()
+    assert all(batch.tiling(i)[0] == 4 for i in range(len(boxes)))
+    # all boxes together: clear, count, scan, fill, gather, advance, scatter,
+    # two merges
+    assert batch.last_step_launches() == 9
+    for (p, u, ps, S), (_, u2, ps2, S2), (grid, ref), w in zip(entries, entries2, refs, boxes):
+        S_ref = oracle_lib.scatter(p, ref.x_prev, ref.D)
+        assert rel(S.cpu().numpy(), S_ref) < 1e-5, w.name
+        assert rel(ps.D.cpu().numpy(), ref.D) < 1e-5, w.name
+        assert rel(ps.v.cpu().numpy(), ref.v) < 1e-5, w.name
+        # the same kernels' arithmetic on the same data: bit for bit
+        assert np.array_equal(S.cpu().numpy(), S2.cpu().numpy()), w.name
+        assert np.array_equal(ps.D.cpu().numpy(), ps2.D.cpu().numpy()), w.name
+        assert np.array_equal(ps.x.cpu().numpy(), ps2.x.cpu().numpy()), w.name
+    batch.close()
+    plain.close()
+
+
 def test_graph_replay_sees_new_contents(erpp, oracle_lib):
     """The graph keeps addresses, not values: rewriting a box's field and
     particles in place between replays is reflected in the next step."""
