@@ -100,14 +100,16 @@ __device__ __forceinline__ void for_each_piece4(const erpp_kparams& kp, const in
   }
 }
 
-// Geometry and piece places of particle i < n (the body of k_bin_count and of
-// its multi-box form).
+// Geometry of particle i < n and its pieces' bins (the body of the count
+// kernels): on_piece(k, bin) takes the particle's k-th piece a place in its
+// bin.
+template <typename OnPiece>
 __device__ __forceinline__ void bin_count_one(
     const erpp_kparams& kp, int64_t i, int64_t n, const double* __restrict__ x0,
     const double* __restrict__ x1, const double* __restrict__ x2, float4* __restrict__ geo_t,
     int4* __restrict__ geo_c, float* __restrict__ xw, int xw_len, float* __restrict__ d0x,
-    float4* __restrict__ lapc, float* __restrict__ up_acc, int64_t acc_stride,
-    int32_t* __restrict__ tile_cnt, int32_t* __restrict__ slot, int ms, uint32_t* err) {
+    float4* __restrict__ lapc, float* __restrict__ up_acc, int64_t acc_stride, int ms,
+    uint32_t* err, OnPiece on_piece) {
   double xv[3] = {x0[i], x1[i], x2[i]};
   if (up_acc && kp.design != 4) {
     up_acc[i] = 0.f;
@@ -194,11 +196,7 @@ __device__ __forceinline__ void bin_count_one(
   }
   int k = 0;
   auto place = [&](int bin) {
-    const int v = atomicAdd(&tile_cnt[bin], 1);
-    if (k < ms)
-      slot[(int64_t)k * n + i] = v;
-    else
-      erpp_set_err(err, ERPP_ERRBIT_BOUNDS);
+    on_piece(k, bin);
     ++k;
   };
   if (kp.design == 4)
@@ -219,7 +217,66 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   bin_count_one(kp, i, n, x0, x1, x2, geo_t, geo_c, xw, xw_len, d0x, lapc, up_acc, acc_stride,
-                tile_cnt, slot, ms, err);
+                ms, err, [&](int k, int bin) {
+                  const int v = atomicAdd(&tile_cnt[bin], 1);
+                  if (k < ms)
+                    slot[(int64_t)k * n + i] = v;
+                  else
+                    erpp_set_err(err, ERPP_ERRBIT_BOUNDS);
+                });
+}
+
+// Counting through a block histogram, for x/y-halo tiles with at most
+// kHistBins tiles (small boxes, where many pieces fall into few tiles and the
+// global increments of the counts would be contended): every piece of the
+// block's 256 particles first takes a place in the block's shared count of
+// its tile, each tile the block touches then takes the block's whole count
+// from its global count in one increment, and a piece's place is that base
+// plus its place in the block.  Called by the whole block (i >= n: no
+// particle).  Pieces beyond kHistPieces of a particle are refused (bounds
+// error); the caller uses it only when ms <= kHistPieces.
+constexpr int kHistBins = 4096;
+constexpr int kHistPieces = 24;
+
+__device__ __forceinline__ void bin_count_hist(
+    const erpp_kparams& kp, int64_t i, int64_t n, const double* __restrict__ x0,
+    const double* __restrict__ x1, const double* __restrict__ x2, float4* __restrict__ geo_t,
+    int4* __restrict__ geo_c, float* __restrict__ d0x, float4* __restrict__ lapc,
+    int32_t* __restrict__ tile_cnt, int32_t* __restrict__ slot, int ms, int nbins,
+    uint32_t* err, int32_t* hist) {
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  int bins[kHistPieces], loc[kHistPieces];
+  int np = 0;
+  if (i < n)
+    bin_count_one(kp, i, n, x0, x1, x2, geo_t, geo_c, nullptr, kp.xs, d0x, lapc, nullptr, 0, ms,
+                  err, [&](int k, int bin) {
+                    if (k < ms && k < kHistPieces) {
+                      bins[k] = bin;
+                      loc[k] = atomicAdd(&hist[bin], 1);
+                      np = k + 1;
+                    } else {
+                      erpp_set_err(err, ERPP_ERRBIT_BOUNDS);
+                    }
+                  });
+  __syncthreads();
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+    const int c = hist[b];
+    if (c > 0) hist[b] = atomicAdd(&tile_cnt[b], c);
+  }
+  __syncthreads();
+  for (int k = 0; k < np; ++k) slot[(int64_t)k * n + i] = hist[bins[k]] + loc[k];
+}
+
+__global__ void __launch_bounds__(256) k_bin_count_hist(
+    erpp_kparams kp, int64_t n, const double* __restrict__ x0, const double* __restrict__ x1,
+    const double* __restrict__ x2, float4* __restrict__ geo_t, int4* __restrict__ geo_c,
+    float* __restrict__ d0x, float4* __restrict__ lapc, int32_t* __restrict__ tile_cnt,
+    int32_t* __restrict__ slot, int ms, int nbins, uint32_t* err) {
+  __shared__ int32_t hist[kHistBins];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bin_count_hist(kp, i, n, x0, x1, x2, geo_t, geo_c, d0x, lapc, tile_cnt, slot, ms, nbins, err,
+                 hist);
 }
 
 // Writes one record per piece, at its bin's start plus the place the piece
@@ -394,12 +451,24 @@ __global__ void k_zero_counts_multi(const erpp_box_dev* __restrict__ boxes) {
 // One block per (box, first particle) item of 256 particles.
 __global__ void __launch_bounds__(256) k_bin_count_multi(const erpp_box_dev* __restrict__ boxes,
                                                          const int2* __restrict__ items) {
+  __shared__ int32_t hist[kHistBins];
   const int2 it = items[blockIdx.x];
   const erpp_box_dev& B = boxes[it.x];
   const int64_t i = (int64_t)it.y + threadIdx.x;
+  if (B.nbins <= kHistBins && B.ms <= kHistPieces) {  // the whole block
+    bin_count_hist(B.kp, i, B.n, B.x[0], B.x[1], B.x[2], B.geo_t, B.geo_c, B.d0x, nullptr,
+                   B.tile_cnt, B.piece_slot, B.ms, B.nbins, B.err, hist);
+    return;
+  }
   if (i >= B.n) return;
   bin_count_one(B.kp, i, B.n, B.x[0], B.x[1], B.x[2], B.geo_t, B.geo_c, nullptr, B.xw_len,
-                B.d0x, nullptr, nullptr, B.cap, B.tile_cnt, B.piece_slot, B.ms, B.err);
+                B.d0x, nullptr, nullptr, B.cap, B.ms, B.err, [&](int k, int bin) {
+                  const int v = atomicAdd(&B.tile_cnt[bin], 1);
+                  if (k < B.ms)
+                    B.piece_slot[(int64_t)k * B.n + i] = v;
+                  else
+                    erpp_set_err(B.err, ERPP_ERRBIT_BOUNDS);
+                });
 }
 
 // Block b scans the counts of box b (chunks of 4096 bins, the running total
@@ -462,7 +531,13 @@ cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bo
   const int ms = ctx->maxseg[0] * ctx->maxseg[1] * ctx->maxseg[2];
   cudaError_t e = cudaMemsetAsync(ctx->tile_cnt, 0, sizeof(int32_t) * nbins, st);
   if (e != cudaSuccess) return e;
-  if (n > 0) {
+  if (n > 0 && kp.design == 4 && !kp.full_force && nbins <= kHistBins && ms <= kHistPieces) {
+    // few tiles (a small box): count through block histograms
+    ++ctx->launches;
+    k_bin_count_hist<<<(int)((n + 255) / 256), 256, 0, st>>>(
+        kp, n, x[0], x[1], x[2], ctx->geo_t, ctx->geo_c, ctx->d0x, nullptr, ctx->tile_cnt,
+        ctx->piece_slot, ms, nbins, ctx->err);
+  } else if (n > 0) {
     int blocks = (int)((n + 255) / 256);
     ++ctx->launches;
     k_bin_count<<<blocks, 256, 0, st>>>(kp, n, x[0], x[1], x[2], ctx->geo_t, ctx->geo_c,
