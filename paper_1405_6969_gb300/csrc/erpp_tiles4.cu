@@ -91,6 +91,7 @@ constexpr uint16_t kEmpty = 0xffffu;
 // two blocks per SM.
 template <int XW>
 struct Batch {
+  // (the gather may take batches twice as large: gather_big_batch)
   static constexpr int kPB = XW <= 8 ? 256 : 128;
 };
 
@@ -379,7 +380,7 @@ __device__ __forceinline__ void row_red_split(unsigned a0, unsigned a1, unsigned
 // floats), then the batch's records, force words (scatter), x-distances,
 // Laplacian moments (general-force gather), unit words, schedule and piece
 // accumulators (gather: value sums, and Laplacian sums with lap).
-template <int XW>
+template <int PB>
 struct Carve {
   float* field;
   int4* rec;
@@ -398,10 +399,9 @@ constexpr int kFieldPad = 16;
 // The unit words, the schedule and the gather's piece accumulators are sized
 // for the tile's tz planes (a piece has at most tz units); the schedule holds
 // whole rounds of up to 512 threads.
-template <int XW>
+template <int PB>
 __host__ __device__ inline size_t carve_bytes(int plane, int tz, int copies, bool gather,
                                               bool lap = false) {
-  constexpr int PB = Batch<XW>::kPB;
   const int NU = PB * tz, NS = (NU + 511) & ~511;
   size_t b = ((size_t)copies * plane + kFieldPad) * 4;
   b += (size_t)PB * 16;          // rec
@@ -416,12 +416,11 @@ __host__ __device__ inline size_t carve_bytes(int plane, int tz, int copies, boo
   return b;
 }
 
-template <int XW>
-__device__ inline Carve<XW> carve(unsigned char* base, int plane, int tz, int copies, bool gather,
+template <int PB>
+__device__ inline Carve<PB> carve(unsigned char* base, int plane, int tz, int copies, bool gather,
                                   bool lap = false) {
-  constexpr int PB = Batch<XW>::kPB;
   const int NU = PB * tz, NS = (NU + 511) & ~511;
-  Carve<XW> c;
+  Carve<PB> c;
   size_t o = 0;
   c.field = reinterpret_cast<float*>(base);
   o += ((size_t)copies * plane + kFieldPad) * 4;
@@ -560,8 +559,8 @@ __device__ void stage_tile_rows(const erpp_kparams& kp, const float* __restrict_
 
 // Builds the unit schedule of pieces [0, np) (records in cv.rec).  Returns
 // the number of rounds.  Called by the whole block; synchronises.
-template <int XW, int NT>
-__device__ int build_schedule(const Carve<XW>& cv, SchedState& ss, int np) {
+template <int PB, int NT>
+__device__ int build_schedule(const Carve<PB>& cv, SchedState& ss, int np) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x;
   if (tid < 16) ss.pair[tid] = 0;
@@ -633,26 +632,36 @@ __device__ __forceinline__ int batch_size(int total, int PB) {
   return (total + nb - 1) / nb;
 }
 
-// A batch holds at most one piece per thread (PB <= threads per block):
-// thread k loads record k of the batch (issued early, so that its latency
+// Thread k loads record k of the batch (issued early, so that its latency
 // overlaps other work), then stages it and, through the particle index, the
-// particle's x-distance and (scatter) force word (asynchronous copies).
+// particle's x-distance and (scatter) force word (asynchronous copies); a
+// batch larger than the block stages its further records k + NT, ... too.
 __device__ __forceinline__ int4 load_rec(const int4* __restrict__ entries, int b0, int np) {
   return threadIdx.x < np ? __ldg(&entries[b0 + threadIdx.x]) : make_int4(0, 0, 0, 0);
 }
-template <int XW, bool FORCES, bool LAP = false>
-__device__ void stage_batch(const Carve<XW>& cv, int4 r, int np, const float* __restrict__ d0x,
+template <int PB, bool FORCES, bool LAP = false>
+__device__ __forceinline__ void stage_one(const Carve<PB>& cv, int k, int4 r,
+                                          const float* __restrict__ d0x,
+                                          const float4* __restrict__ fscat,
+                                          const float4* __restrict__ lapc) {
+  cv.rec[k] = r;
+  cp_async4(cv.dxb + k, d0x + r.x);
+  if (FORCES) cp_async16(cv.fsb + k, fscat + r.x);
+  if (LAP) {
+    cp_async16(cv.lcb + 2 * k, lapc + 2 * (size_t)r.x);
+    cp_async16(cv.lcb + 2 * k + 1, lapc + 2 * (size_t)r.x + 1);
+  }
+}
+template <int PB, bool FORCES, bool LAP = false>
+__device__ void stage_batch(const Carve<PB>& cv, int4 r, int np, int b0,
+                            const int4* __restrict__ entries, const float* __restrict__ d0x,
                             const float4* __restrict__ fscat,
                             const float4* __restrict__ lapc = nullptr) {
   const int k = threadIdx.x;
-  if (k < np) {
-    cv.rec[k] = r;
-    cp_async4(cv.dxb + k, d0x + r.x);
-    if (FORCES) cp_async16(cv.fsb + k, fscat + r.x);
-    if (LAP) {
-      cp_async16(cv.lcb + 2 * k, lapc + 2 * (size_t)r.x);
-      cp_async16(cv.lcb + 2 * k + 1, lapc + 2 * (size_t)r.x + 1);
-    }
+  if (k < np) stage_one<PB, FORCES, LAP>(cv, k, r, d0x, fscat, lapc);
+  if constexpr (PB > 256) {
+    for (int j = k + blockDim.x; j < np; j += blockDim.x)
+      stage_one<PB, FORCES, LAP>(cv, j, __ldg(&entries[b0 + j]), d0x, fscat, lapc);
   }
 }
 
@@ -673,20 +682,19 @@ struct UnitRows {
 // plane's own factors.  tmap: the field's tensor map (parameter or global
 // memory).  Returns bit 0: a bounded wait ran out (the block gave the tile
 // up); bit 1: the staging barriers were initialised.
-template <int XM, int LMIN, int XW, int NT, bool LAP>
+template <int XM, int LMIN, int XW, int NT, bool LAP, int PB>
 __device__ __forceinline__ int gather_tile4(
     const erpp_kparams& kp, int tile, const float* __restrict__ u, const CUtensorMap* tmap,
     int use_tma, const int32_t* __restrict__ start, const int4* __restrict__ entries,
     int64_t ecap, const float* __restrict__ d0x, const float4* __restrict__ lapc,
     float4* __restrict__ up_part, float4* __restrict__ lap_part, uint32_t* err,
     unsigned char* smem_raw, SchedState& ss, uint64_t& tma_bar, uint64_t& stall_bar) {
-  constexpr int PB = Batch<XW>::kPB;
-  static_assert(PB <= NT, "a batch holds at most one piece per thread");
+  static_assert(PB <= 1024, "unit words hold the piece index in 10 bits");
   const int e0 = start[tile];
   const int e1 = (int)min((int64_t)start[tile + 1], ecap);
   if (e0 >= e1) return 0;
   const int tzs = kp.T[2];  // planes per tile: units per piece, at most
-  const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, tzs, 3, true, LAP);
+  const Carve<PB> cv = carve<PB>(smem_raw, kp.plane, tzs, 3, true, LAP);
   int b[3], ext[3], tt[3];
   tile_origin4(kp, tile, b, ext, tt);
   // one TMA box when the staged rows need no periodic wrap
@@ -740,9 +748,9 @@ __device__ __forceinline__ int gather_tile4(
   const unsigned fbase = shared_addr(cv.field);
   for (int b0 = e0; b0 < e1; b0 += bs) {
     const int np = min(bs, e1 - b0);
-    stage_batch<XW, false, LAP>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, d0x,
-                                nullptr, lapc);
-    const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
+    stage_batch<PB, false, LAP>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, b0,
+                                entries, d0x, nullptr, lapc);
+    const int R = build_schedule<PB, NT>(cv, ss, np);  // synchronises
     cp_async_wait_all();                            // field (first batch), x-distances
     // One thread waits (bounded) for the staged field; the block learns the
     // outcome at the barrier and either goes on or returns as a whole.
@@ -901,7 +909,7 @@ __device__ __forceinline__ int gather_tile4(
   return (tma || rows) ? 2 : 0;
 }
 
-template <int XM, int LMIN, int XW, int NT, bool LAP>
+template <int XM, int LMIN, int XW, int NT, bool LAP, int PB>
 __global__ void __launch_bounds__(NT, LAP ? 2 : 768 / NT) k_gather4(
     erpp_kparams kp, const float* __restrict__ u, const __grid_constant__ CUtensorMap tmap,
     int use_tma, const int32_t* __restrict__ start, const int4* __restrict__ entries,
@@ -911,9 +919,9 @@ __global__ void __launch_bounds__(NT, LAP ? 2 : 768 / NT) k_gather4(
   __shared__ SchedState ss;
   __shared__ __align__(8) uint64_t tma_bar;
   __shared__ __align__(8) uint64_t stall_bar;  // debug_stall only: never completed
-  gather_tile4<XM, LMIN, XW, NT, LAP>(kp, blockIdx.x, u, &tmap, use_tma, start, entries, ecap,
-                                      d0x, lapc, up_part, lap_part, err, smem_raw, ss, tma_bar,
-                                      stall_bar);
+  gather_tile4<XM, LMIN, XW, NT, LAP, PB>(kp, blockIdx.x, u, &tmap, use_tma, start, entries,
+                                          ecap, d0x, lapc, up_part, lap_part, err, smem_raw, ss,
+                                          tma_bar, stall_bar);
 }
 
 // MODE 0: 32-bit fixed point (FP32 atomics on dense tiles); MODE 1: split
@@ -940,7 +948,8 @@ struct TileAcc {
 // end (MODE 1).  Called by the whole block.
 template <int XM, int LMIN, int XW, int MODE, int NT>
 __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile,
-                                                const Carve<XW>& cv, SchedState& ss, float* red,
+                                                const Carve<Batch<XW>::kPB>& cv, SchedState& ss,
+                                                float* red,
                                                 const int32_t* __restrict__ start,
                                                 const int4* __restrict__ entries, int64_t ecap,
                                                 const float* __restrict__ d0x,
@@ -1021,8 +1030,9 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
     const unsigned fbase = shared_addr(smem);
     for (int b0 = e0; b0 < e1; b0 += bs) {
       const int np = min(bs, e1 - b0);
-      stage_batch<XW, true>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, d0x, fscat);
-      const int R = build_schedule<XW, NT>(cv, ss, np);  // synchronises
+      stage_batch<PB, true>(cv, b0 == e0 ? rfirst : load_rec(entries, b0, np), np, b0, entries,
+                            d0x, fscat);
+      const int R = build_schedule<PB, NT>(cv, ss, np);  // synchronises
       cp_async_wait_all();
       __syncthreads();
       if (fixedp && single) {
@@ -1145,7 +1155,7 @@ __device__ __forceinline__ void scatter_tile4(const erpp_kparams& kp, int tile,
   constexpr int NW = NT / 32;
   constexpr int PB = Batch<XW>::kPB;
   static_assert(PB <= NT, "a batch holds at most one piece per thread");
-  const Carve<XW> cv = carve<XW>(smem_raw, kp.plane, kp.T[2], MODE == 1 ? 6 : 3, false);
+  const Carve<PB> cv = carve<PB>(smem_raw, kp.plane, kp.T[2], MODE == 1 ? 6 : 3, false);
   float* smem = cv.field;
   const TileAcc ta =
       scatter_tile<XM, LMIN, XW, MODE, NT>(kp, tile, cv, ss, red, start, entries, ecap, d0x,
@@ -1495,12 +1505,12 @@ bool field_tensor_map(const erpp_kparams& kp, const float* u, CUtensorMap* map) 
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int XM, int LMIN, int XW, int NT, bool LAP>
+template <int XM, int LMIN, int XW, int NT, bool LAP, int PB>
 cudaError_t gather4_nt(erpp_ctx* ctx, const float* u, cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;
   if (LAP && (!ctx->lapc || !ctx->lap_part)) return cudaErrorInvalidValue;
-  const size_t sm = carve_bytes<XW>(kp.plane, kp.T[2], 3, true, LAP);
-  auto kern = k_gather4<XM, LMIN, XW, NT, LAP>;
+  const size_t sm = carve_bytes<PB>(kp.plane, kp.T[2], 3, true, LAP);
+  auto kern = k_gather4<XM, LMIN, XW, NT, LAP, PB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   CUtensorMap map;
@@ -1513,14 +1523,31 @@ cudaError_t gather4_nt(erpp_ctx* ctx, const float* u, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Blocks of the gather per SM for a dynamic shared-memory size (the SM's
+// 228 KB, 1 KB reserved and about 0.4 KB of static shared memory per block).
+inline int gather_blocks_per_sm(size_t smem) {
+  return (int)((228u * 1024u) / (smem + 1024u + 512u));
+}
+// The gather takes batches of twice the pieces when that costs no block per
+// SM (at most three: its registers allow three 256-thread blocks): more units
+// per batch fill the schedule's rounds better.
+inline bool gather_big_batch(size_t small, size_t big) {
+  return std::min(gather_blocks_per_sm(big), 3) >= std::min(gather_blocks_per_sm(small), 3);
+}
+
 // LAP (the general force's gather) always runs 256-thread blocks.
 template <int XM, int LMIN, int XW, bool LAP = false>
 cudaError_t gather4(erpp_ctx* ctx, const float* u, cudaStream_t st) {
+  constexpr int PB = Batch<XW>::kPB;
   if constexpr (LAP) {
-    return gather4_nt<XM, LMIN, XW, 256, true>(ctx, u, st);
+    return gather4_nt<XM, LMIN, XW, 256, true, PB>(ctx, u, st);
   } else {
-    return ctx->kp.nthreads == 512 ? gather4_nt<XM, LMIN, XW, 512, false>(ctx, u, st)
-                                   : gather4_nt<XM, LMIN, XW, 256, false>(ctx, u, st);
+    if (ctx->kp.nthreads == 512) return gather4_nt<XM, LMIN, XW, 512, false, PB>(ctx, u, st);
+    const erpp_kparams& kp = ctx->kp;
+    if (gather_big_batch(carve_bytes<PB>(kp.plane, kp.T[2], 3, true),
+                         carve_bytes<2 * PB>(kp.plane, kp.T[2], 3, true)))
+      return gather4_nt<XM, LMIN, XW, 256, false, 2 * PB>(ctx, u, st);
+    return gather4_nt<XM, LMIN, XW, 256, false, PB>(ctx, u, st);
   }
 }
 
@@ -1530,7 +1557,7 @@ cudaError_t gather4(erpp_ctx* ctx, const float* u, cudaStream_t st) {
 template <int XM, int LMIN, int XW, int MODE, int NT, bool CL>
 cudaError_t scatter4_mode(erpp_ctx* ctx, float* S, cudaStream_t st) {
   const erpp_kparams& kp = ctx->kp;
-  const size_t sm = carve_bytes<XW>(kp.plane, kp.T[2], MODE == 1 ? 6 : 3, false);
+  const size_t sm = carve_bytes<Batch<XW>::kPB>(kp.plane, kp.T[2], MODE == 1 ? 6 : 3, false);
   auto kern = k_scatter4<XM, LMIN, XW, MODE, NT, CL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -1642,7 +1669,7 @@ __global__ void __launch_bounds__(256, 3) k_gather4_multi(const BoxTiles* __rest
     if (it >= nitems) break;
     const int2 bt = items[it];
     const BoxTiles& B = boxes[bt.x];
-    const int r = gather_tile4<XM, LMIN, XW, 256, false>(
+    const int r = gather_tile4<XM, LMIN, XW, 256, false, Batch<XW>::kPB>(
         B.kp, bt.y, B.u, &B.tmap, B.use_tma, B.start, B.entries, B.ecap, B.d0x, nullptr,
         B.up_part, nullptr, B.err, smem_raw, ss, tma_bar, stall_bar);
     // every thread is done with the tile, its barriers and `item`
@@ -1723,8 +1750,11 @@ int xw4(const erpp_kparams& kp) {
 size_t smem_bytes4(const erpp_kparams& kp, int copies, bool gather) {
   const bool lap = gather && kp.full_force;
   const int tz = kp.plane / kp.pxy;
-  return xw4(kp) == 8 ? carve_bytes<8>(kp.plane, tz, copies, gather, lap)
-                      : carve_bytes<16>(kp.plane, tz, copies, gather, lap);
+  if (gather)  // the smaller batch: the launch takes the larger only when it fits as well
+    return xw4(kp) == 8 ? carve_bytes<Batch<8>::kPB>(kp.plane, tz, copies, true, lap)
+                        : carve_bytes<Batch<16>::kPB>(kp.plane, tz, copies, true, lap);
+  return xw4(kp) == 8 ? carve_bytes<Batch<8>::kPB>(kp.plane, tz, copies, false, lap)
+                      : carve_bytes<Batch<16>::kPB>(kp.plane, tz, copies, false, lap);
 }
 
 template <bool LAP>
