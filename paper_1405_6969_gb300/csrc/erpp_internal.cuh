@@ -511,11 +511,25 @@ __device__ __forceinline__ void erpp_gathered(const erpp_kparams& kp, const erpp
   if (kp.design == 4) {
     const int np = __float_as_int(gt.w);
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    for (int k = 0; k < np; ++k) {
-      const float4 v = acc.up_part[acc.piece_slot[(int64_t)k * acc.n + i]];
-      a0 += v.x;
-      a1 += v.y;
-      a2 += v.z;
+    // four pieces at a time: their places, then their sums, are loaded
+    // together (independent loads in flight at once), then added in order
+    for (int k0 = 0; k0 < np; k0 += 4) {
+      int sl[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        sl[j] = k0 + j < np ? acc.piece_slot[(int64_t)(k0 + j) * acc.n + i] : -1;
+      float4 v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        v[j] = sl[j] >= 0 ? acc.up_part[sl[j]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (k0 + j < np) {
+          a0 += v[j].x;
+          a1 += v[j].y;
+          a2 += v[j].z;
+        }
+      }
     }
     out[0] = a0;
     out[1] = a1;
