@@ -168,7 +168,7 @@ def test_config_adjoint_128cube_autograd(erpp, oracle_lib):
     assert rel(gD, rdD) < 1e-5
     assert rel(gx, rdx) < 1e-5
     L_ref = float(np.sum((S_ref - T) ** 2))
-    assert abs(float(loss) - L_ref) < 1e-5 * L_ref
+    assert abs(float(loss.detach()) - L_ref) < 1e-5 * L_ref
 
     # central differences of the FP64 oracle loss, evaluated locally: moving
     # particle i changes S only on its stencil box
