@@ -623,6 +623,26 @@ def main():
                     "peak_kind": peak_kind}
     step_gbs = alg["step"] / (ms_per_step * 1e-3) / 1e9
 
+    # the scatter phase against the measured rate of the shared-memory add it
+    # accumulates with: each stencil node of each particle receives one
+    # contribution per force component (one 32-bit add, two with the split
+    # words of the compensated form)
+    atomics = None
+    if nsteps > 0 and args.weights == "gaussian":
+        from paper_1405_6969_gb300 import shared_add_rate
+        peak_s32 = shared_add_rate("s32")
+        updates = 3 * (nodes_per_step // 2)
+        ach = updates / (per["scatter"] * 1e-3)
+        atomics = {"kernel": "scatter phase (accumulation, write-out, halo merges)",
+                   "node_component_updates": updates,
+                   "adds_per_update": 2 if args.kahan else 1,
+                   "achieved_updates_per_s": ach,
+                   "peak_adds_per_s": peak_s32,
+                   "frac": ach * (2 if args.kahan else 1) / peak_s32,
+                   "peak_fp32_adds_per_s": shared_add_rate("f32"),
+                   "peak_kind": "measured live: shared-memory 32-bit atomic add, conflict-free "
+                                "lanes, every SM full (erpp_shared_add_rate)"}
+
     # the closed loop of the shear workload: coupling step, then the fluid
     # stand-in forced by the new source (the fluid is timed on its own too)
     loop = None
@@ -778,6 +798,7 @@ def main():
             "step_hbm": {"alg_bytes": alg["step"], "achieved_gbs": step_gbs,
                          "frac": step_gbs / peak},
             "roofline": roofline,
+            "atomics": atomics,
             "cpu_baseline": cpu,
             "error_vs_oracle": errors,
             "kahan": extra.get("kahan"),

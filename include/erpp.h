@@ -477,6 +477,24 @@ erpp_status erpp_last_step_launches(erpp_ctx* ctx, int32_t* n);
 erpp_status erpp_profile_enable(erpp_ctx* ctx, int enable);
 erpp_status erpp_profile_read(erpp_ctx* ctx, double ms[4], int64_t* steps);
 
+/* Measured peak of the scatter's accumulating operation (a measurement aid,
+ * not part of the method).  In the scatter (Sec. 2.4, Eq.
+ * ns_regularized_filtered) each stencil node of each particle receives one
+ * contribution per force component, which the tile kernels add to the
+ * staged tile with one shared-memory atomic add: a 32-bit fixed-point
+ * integer (ERPP_RATE_SHARED_S32), or an FP32 value on tiles of more than
+ * 1024 pieces (ERPP_RATE_SHARED_F32).  erpp_shared_add_rate times that add
+ * on the current device with nothing else limiting it (every SM full of
+ * 256-thread blocks whose lanes add to 32 distinct banks, 16 adds unrolled
+ * per loop iteration; the fastest of three timed launches after one
+ * warm-up) and writes the lane adds completed per second to the HOST
+ * double *adds_per_s.  Synchronous: it allocates 4 bytes of device memory,
+ * a stream and two events, and frees them before returning.  ERPP_EINVAL
+ * for another kind or a null pointer (*adds_per_s is then untouched),
+ * ERPP_ECUDA or ERPP_ENOMEM when a CUDA call fails (*adds_per_s = 0). */
+enum { ERPP_RATE_SHARED_S32 = 0, ERPP_RATE_SHARED_F32 = 1 };
+erpp_status erpp_shared_add_rate(int32_t kind, double* adds_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,7 +8,8 @@ The computation lives in the CUDA library ``liberpp.so`` behind the C ABI of
 from ._lib import (FP32, FP64, FULL_FORCE, KAHAN, LAG, NORMALIZE, PIC,  # noqa: F401
                    POINT_GATHER, SELF_REMOVAL, ErppError, load)
 from .erpp import (Batch, Context, Interpolate, ParticleState, ScatterSource,  # noqa: F401
-                   StokesFluid)
+                   StokesFluid, shared_add_rate)
 
 __all__ = ["Batch", "Context", "StokesFluid", "ParticleState", "ScatterSource", "Interpolate", "ErppError", "load",
+           "shared_add_rate",
            "FP32", "FP64", "NORMALIZE", "SELF_REMOVAL", "KAHAN", "PIC", "POINT_GATHER", "LAG", "FULL_FORCE"]

@@ -92,6 +92,7 @@ _SIGS = {
     "erpp_interpolate_noalloc": (_st, [ctypes.POINTER(Params), _vp, _i64, _dp3, _dp3, _vp]),
     "erpp_profile_enable": (_st, [_vp, ctypes.c_int]),
     "erpp_profile_read": (_st, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)]),
+    "erpp_shared_add_rate": (_st, [ctypes.c_int32, _dp]),
     "erpp_batch_init": (_st, [ctypes.c_int32, ctypes.POINTER(BoxDesc), ctypes.POINTER(_vp)]),
     "erpp_step_batched": (_st, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
     "erpp_batch_check": (_st, [_vp, _vp]),

@@ -458,6 +458,21 @@ class Batch:
             pass
 
 
+SHARED_ADD_KINDS = {"s32": 0, "f32": 1}
+
+
+def shared_add_rate(kind="s32"):
+    """Lane adds per second of the shared-memory atomic add the scatter
+    accumulates with, measured on the current device with nothing else
+    limiting it (erpp_shared_add_rate): "s32" the 32-bit fixed-point add,
+    "f32" the FP32 add of dense tiles."""
+    lib = _lib.load()
+    out = ctypes.c_double(0.0)
+    _lib.check(lib.erpp_shared_add_rate(SHARED_ADD_KINDS[kind], ctypes.byref(out)),
+               "erpp_shared_add_rate")
+    return float(out.value)
+
+
 class ScatterSource(torch.autograd.Function):
     """S = source(x, D) (Eq. ns_regularized_filtered) with its hand-written
     adjoint: ``ScatterSource.apply(ctx, x, D)`` for [3, n] float64 x and D."""

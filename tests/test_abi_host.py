@@ -61,5 +61,6 @@ def test_null_arguments(lib):
     assert so.erpp_destroy(None) == 0
     assert so.erpp_step(None, None, None, None, 0, None) == 1
     assert so.erpp_check(None, None) == 1
+    assert so.erpp_shared_add_rate(0, None) == 1
     for s in range(8):
         assert so.erpp_status_string(s)
