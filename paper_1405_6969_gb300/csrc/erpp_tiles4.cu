@@ -75,6 +75,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "erpp_internal.cuh"
@@ -288,26 +289,27 @@ __device__ __forceinline__ int mul_hi_round(int g, int w) {
 // reach holds a finite value: staged field, or zeros the gather wrote).
 // Scatter (fixed point): u_c(q) += high word of G_c(q) W.  Scatter (FP32):
 // u_c(q) += f_c w e_x(q).  a0..a2: shared addresses of the row's first node
-// per component.
-template <int Q, int XM>
+// per component.  Slots Q < NQ are visited (NQ = LMIN when no lane's window
+// is longer: slots past a window have weight 0 and add nothing).
+template <int Q, int XM, int NQ = XM>
 __device__ __forceinline__ void row_dot(unsigned a0, unsigned a1, unsigned a2, const float (&ex)[XM],
                                         float& x0, float& x1, float& x2) {
-  if constexpr (Q < XM) {
+  if constexpr (Q < NQ) {
     x0 = fmaf(ex[Q], lds_f32<4 * Q>(a0), x0);
     x1 = fmaf(ex[Q], lds_f32<4 * Q>(a1), x1);
     x2 = fmaf(ex[Q], lds_f32<4 * Q>(a2), x2);
-    row_dot<Q + 1, XM>(a0, a1, a2, ex, x0, x1, x2);
+    row_dot<Q + 1, XM, NQ>(a0, a1, a2, ex, x0, x1, x2);
   }
 }
 
 // row_dot with a second set of x-weights on the same loaded values: x_c +=
 // e_x(q) u_c(q) and y_c += e2_x(q) u_c(q) (the general force's gather of the
 // velocity and of its Laplacian).
-template <int Q, int XM>
+template <int Q, int XM, int NQ = XM>
 __device__ __forceinline__ void row_dot2(unsigned a0, unsigned a1, unsigned a2,
                                          const float (&ex)[XM], const float (&e2)[XM], float& x0,
                                          float& x1, float& x2, float& y0, float& y1, float& y2) {
-  if constexpr (Q < XM) {
+  if constexpr (Q < NQ) {
     const float u0 = lds_f32<4 * Q>(a0), u1 = lds_f32<4 * Q>(a1), u2 = lds_f32<4 * Q>(a2);
     x0 = fmaf(ex[Q], u0, x0);
     x1 = fmaf(ex[Q], u1, x1);
@@ -315,36 +317,36 @@ __device__ __forceinline__ void row_dot2(unsigned a0, unsigned a1, unsigned a2,
     y0 = fmaf(e2[Q], u0, y0);
     y1 = fmaf(e2[Q], u1, y1);
     y2 = fmaf(e2[Q], u2, y2);
-    row_dot2<Q + 1, XM>(a0, a1, a2, ex, e2, x0, x1, x2, y0, y1, y2);
+    row_dot2<Q + 1, XM, NQ>(a0, a1, a2, ex, e2, x0, x1, x2, y0, y1, y2);
   }
 }
 
-template <int Q, int XM, int LMIN>
+template <int Q, int XM, int LMIN, int NQ = XM>
 __device__ __forceinline__ void row_red_fixed(unsigned a0, unsigned a1, unsigned a2,
                                               const int (&G0)[XM], const int (&G1)[XM],
                                               const int (&G2)[XM], int W, int lx) {
-  if constexpr (Q < XM) {
+  if constexpr (Q < NQ) {
     if (Q < LMIN || Q < lx) {
       red_s32<4 * Q>(a0, mul_hi_round(G0[Q], W));
       red_s32<4 * Q>(a1, mul_hi_round(G1[Q], W));
       red_s32<4 * Q>(a2, mul_hi_round(G2[Q], W));
     }
-    row_red_fixed<Q + 1, XM, LMIN>(a0, a1, a2, G0, G1, G2, W, lx);
+    row_red_fixed<Q + 1, XM, LMIN, NQ>(a0, a1, a2, G0, G1, G2, W, lx);
   }
 }
 
-template <int Q, int XM, int LMIN>
+template <int Q, int XM, int LMIN, int NQ = XM>
 __device__ __forceinline__ void row_red_f32(unsigned a0, unsigned a1, unsigned a2,
                                             const float (&ex)[XM], float f0, float f1, float f2,
                                             float wy, int lx) {
-  if constexpr (Q < XM) {
+  if constexpr (Q < NQ) {
     if (Q < LMIN || Q < lx) {
       const float wq = wy * ex[Q];
       red_f32<4 * Q>(a0, f0 * wq);
       red_f32<4 * Q>(a1, f1 * wq);
       red_f32<4 * Q>(a2, f2 * wq);
     }
-    row_red_f32<Q + 1, XM, LMIN>(a0, a1, a2, ex, f0, f1, f2, wy, lx);
+    row_red_f32<Q + 1, XM, LMIN, NQ>(a0, a1, a2, ex, f0, f1, f2, wy, lx);
   }
 }
 
@@ -362,17 +364,17 @@ __device__ __forceinline__ void red_split(unsigned a, unsigned lo, int g, int w)
   red_s32<OFF>(a + lo, (int)(l >> 17));
 }
 
-template <int Q, int XM, int LMIN>
+template <int Q, int XM, int LMIN, int NQ = XM>
 __device__ __forceinline__ void row_red_split(unsigned a0, unsigned a1, unsigned a2, unsigned lo,
                                               const int (&G0)[XM], const int (&G1)[XM],
                                               const int (&G2)[XM], int W, int lx) {
-  if constexpr (Q < XM) {
+  if constexpr (Q < NQ) {
     if (Q < LMIN || Q < lx) {
       red_split<4 * Q>(a0, lo, G0[Q], W);
       red_split<4 * Q>(a1, lo, G1[Q], W);
       red_split<4 * Q>(a2, lo, G2[Q], W);
     }
-    row_red_split<Q + 1, XM, LMIN>(a0, a1, a2, lo, G0, G1, G2, W, lx);
+    row_red_split<Q + 1, XM, LMIN, NQ>(a0, a1, a2, lo, G0, G1, G2, W, lx);
   }
 }
 
@@ -824,50 +826,58 @@ __device__ __forceinline__ int gather_tile4(
       const unsigned pl4 = 4u * (unsigned)plane, px4 = 4u * (unsigned)px;
       const unsigned abase = fbase + 4u * (unsigned)(active ? ur.base : lane);
       const unsigned aend = abase + px4 * (unsigned)ur.ly;
-      unsigned ar = abase + px4 * (unsigned)ur.rot;
-      float dy = ur.d0y + (float)ur.rot;
+      // the rows, visiting the slots of the longest window in the warp
+      auto unit_rows = [&](auto nq) {
+        constexpr int NQ = decltype(nq)::value;
+        unsigned ar = abase + px4 * (unsigned)ur.rot;
+        float dy = ur.d0y + (float)ur.rot;
 #pragma unroll 1
-      for (int t = 0; t < rows; ++t) {
-        const float e = exp2f(-fmaf(by * dy, dy, ur.ezz));
-        const bool in = t < ur.ly;
-        const float wr = in ? e : 0.f;
-        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-        float y0 = 0.f, y1 = 0.f, y2 = 0.f;
-        if constexpr (LAP)
-          row_dot2<0, XM>(ar, ar + pl4, ar + 2 * pl4, ex, e2, x0, x1, x2, y0, y1, y2);
-        else
-          row_dot<0, XM>(ar, ar + pl4, ar + 2 * pl4, ex, x0, x1, x2);
-        // LAP: the row's Laplacian term, (P_y + P_z) x_c + y_c
-        float pr = 0.f;
-        if (LAP) {
-          const float ddy = dy - my;
-          pr = fmaf(kp.lap_k[1], fmaf(ddy, ddy, -vy), pz);
-        }
-        if (in && ar == abase) {
-          r0 = wr * x0;
-          r1 = wr * x1;
-          r2 = wr * x2;
+        for (int t = 0; t < rows; ++t) {
+          const float e = exp2f(-fmaf(by * dy, dy, ur.ezz));
+          const bool in = t < ur.ly;
+          const float wr = in ? e : 0.f;
+          float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+          float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+          if constexpr (LAP)
+            row_dot2<0, XM, NQ>(ar, ar + pl4, ar + 2 * pl4, ex, e2, x0, x1, x2, y0, y1, y2);
+          else
+            row_dot<0, XM, NQ>(ar, ar + pl4, ar + 2 * pl4, ex, x0, x1, x2);
+          // LAP: the row's Laplacian term, (P_y + P_z) x_c + y_c
+          float pr = 0.f;
           if (LAP) {
-            q0 = wr * fmaf(pr, x0, y0);
-            q1 = wr * fmaf(pr, x1, y1);
-            q2 = wr * fmaf(pr, x2, y2);
+            const float ddy = dy - my;
+            pr = fmaf(kp.lap_k[1], fmaf(ddy, ddy, -vy), pz);
           }
-        } else {
-          a0 = fmaf(wr, x0, a0);
-          a1 = fmaf(wr, x1, a1);
-          a2 = fmaf(wr, x2, a2);
-          if (LAP) {
-            l0 = fmaf(wr, fmaf(pr, x0, y0), l0);
-            l1 = fmaf(wr, fmaf(pr, x1, y1), l1);
-            l2 = fmaf(wr, fmaf(pr, x2, y2), l2);
+          if (in && ar == abase) {
+            r0 = wr * x0;
+            r1 = wr * x1;
+            r2 = wr * x2;
+            if (LAP) {
+              q0 = wr * fmaf(pr, x0, y0);
+              q1 = wr * fmaf(pr, x1, y1);
+              q2 = wr * fmaf(pr, x2, y2);
+            }
+          } else {
+            a0 = fmaf(wr, x0, a0);
+            a1 = fmaf(wr, x1, a1);
+            a2 = fmaf(wr, x2, a2);
+            if (LAP) {
+              l0 = fmaf(wr, fmaf(pr, x0, y0), l0);
+              l1 = fmaf(wr, fmaf(pr, x1, y1), l1);
+              l2 = fmaf(wr, fmaf(pr, x2, y2), l2);
+            }
           }
+          ar += px4;
+          dy += 1.f;
+          const bool wrap = ar == aend;
+          ar = wrap ? abase : ar;
+          dy = wrap ? ur.d0y : dy;
         }
-        ar += px4;
-        dy += 1.f;
-        const bool wrap = ar == aend;
-        ar = wrap ? abase : ar;
-        dy = wrap ? ur.d0y : dy;
-      }
+      };
+      if (LMIN < XM && __all_sync(0xffffffffu, ur.lx <= LMIN))
+        unit_rows(std::integral_constant<int, LMIN>());
+      else
+        unit_rows(std::integral_constant<int, XM>());
       if (active) {
         // the unit's own slot (piece k, plane uz): no two units share one
         float* pa = cv.pacc + uz * PB + k;
@@ -1084,46 +1094,54 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
         const unsigned pl4 = 4u * (unsigned)plane, px4 = 4u * (unsigned)px;
         const unsigned abase = fbase + 4u * (unsigned)(active ? ur.base : lane);
         const unsigned aend = abase + px4 * (unsigned)ur.ly;
-        unsigned ar = abase + px4 * (unsigned)ur.rot;
-        float dy = ur.d0y + (float)ur.rot;
-        if (MODE == 1 && fixedp) {
-          const unsigned lo = 3u * pl4;  // the low sums follow the three components
+        // the rows, visiting the slots of the longest window in the warp
+        auto unit_rows = [&](auto nq) {
+          constexpr int NQ = decltype(nq)::value;
+          unsigned ar = abase + px4 * (unsigned)ur.rot;
+          float dy = ur.d0y + (float)ur.rot;
+          if (MODE == 1 && fixedp) {
+            const unsigned lo = 3u * pl4;  // the low sums follow the three components
 #pragma unroll 1
-          for (int t = 0; t < rows; ++t) {
-            const float e = exp2f(-by * dy * dy);
-            const int W = t < ur.ly ? __float2int_rn(e * 2147483648.f) : 0;
-            row_red_split<0, XM, LMIN>(ar, ar + pl4, ar + 2 * pl4, lo, G0, G1, G2, W, ur.lx);
-            ar += px4;
-            dy += 1.f;
-            const bool wrap = ar == aend;
-            ar = wrap ? abase : ar;
-            dy = wrap ? ur.d0y : dy;
-          }
-        } else if (fixedp) {
+            for (int t = 0; t < rows; ++t) {
+              const float e = exp2f(-by * dy * dy);
+              const int W = t < ur.ly ? __float2int_rn(e * 2147483648.f) : 0;
+              row_red_split<0, XM, LMIN, NQ>(ar, ar + pl4, ar + 2 * pl4, lo, G0, G1, G2, W, ur.lx);
+              ar += px4;
+              dy += 1.f;
+              const bool wrap = ar == aend;
+              ar = wrap ? abase : ar;
+              dy = wrap ? ur.d0y : dy;
+            }
+          } else if (fixedp) {
 #pragma unroll 1
-          for (int t = 0; t < rows; ++t) {
-            const float e = exp2f(-by * dy * dy);
-            const int W = t < ur.ly ? __float2int_rn(e * 2147483648.f) : 0;
-            row_red_fixed<0, XM, LMIN>(ar, ar + pl4, ar + 2 * pl4, G0, G1, G2, W, ur.lx);
-            ar += px4;
-            dy += 1.f;
-            const bool wrap = ar == aend;
-            ar = wrap ? abase : ar;
-            dy = wrap ? ur.d0y : dy;
-          }
-        } else {
+            for (int t = 0; t < rows; ++t) {
+              const float e = exp2f(-by * dy * dy);
+              const int W = t < ur.ly ? __float2int_rn(e * 2147483648.f) : 0;
+              row_red_fixed<0, XM, LMIN, NQ>(ar, ar + pl4, ar + 2 * pl4, G0, G1, G2, W, ur.lx);
+              ar += px4;
+              dy += 1.f;
+              const bool wrap = ar == aend;
+              ar = wrap ? abase : ar;
+              dy = wrap ? ur.d0y : dy;
+            }
+          } else {
 #pragma unroll 1
-          for (int t = 0; t < rows; ++t) {
-            const float e = exp2f(-by * dy * dy);
-            const float wy = t < ur.ly ? e : 0.f;
-            row_red_f32<0, XM, LMIN>(ar, ar + pl4, ar + 2 * pl4, ex, f0, f1, f2, wy, ur.lx);
-            ar += px4;
-            dy += 1.f;
-            const bool wrap = ar == aend;
-            ar = wrap ? abase : ar;
-            dy = wrap ? ur.d0y : dy;
+            for (int t = 0; t < rows; ++t) {
+              const float e = exp2f(-by * dy * dy);
+              const float wy = t < ur.ly ? e : 0.f;
+              row_red_f32<0, XM, LMIN, NQ>(ar, ar + pl4, ar + 2 * pl4, ex, f0, f1, f2, wy, ur.lx);
+              ar += px4;
+              dy += 1.f;
+              const bool wrap = ar == aend;
+              ar = wrap ? abase : ar;
+              dy = wrap ? ur.d0y : dy;
+            }
           }
-        }
+        };
+        if (LMIN < XM && __all_sync(0xffffffffu, ur.lx <= LMIN))
+          unit_rows(std::integral_constant<int, LMIN>());
+        else
+          unit_rows(std::integral_constant<int, XM>());
       }
       __syncthreads();
     }
