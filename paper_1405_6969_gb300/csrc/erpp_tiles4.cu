@@ -83,7 +83,6 @@
 namespace {
 
 // Threads per block of the tile kernels: 256 or 512 (a tiling option).
-constexpr int kMaxTz = 4;         // z-planes per tile (units per piece)
 constexpr int kDenseTile = 1024;  // pieces above which a tile accumulates in FP32
 constexpr int kSplitMaxPieces = 65535;  // compensated mode: most pieces of a split-word tile
 constexpr uint16_t kEmpty = 0xffffu;
