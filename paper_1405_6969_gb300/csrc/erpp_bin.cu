@@ -471,13 +471,13 @@ __global__ void __launch_bounds__(256) k_bin_count_multi(const erpp_box_dev* __r
                 });
 }
 
-// Block b scans the counts of box b (chunks of 4096 bins, the running total
-// carried from chunk to chunk) into its starts, total at start[nbins].
-__global__ void __launch_bounds__(1024) k_scan_multi(const erpp_box_dev* __restrict__ boxes) {
+// One block of 1024 threads scans nbins counts into their starts (chunks of
+// 4096 bins, the running total carried from chunk to chunk), total at
+// start[nbins].
+__device__ __forceinline__ void block_scan_bins(const int32_t* __restrict__ cnt,
+                                                int32_t* __restrict__ start, int nbins) {
   __shared__ int32_t ws[32];
   __shared__ int32_t tot;
-  const erpp_box_dev& B = boxes[blockIdx.x];
-  const int nbins = B.nbins;
   int32_t carry = 0;
   for (int c0 = 0; c0 < nbins; c0 += kScanChunk) {
     const int base = c0 + threadIdx.x * 4;
@@ -485,19 +485,33 @@ __global__ void __launch_bounds__(1024) k_scan_multi(const erpp_box_dev* __restr
     int32_t s = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      v[k] = (base + k < nbins) ? B.tile_cnt[base + k] : 0;
+      v[k] = (base + k < nbins) ? cnt[base + k] : 0;
       s += v[k];
     }
     int32_t run = carry + block_exclusive_scan(s, ws, &tot);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      if (base + k < nbins) B.tile_start[base + k] = run;
+      if (base + k < nbins) start[base + k] = run;
       run += v[k];
     }
     carry += tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0) B.tile_start[nbins] = carry;
+  if (threadIdx.x == 0) start[nbins] = carry;
+}
+
+// The scan of a box with at most kScanOneBins bins: one launch instead of
+// three.
+constexpr int kScanOneBins = 65536;
+__global__ void __launch_bounds__(1024) k_scan_one(const int32_t* __restrict__ cnt,
+                                                   int32_t* __restrict__ start, int nbins) {
+  block_scan_bins(cnt, start, nbins);
+}
+
+// Block b scans the counts of box b into its starts.
+__global__ void __launch_bounds__(1024) k_scan_multi(const erpp_box_dev* __restrict__ boxes) {
+  const erpp_box_dev& B = boxes[blockIdx.x];
+  block_scan_bins(B.tile_cnt, B.tile_start, B.nbins);
 }
 
 __global__ void __launch_bounds__(256) k_bin_fill_multi(const erpp_box_dev* __restrict__ boxes,
@@ -548,10 +562,15 @@ cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bo
                                         ctx->cap, ctx->tile_cnt, ctx->piece_slot, ms, ctx->err);
   }
   const int nchunks = (nbins + kScanChunk - 1) / kScanChunk;
-  ctx->launches += 3;
-  k_scan_local<<<nchunks, 1024, 0, st>>>(ctx->tile_cnt, ctx->tile_start, ctx->scan_tmp, nbins);
-  k_scan_top<<<1, 1024, 0, st>>>(ctx->scan_tmp, nchunks, ctx->tile_start, nbins);
-  k_scan_add<<<(nbins + 255) / 256, 256, 0, st>>>(ctx->tile_start, ctx->scan_tmp, nbins);
+  if (nbins <= kScanOneBins) {
+    ++ctx->launches;
+    k_scan_one<<<1, 1024, 0, st>>>(ctx->tile_cnt, ctx->tile_start, nbins);
+  } else {
+    ctx->launches += 3;
+    k_scan_local<<<nchunks, 1024, 0, st>>>(ctx->tile_cnt, ctx->tile_start, ctx->scan_tmp, nbins);
+    k_scan_top<<<1, 1024, 0, st>>>(ctx->scan_tmp, nchunks, ctx->tile_start, nbins);
+    k_scan_add<<<(nbins + 255) / 256, 256, 0, st>>>(ctx->tile_start, ctx->scan_tmp, nbins);
+  }
   if (n > 0) {
     int blocks = (int)((n + 255) / 256);
     ++ctx->launches;

@@ -252,9 +252,9 @@ def test_step_reproducible(erpp, name, w, npart):
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_step_launch_count(erpp, precision):
     """The library's own count of the kernels one step launches: FP32 =
-    binning (count, three scan kernels, fill) + gather + advance + scatter +
-    one or two halo merge kernels; FP64 plain form = gather + advance +
-    scatter."""
+    binning (count, one scan kernel for boxes of at most 65536 tiles, fill)
+    + gather + advance + scatter + one or two halo merge kernels; FP64 plain
+    form = gather + advance + scatter."""
     w = CASES[0][1]
     grid, st = _setup(w, CASES[0][2])
     ctx = erpp.Context(w.params(), precision=precision)
@@ -266,10 +266,10 @@ def test_step_launch_count(erpp, precision):
     if precision == "fp64":
         assert n == 3
     else:
-        # binning 5, gather, advance, scatter, then the halo merges: two
-        # through strips (10), one with the x-halo in clusters (9)
-        assert n == 10
-        for mode, want in (("cluster", 9), ("xclip", 9), ("merge", 10)):
+        # binning 3, gather, advance, scatter, then the halo merges: two
+        # through strips (8), one with the x-halo in clusters (7)
+        assert n == 8
+        for mode, want in (("cluster", 7), ("xclip", 7), ("merge", 8)):
             ctx.set_scatter_mode(mode)
             ctx.step(grid_t(grid, precision), ps)
             ctx.check()
