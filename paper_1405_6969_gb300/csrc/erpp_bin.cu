@@ -501,11 +501,40 @@ __device__ __forceinline__ void block_scan_bins(const int32_t* __restrict__ cnt,
 }
 
 // The scan of a box with at most kScanOneBins bins: one launch instead of
-// three.
+// three.  Up to 16384 bins each of the 1024 threads loads its run of 16
+// counts at once (four 16-byte loads), so the block waits for one round trip;
+// larger boxes go chunk by chunk.
 constexpr int kScanOneBins = 65536;
 __global__ void __launch_bounds__(1024) k_scan_one(const int32_t* __restrict__ cnt,
                                                    int32_t* __restrict__ start, int nbins) {
-  block_scan_bins(cnt, start, nbins);
+  if (nbins > 16 * 1024 || (nbins & 15) != 0) {
+    block_scan_bins(cnt, start, nbins);
+    return;
+  }
+  __shared__ int32_t ws[32];
+  __shared__ int32_t tot;
+  const int base = threadIdx.x * 16;
+  int4 v[4];
+  int32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = base < nbins ? reinterpret_cast<const int4*>(cnt + base)[k] : make_int4(0, 0, 0, 0);
+    s += v[k].x + v[k].y + v[k].z + v[k].w;
+  }
+  int32_t run = block_exclusive_scan(s, ws, &tot);
+  if (base < nbins) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      int4 o;
+      o.x = run;
+      o.y = o.x + v[k].x;
+      o.z = o.y + v[k].y;
+      o.w = o.z + v[k].z;
+      run = o.w + v[k].w;
+      reinterpret_cast<int4*>(start + base)[k] = o;
+    }
+  }
+  if (threadIdx.x == 0) start[nbins] = tot;
 }
 
 // Block b scans the counts of box b into its starts.
