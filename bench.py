@@ -461,8 +461,6 @@ def workload_record(w, args, peak, kahan=False, steps=100, made=None):
     for k in range(max(3, args.warmup)):
         ctx.step(u, ps, S=S, first_step=(k == 0))
     ctx.check()
-    ctx.profile_enable(True)
-    ctx.profile_read()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -471,6 +469,13 @@ def workload_record(w, args, peak, kahan=False, steps=100, made=None):
         ctx.step(u, ps, S=S)
     e1.record(stream)
     torch.cuda.synchronize()
+    ctx.check()
+    # per-phase times in steps of their own (no events between the timed
+    # steps' kernels)
+    ctx.profile_enable(True)
+    ctx.profile_read()
+    for _ in range(min(steps, 50)):
+        ctx.step(u, ps, S=S)
     phase_ms, nsteps = ctx.profile_read()
     ctx.profile_enable(False)
     ctx.check()
@@ -571,8 +576,6 @@ def main():
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
-    ctx.profile_enable(True)
-    ctx.profile_read()
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -586,6 +589,14 @@ def main():
     if ws > 1:
         dist.barrier()
     clocks = sampler.stop()
+    ctx.check()
+    # per-phase times from the library's events on the launching stream, in
+    # steps of their own (events between the phases would sit between kernels
+    # that otherwise launch back to back, so the timed steps above have none)
+    ctx.profile_enable(True)
+    ctx.profile_read()
+    for _ in range(min(args.steps, 50)):
+        ctx.step(u, ps, S=S)
     phase_ms, nsteps = ctx.profile_read()
     ctx.profile_enable(False)
     ctx.check()

@@ -214,6 +214,7 @@ __global__ void k_bin_count(erpp_kparams kp, int64_t n, const double* __restrict
                             int64_t acc_stride,
                             int32_t* __restrict__ tile_cnt, int32_t* __restrict__ slot, int ms,
                             uint32_t* err) {
+  erpp_pdl_enter();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   bin_count_one(kp, i, n, x0, x1, x2, geo_t, geo_c, xw, xw_len, d0x, lapc, up_acc, acc_stride,
@@ -274,6 +275,7 @@ __global__ void __launch_bounds__(256) k_bin_count_hist(
     float* __restrict__ d0x, float4* __restrict__ lapc, int32_t* __restrict__ tile_cnt,
     int32_t* __restrict__ slot, int ms, int nbins, uint32_t* err) {
   __shared__ int32_t hist[kHistBins];
+  erpp_pdl_enter();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bin_count_hist(kp, i, n, x0, x1, x2, geo_t, geo_c, d0x, lapc, tile_cnt, slot, ms, nbins, err,
                  hist);
@@ -358,6 +360,7 @@ __global__ void k_bin_fill(erpp_kparams kp, int64_t n, const float4* __restrict_
                            const int4* __restrict__ geo_c, const int32_t* __restrict__ start,
                            int32_t* __restrict__ slot, int ms,
                            int4* __restrict__ entries, int64_t cap, uint32_t* err) {
+  erpp_pdl_enter();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   bin_fill_one(kp, i, n, geo_t, geo_c, start, slot, ms, entries, cap, err);
@@ -507,6 +510,7 @@ __device__ __forceinline__ void block_scan_bins(const int32_t* __restrict__ cnt,
 constexpr int kScanOneBins = 65536;
 __global__ void __launch_bounds__(1024) k_scan_one(const int32_t* __restrict__ cnt,
                                                    int32_t* __restrict__ start, int nbins) {
+  erpp_pdl_enter();
   if (nbins > 16 * 1024 || (nbins & 15) != 0) {
     block_scan_bins(cnt, start, nbins);
     return;
@@ -577,23 +581,29 @@ cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bo
   if (n > 0 && kp.design == 4 && !kp.full_force && nbins <= kHistBins && ms <= kHistPieces) {
     // few tiles (a small box): count through block histograms
     ++ctx->launches;
-    k_bin_count_hist<<<(int)((n + 255) / 256), 256, 0, st>>>(
-        kp, n, x[0], x[1], x[2], ctx->geo_t, ctx->geo_c, ctx->d0x, nullptr, ctx->tile_cnt,
-        ctx->piece_slot, ms, nbins, ctx->err);
+    float4* no_lapc = nullptr;
+    e = erpp_launch_pdl(k_bin_count_hist, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st,
+                        0u, kp, n, x[0], x[1], x[2], ctx->geo_t, ctx->geo_c, ctx->d0x, no_lapc,
+                        ctx->tile_cnt, ctx->piece_slot, ms, nbins, ctx->err);
+    if (e != cudaSuccess) return e;
   } else if (n > 0) {
     int blocks = (int)((n + 255) / 256);
     ++ctx->launches;
-    k_bin_count<<<blocks, 256, 0, st>>>(kp, n, x[0], x[1], x[2], ctx->geo_t, ctx->geo_c,
-                                        kp.design == 4 ? nullptr : ctx->xw, ctx->xw_len,
-                                        kp.design == 4 ? ctx->d0x : nullptr,
-                                        kp.design == 4 && kp.full_force ? ctx->lapc : nullptr,
-                                        zero_acc ? ctx->up_acc : nullptr,
-                                        ctx->cap, ctx->tile_cnt, ctx->piece_slot, ms, ctx->err);
+    float* xw = kp.design == 4 ? nullptr : ctx->xw;
+    float* d0x = kp.design == 4 ? ctx->d0x : nullptr;
+    float4* lapc = kp.design == 4 && kp.full_force ? ctx->lapc : nullptr;
+    float* up_acc = zero_acc ? ctx->up_acc : nullptr;
+    e = erpp_launch_pdl(k_bin_count, dim3(blocks), dim3(256), 0, st, 0u, kp, n, x[0], x[1], x[2],
+                        ctx->geo_t, ctx->geo_c, xw, ctx->xw_len, d0x, lapc, up_acc, ctx->cap,
+                        ctx->tile_cnt, ctx->piece_slot, ms, ctx->err);
+    if (e != cudaSuccess) return e;
   }
   const int nchunks = (nbins + kScanChunk - 1) / kScanChunk;
   if (nbins <= kScanOneBins) {
     ++ctx->launches;
-    k_scan_one<<<1, 1024, 0, st>>>(ctx->tile_cnt, ctx->tile_start, nbins);
+    e = erpp_launch_pdl(k_scan_one, dim3(1), dim3(1024), 0, st, 0u,
+                        (const int32_t*)ctx->tile_cnt, ctx->tile_start, nbins);
+    if (e != cudaSuccess) return e;
   } else {
     ctx->launches += 3;
     k_scan_local<<<nchunks, 1024, 0, st>>>(ctx->tile_cnt, ctx->tile_start, ctx->scan_tmp, nbins);
@@ -603,9 +613,11 @@ cudaError_t bin_particles(erpp_ctx* ctx, int64_t n, const double* const x[3], bo
   if (n > 0) {
     int blocks = (int)((n + 255) / 256);
     ++ctx->launches;
-    k_bin_fill<<<blocks, 256, 0, st>>>(kp, n, ctx->geo_t, ctx->geo_c, ctx->tile_start,
-                                       ctx->piece_slot, ms, ctx->entries, ctx->entries_cap,
-                                       ctx->err);
+    e = erpp_launch_pdl(k_bin_fill, dim3(blocks), dim3(256), 0, st, 0u, kp, n,
+                        (const float4*)ctx->geo_t, (const int4*)ctx->geo_c,
+                        (const int32_t*)ctx->tile_start, ctx->piece_slot, ms, ctx->entries,
+                        ctx->entries_cap, ctx->err);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }

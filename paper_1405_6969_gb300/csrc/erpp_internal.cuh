@@ -444,6 +444,47 @@ __device__ __forceinline__ void erpp_set_err(uint32_t* err, uint32_t bit) {
   if (err) atomicOr(err, bit);
 }
 
+// Programmatic dependent launch between the kernels of a step.  Each such
+// kernel calls erpp_pdl_enter() before touching global memory: it lets the
+// next kernel on the stream be launched once every block of this one has
+// started, then waits until the previous kernel has completed and its writes
+// are visible.  A kernel launched without the attribute returns from the wait
+// at once.  The next kernel's blocks, once resident, wait in hardware (no
+// polling), and they are only launched after every block of this kernel is
+// resident or done, so no block waits for one that cannot run.
+__device__ __forceinline__ void erpp_pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launches kern on st with programmatic stream serialisation (the kernel
+// must call erpp_pdl_enter() first) and, when cluster_x > 0, clusters of
+// cluster_x blocks along x.
+template <typename... P, typename... A>
+inline cudaError_t erpp_launch_pdl(void (*kern)(P...), dim3 grid, dim3 block, size_t smem,
+                                   cudaStream_t st, unsigned cluster_x, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[2];
+  int na = 0;
+  at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[na].val.programmaticStreamSerializationAllowed = 1;
+  ++na;
+  if (cluster_x > 0) {
+    at[na].id = cudaLaunchAttributeClusterDimension;
+    at[na].val.clusterDim.x = cluster_x;
+    at[na].val.clusterDim.y = 1;
+    at[na].val.clusterDim.z = 1;
+    ++na;
+  }
+  cfg.attrs = at;
+  cfg.numAttrs = na;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<A&&>(args)...);
+}
+
 // Kernel normalisation of one particle from its geometry record: the gather
 // returns norm * sum_j e_x e_y e_z u_j with e_a = 2^(-beta_a d_a^2) (d in grid
 // units), so norm = 1 / (sum_x e_x sum_y e_y sum_z e_z) for unit discrete mass
