@@ -972,7 +972,10 @@ __device__ __forceinline__ TileAcc scatter_tile(const erpp_kparams& kp, int tile
   const int plane = kp.plane, px = kp.px, pxy = kp.pxy;
   const bool any = e0 < e1;
   const bool fixedp = (e1 - e0) <= (MODE == 0 ? kDenseTile : kSplitMaxPieces);
-  const int bs = any ? batch_size(e1 - e0, PB) : 1;
+  // batches of PB pieces, the remainder last: at about 1.8 units per piece a
+  // full batch nearly fills two rounds of 256 lanes, where an even split of
+  // a 370-piece tile needs two rounds for each half
+  const int bs = any ? PB : 1;
   const int4 rfirst = load_rec(entries, e0, min(bs, e1 - e0));  // overlaps the clearing
   float scale = 1.f, inv_scale = 1.f;
   {
